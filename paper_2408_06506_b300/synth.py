@@ -1,0 +1,438 @@
+"""Seeded synthetic inputs for the tactile step.
+
+This module only *makes inputs*: analytic object shapes baked into signed-distance
+grids, taxel templates, pad poses and twists, contact parameters, elastomer depth
+maps and per-pixel shading coefficients.  It contains none of the tactile step's
+own arithmetic (no SDF interpolation, no force law, no normal estimation, no
+shading); both the CUDA library and the FP64 oracle consume what it produces.
+
+Conventions shared by every consumer:
+
+* SDF grid: float32 array ``[n2][n1][n0]`` (x fastest), node ``(i, j, k)`` at
+  ``origin + (i, j, k) * voxel`` in the object frame; negative inside the object.
+* Taxel template: float32 ``[T][3]`` in the pad frame, on the ``z = 0`` plane,
+  row-major over ``ny`` rows by ``nx`` columns at ``pitch`` metres, centred.
+  The pad's ``+z`` axis is the outward normal pointing toward the object.
+* Pad pose: float32 ``[7]`` = ``(tx, ty, tz, qw, qx, qy, qz)``, the transform from
+  pad frame to object frame, ``x_o = R(q) x_p + t``.
+* Pad twist: float32 ``[6]`` = ``(vx, vy, vz, wx, wy, wz)``, the pad's velocity
+  relative to the object in the object frame, referenced at the object origin:
+  a pad-fixed point at ``x_o`` moves with ``v + w x x_o``.
+* Depth map: float32 ``[H][W]``, camera-to-gel distance in metres; the
+  undeformed gel reads the constant ``D0``.
+* Shading coefficients: float32 ``[S][6][3][H][W]`` (term, channel, row, col).
+
+Random streams use NumPy's PCG64 with the seeds stated by each function.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+D0 = 0.020  # undeformed camera-to-gel distance [m]
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# ---------------------------------------------------------------------------
+# Analytic shapes (object frame, centred at the origin, prism/cylinder axis = z)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Shape:
+    kind: str                 # "sphere" | "box" | "cylinder" | "hexprism" | "plane"
+    dims: tuple               # sphere (R,), box (hx, hy, hz), cylinder (r, hz), hexprism (apothem, hz)
+                              # plane (nx, ny, nz, offset): occupied where n.x < offset
+
+    def extent(self) -> float:
+        """Largest full dimension of the shape (for grid sizing)."""
+        k, d = self.kind, self.dims
+        if k == "sphere":
+            return 2 * d[0]
+        if k == "box":
+            return 2 * max(d)
+        if k == "cylinder":
+            return 2 * max(d[0], d[1])
+        if k == "hexprism":
+            return 2 * max(2 * d[0] / math.sqrt(3.0), d[1])
+        raise ValueError(k)
+
+    def sdf(self, x: np.ndarray) -> np.ndarray:
+        """Exact signed distance at points ``x[..., 3]`` (float64)."""
+        k, d = self.kind, self.dims
+        if k == "sphere":
+            return np.linalg.norm(x, axis=-1) - d[0]
+        if k == "plane":
+            n = np.asarray(d[:3], dtype=np.float64)
+            n = n / np.linalg.norm(n)
+            return x @ n - d[3]
+        if k == "box":
+            q = np.abs(x) - np.asarray(d, dtype=np.float64)
+            outside = np.linalg.norm(np.maximum(q, 0.0), axis=-1)
+            inside = np.minimum(q.max(axis=-1), 0.0)
+            return outside + inside
+        if k == "cylinder":
+            r, hz = d
+            q = np.stack([np.hypot(x[..., 0], x[..., 1]) - r, np.abs(x[..., 2]) - hz], -1)
+            return np.linalg.norm(np.maximum(q, 0.0), axis=-1) + np.minimum(q.max(axis=-1), 0.0)
+        if k == "hexprism":
+            a, hz = d
+            d2 = _hexagon_sdf(x[..., 0], x[..., 1], a)
+            q = np.stack([d2, np.abs(x[..., 2]) - hz], -1)
+            return np.linalg.norm(np.maximum(q, 0.0), axis=-1) + np.minimum(q.max(axis=-1), 0.0)
+        raise ValueError(k)
+
+    def support(self, dvec: np.ndarray) -> float:
+        """max over points x of the shape of dvec . x (support function)."""
+        k, d = self.kind, self.dims
+        dvec = np.asarray(dvec, dtype=np.float64)
+        if k == "sphere":
+            return d[0] * float(np.linalg.norm(dvec))
+        if k == "box":
+            return float(np.abs(dvec) @ np.asarray(d, dtype=np.float64))
+        if k == "cylinder":
+            return d[0] * float(np.hypot(dvec[0], dvec[1])) + d[1] * abs(float(dvec[2]))
+        if k == "hexprism":
+            verts = _hexagon_vertices(d[0])
+            return float(np.max(verts @ dvec[:2])) + d[1] * abs(float(dvec[2]))
+        raise ValueError(k)
+
+
+def _hexagon_vertices(apothem: float) -> np.ndarray:
+    """Regular hexagon with flat sides at y = +-apothem: vertices at 0, 60, ... degrees."""
+    rho = 2.0 * apothem / math.sqrt(3.0)
+    ang = np.arange(6) * (math.pi / 3.0)
+    return np.stack([rho * np.cos(ang), rho * np.sin(ang)], -1)
+
+
+def _hexagon_sdf(px: np.ndarray, py: np.ndarray, apothem: float) -> np.ndarray:
+    """Exact 2-D signed distance to the hexagon of ``_hexagon_vertices``.
+
+    Fold by symmetry: first into the quadrant x, y >= 0, then mirror across the
+    60-degree line through the centre, so the point lies in the wedge 60..120
+    degrees that the top side (y = apothem, |x| <= apothem/sqrt 3) spans.  In that
+    wedge the top side holds the nearest boundary point: inside, the distance is
+    apothem - y; outside, it is the distance to the clamped point on the side.
+    """
+    x = np.abs(px)
+    y = np.abs(py)
+    ux, uy = 0.5, math.sqrt(3.0) / 2.0          # unit vector of the 60-degree line
+    below = (ux * y - uy * x) < 0.0             # angle under 60 degrees
+    pu = x * ux + y * uy
+    x, y = np.where(below, 2 * pu * ux - x, x), np.where(below, 2 * pu * uy - y, y)
+    half_side = apothem / math.sqrt(3.0)
+    dx = x - np.clip(x, -half_side, half_side)
+    dy = y - apothem
+    return np.where(dy > 0.0, np.hypot(dx, dy), dy)
+
+
+@dataclass
+class Grid:
+    data: np.ndarray          # float32 [n2][n1][n0]
+    origin: np.ndarray        # float32 [3]
+    voxel: float              # float32-representable
+    shape: Shape | None = None
+
+    @property
+    def n(self) -> tuple:
+        return (self.data.shape[2], self.data.shape[1], self.data.shape[0])
+
+
+def bake(shape: Shape, n: int | tuple, voxel: float, origin=None) -> Grid:
+    """Sample the shape's exact SDF at the grid nodes (float64 -> float32)."""
+    if isinstance(n, int):
+        n = (n, n, n)
+    voxel = float(np.float32(voxel))
+    if origin is None:
+        origin = [-(n[a] - 1) * voxel / 2.0 for a in range(3)]
+    origin = np.asarray(origin, dtype=np.float32)
+    ax = [origin[a].astype(np.float64) + np.arange(n[a], dtype=np.float64) * voxel for a in range(3)]
+    zz, yy, xx = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    pts = np.stack([xx, yy, zz], -1)
+    data = shape.sdf(pts).astype(np.float32)
+    return Grid(np.ascontiguousarray(data), origin, voxel, shape)
+
+
+def bake_field(values_fn, n: tuple, voxel: float, origin) -> Grid:
+    """Bake an arbitrary callable f(x, y, z) (float64 arrays) into a grid."""
+    voxel = float(np.float32(voxel))
+    origin = np.asarray(origin, dtype=np.float32)
+    ax = [origin[a].astype(np.float64) + np.arange(n[a], dtype=np.float64) * voxel for a in range(3)]
+    zz, yy, xx = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    return Grid(np.ascontiguousarray(values_fn(xx, yy, zz).astype(np.float32)), origin, voxel, None)
+
+
+# ---------------------------------------------------------------------------
+# Rotations (input synthesis only)
+# ---------------------------------------------------------------------------
+
+def quat_to_matrix(q) -> np.ndarray:
+    w, x, y, z = (float(v) for v in q)
+    s = math.sqrt(w * w + x * x + y * y + z * z)
+    w, x, y, z = w / s, x / s, y / s, z / s
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+        [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+        [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def quat_multiply(a, b):
+    aw, ax, ay, az = a
+    bw, bx, by, bz = b
+    return np.array([aw * bw - ax * bx - ay * by - az * bz,
+                     aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx,
+                     aw * bz + ax * by - ay * bx + az * bw])
+
+
+def random_quaternion(g: np.random.Generator) -> np.ndarray:
+    """Uniform on SO(3): a normalised 4-D Gaussian, sign fixed to qw >= 0."""
+    q = g.standard_normal(4)
+    q /= np.linalg.norm(q)
+    return q if q[0] >= 0 else -q
+
+
+def quat_from_axis_angle(axis, angle) -> np.ndarray:
+    axis = np.asarray(axis, dtype=np.float64)
+    axis = axis / np.linalg.norm(axis)
+    return np.concatenate([[math.cos(angle / 2)], math.sin(angle / 2) * axis])
+
+
+# ---------------------------------------------------------------------------
+# Pads
+# ---------------------------------------------------------------------------
+
+def taxel_grid(ny: int, nx: int, pitch: float) -> np.ndarray:
+    """Taxel template [ny*nx][3] (row-major, x fastest), centred, z = 0."""
+    xs = (np.arange(nx) - (nx - 1) / 2.0) * pitch
+    ys = (np.arange(ny) - (ny - 1) / 2.0) * pitch
+    yy, xx = np.meshgrid(ys, xs, indexing="ij")
+    return np.ascontiguousarray(np.stack([xx, yy, np.zeros_like(xx)], -1).reshape(-1, 3).astype(np.float32))
+
+
+def place_pad(shape: Shape, q: np.ndarray, delta: float, offset_xy=(0.0, 0.0)) -> np.ndarray:
+    """Pose whose pad plane cuts ``delta`` metres into the shape (negative = gap).
+
+    The pad normal ``n = R e_z`` points toward the object; the object's point
+    nearest the pad along ``n`` sits at ``n.x = -support(-n)``; the pad plane is
+    put ``delta`` beyond it, and shifted in-plane by ``offset_xy`` (pad axes).
+    """
+    Rm = quat_to_matrix(q)
+    n = Rm[:, 2]
+    lowest = -shape.support(-n)
+    t = (lowest + delta) * n + offset_xy[0] * Rm[:, 0] + offset_xy[1] * Rm[:, 1]
+    return np.concatenate([t, q]).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# Depth maps and shading coefficients
+# ---------------------------------------------------------------------------
+
+def pixel_plane_points(H: int, W: int, extent_x: float, extent_y: float) -> np.ndarray:
+    """Pad-frame points (pixel centres on z = 0) of an H x W image covering the pad."""
+    xs = -extent_x / 2 + (np.arange(W) + 0.5) * (extent_x / W)
+    ys = -extent_y / 2 + (np.arange(H) + 0.5) * (extent_y / H)
+    yy, xx = np.meshgrid(ys, xs, indexing="ij")
+    return np.stack([xx, yy, np.zeros_like(xx)], -1)
+
+
+def depth_map(shape: Shape, pose: np.ndarray, H: int, W: int, extent_x: float, extent_y: float,
+              d0: float = D0) -> np.ndarray:
+    """Heightfield of the gel: D = D0 - max(0, -sdf(pixel point on the pad plane)).
+
+    A synthetic stand-in for the in-sensor camera render; it gives a flat
+    background with an indentation blob wherever the object cuts the pad plane.
+    """
+    P = pixel_plane_points(H, W, extent_x, extent_y).reshape(-1, 3)
+    Rm = quat_to_matrix(pose[3:7])
+    xo = P @ Rm.T + pose[:3].astype(np.float64)
+    pen = np.maximum(0.0, -shape.sdf(xo))
+    return (d0 - pen).reshape(H, W).astype(np.float32)
+
+
+def shading_coeffs(n_sensor: int, H: int, W: int, seed: int) -> np.ndarray:
+    """Per-pixel quadratic shading coefficients [S][6][3][H][W].
+
+    Term 0 is the background: 90 + 60 (1 - r^2) plus a per-channel offset, with
+    r the pixel's radius normalised to the image half-diagonal.  Terms 1-2 are
+    drawn U(-120, 120), terms 3-5 U(-80, 80) at the four image corners and
+    varied bilinearly across the image.
+    """
+    g = rng(seed)
+    out = np.empty((n_sensor, 6, 3, H, W), dtype=np.float32)
+    v = (np.arange(H) + 0.5) / H
+    u = (np.arange(W) + 0.5) / W
+    vv, uu = np.meshgrid(v, u, indexing="ij")
+    r2 = ((uu - 0.5) ** 2 + (vv - 0.5) ** 2) / 0.5
+    for s in range(n_sensor):
+        offs = g.uniform(-20, 20, size=3)
+        for c in range(3):
+            out[s, 0, c] = 90.0 + 60.0 * (1.0 - r2) + offs[c]
+        for k in range(1, 6):
+            amp = 120.0 if k <= 2 else 80.0
+            for c in range(3):
+                cor = g.uniform(-amp, amp, size=4)  # (0,0) (0,1) (1,0) (1,1)
+                out[s, k, c] = ((1 - vv) * (1 - uu) * cor[0] + (1 - vv) * uu * cor[1]
+                                + vv * (1 - uu) * cor[2] + vv * uu * cor[3])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Whole workloads
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Scene:
+    """Everything one tactile step consumes (host numpy arrays)."""
+    grids: list                       # list[Grid]
+    taxels: np.ndarray                # [T][3] f32
+    obj_id: np.ndarray                # [E] i32
+    pad_pose: np.ndarray              # [E][P][7] f32
+    pad_twist: np.ndarray             # [E][P][6] f32
+    k_n: np.ndarray                   # [1] or [E] f32
+    k_d: np.ndarray
+    k_t: np.ndarray
+    mu: np.ndarray
+    H: int = 0
+    W: int = 0
+    pitch_x: float = 0.0
+    pitch_y: float = 0.0
+    coeffs: np.ndarray | None = None  # [S][6][3][H][W] f32
+    sensor_id: np.ndarray | None = None   # [E*P] i32
+    depth_map: np.ndarray | None = None   # [E][P][H][W] f32
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def E(self):
+        return self.pad_pose.shape[0]
+
+    @property
+    def P(self):
+        return self.pad_pose.shape[1]
+
+    @property
+    def T(self):
+        return self.taxels.shape[0]
+
+
+def scene_sphere_pad(seed: int = 1, E: int = 1, ny: int = 16, nx: int = 20, pitch: float = 1e-3,
+                     R: float = 5e-3, n: int = 64, voxel: float = 0.25e-3, H: int = 120, W: int = 160,
+                     vel_sigma: float = 0.02, with_images: bool = True) -> Scene:
+    """One pad pressed by a sphere (R = 5 mm, 64^3 grid at 0.25 mm), per env.
+
+    Indentation U(0, 1 mm), in-plane offset U(-3, 3 mm), twist v ~ N(0, 0.02 m/s)
+    per axis with zero angular part; k_n = 1e4, k_d = 0, k_t = 1e2, mu = 0.5;
+    a 160 x 120 depth map of the same contact and seeded shading coefficients
+    (seed + 100).
+    """
+    g = rng(seed)
+    shape = Shape("sphere", (R,))
+    grid = bake(shape, n, voxel)
+    taxels = taxel_grid(ny, nx, pitch)
+    pose = np.zeros((E, 1, 7), np.float32)
+    twist = np.zeros((E, 1, 6), np.float32)
+    ext_x, ext_y = (nx - 1) * pitch, (ny - 1) * pitch
+    dmaps = np.zeros((E, 1, H, W), np.float32) if with_images else None
+    for e in range(E):
+        delta = g.uniform(0.0, 1e-3)
+        off = g.uniform(-3e-3, 3e-3, size=2)
+        q = np.array([1.0, 0.0, 0.0, 0.0])
+        pose[e, 0] = place_pad(shape, q, delta, off)
+        twist[e, 0, :3] = g.normal(0.0, vel_sigma, size=3)
+        if with_images:
+            dmaps[e, 0] = depth_map(shape, pose[e, 0], H, W, ext_x, ext_y)
+    sc = Scene([grid], taxels, np.zeros(E, np.int32), pose, twist,
+               np.array([1e4], np.float32), np.array([0.0], np.float32),
+               np.array([1e2], np.float32), np.array([0.5], np.float32))
+    if with_images:
+        sc.H, sc.W = H, W
+        sc.pitch_x, sc.pitch_y = ext_x / W, ext_y / H
+        sc.coeffs = shading_coeffs(1, H, W, seed + 100)
+        sc.sensor_id = np.zeros(E, np.int32)
+        sc.depth_map = dmaps
+    return sc
+
+
+def object_set(seed: int, n_obj: int = 8, n: int = 128, dims_mm=(5.0, 20.0)) -> list:
+    """Cylinders, boxes and hexagonal prisms with seeded dimensions, baked at n^3.
+
+    Kinds cycle 3 cylinders, 3 boxes, 2 hex prisms (for 8 objects); each full
+    dimension is U(dims_mm) millimetres; the grid side is the largest dimension
+    plus 6 mm, so the voxel is side / (n - 1).
+    """
+    g = rng(seed)
+    kinds = (["cylinder"] * 3 + ["box"] * 3 + ["hexprism"] * 2)
+    grids = []
+    lo, hi = dims_mm[0] * 1e-3, dims_mm[1] * 1e-3
+    for i in range(n_obj):
+        kind = kinds[i % len(kinds)]
+        if kind == "cylinder":
+            shape = Shape(kind, (g.uniform(lo, hi) / 2, g.uniform(lo, hi) / 2))
+        elif kind == "box":
+            shape = Shape(kind, tuple(g.uniform(lo, hi, size=3) / 2))
+        else:
+            shape = Shape(kind, (g.uniform(lo, hi) / 2, g.uniform(lo, hi) / 2))
+        side = shape.extent() + 6e-3
+        grids.append(bake(shape, n, side / (n - 1)))
+    return grids
+
+
+def scene_objects(seed: int = 2, E: int = 4096, P: int = 2, ny: int = 20, nx: int = 25,
+                  pitch: float = 1e-3, n_obj: int = 8, n: int = 128, H: int = 240, W: int = 320,
+                  vel_sigma: float = 0.05, depth_maps: str = "exact", n_distinct_maps: int = 256,
+                  grids: list | None = None) -> Scene:
+    """E envs x P pads against one of ``n_obj`` objects each.
+
+    Pad orientation uniform on SO(3); the pad plane cuts U(-2, 2) mm into the
+    object's nearest point (about half the pads touch) with an in-plane offset
+    U(-2, 2) mm; twist v ~ N(0, 0.05 m/s) per axis, zero angular part; obj_id
+    U{0..n_obj-1}; contact parameters per env (k_n U(0.5e4, 1.5e4), k_d 0,
+    k_t U(50, 150), mu U(0.3, 0.7)); pad slot p uses sensor model p.
+
+    ``depth_maps``: "exact" renders every pad's own heightfield; "cycled" renders
+    ``n_distinct_maps`` of them and fills the batch by cycling through those
+    (each slot is still its own buffer); "none" skips images.
+    """
+    g = rng(seed)
+    if grids is None:
+        grids = object_set(seed, n_obj, n)
+    taxels = taxel_grid(ny, nx, pitch)
+    obj = g.integers(0, len(grids), size=E).astype(np.int32)
+    pose = np.zeros((E, P, 7), np.float32)
+    twist = np.zeros((E, P, 6), np.float32)
+    for e in range(E):
+        shape = grids[obj[e]].shape
+        for p in range(P):
+            q = random_quaternion(g)
+            delta = g.uniform(-2e-3, 2e-3)
+            off = g.uniform(-2e-3, 2e-3, size=2)
+            pose[e, p] = place_pad(shape, q, delta, off)
+            twist[e, p, :3] = g.normal(0.0, vel_sigma, size=3)
+    k_n = g.uniform(0.5e4, 1.5e4, size=E).astype(np.float32)
+    k_d = np.zeros(E, np.float32)
+    k_t = g.uniform(50.0, 150.0, size=E).astype(np.float32)
+    mu = g.uniform(0.3, 0.7, size=E).astype(np.float32)
+    sc = Scene(grids, taxels, obj, pose, twist, k_n, k_d, k_t, mu)
+    if depth_maps != "none":
+        ext_x, ext_y = (nx - 1) * pitch, (ny - 1) * pitch
+        sc.H, sc.W = H, W
+        sc.pitch_x, sc.pitch_y = ext_x / W, ext_y / H
+        sc.coeffs = shading_coeffs(P, H, W, seed + 100)
+        sc.sensor_id = np.tile(np.arange(P, dtype=np.int32), E)
+        B = E * P
+        dm = np.empty((E, P, H, W), np.float32)
+        flat = dm.reshape(B, H, W)
+        nd = B if depth_maps == "exact" else min(B, n_distinct_maps)
+        for b in range(nd):
+            e, p = divmod(b, P)
+            flat[b] = depth_map(grids[obj[e]].shape, pose[e, p], H, W, ext_x, ext_y)
+        for b in range(nd, B):
+            flat[b] = flat[b % nd]
+        sc.depth_map = dm
+        sc.meta["distinct_depth_maps"] = nd
+    return sc
