@@ -1,0 +1,419 @@
+"""Benchmark of the fused tactile step (TacSL, arXiv 2408.06506) on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--envs E] [--no-e2e] [--no-cpu-baseline]
+
+Workload (per GPU): 4096 envs x 2 pads x 20x25 taxels against eight 128^3 float32
+SDFs (3 cylinders, 3 boxes, 2 hex prisms, seeded 5-20 mm), random poses within
++-2 mm of contact, v ~ N(0, 0.05 m/s), and 8192 320x240 float32 depth maps shaded to
+uint8 RGB by two sensors' per-pixel quadratic models.  A step is one tacsl_tactile_step
+launch over all of it: 4,096,000 taxel-points and 8192 tactile images.
+
+The JSON line reports taxel-points/s (value) and tactile images/s, the roofline of the
+step kernel against the measured HBM copy bandwidth, an end-to-end figure through host
+buffers, SM clocks sampled during the timed region, and the FP64 oracle timed on the
+host's cores on a bounded sample of the same workload.
+
+--impl reference times that oracle alone, as the reference arm.
+Multi-GPU (torchrun): every rank runs its own 4096 envs (weak scaling, no collective
+on the data path); ranks meet only at the barriers around the timed region and for the
+max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "taxel-points/s + tactile images/s at 4096 envs vs plain; served p50/p99 latency"
+WORKLOAD = "4096 envs x 2 pads x 20x25 taxels, 8 SDFs 128^3 f32, 8192 depth maps 320x240 f32 -> uint8 RGB"
+L2_BYTES = 126 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--envs", type=int, default=4096)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--seed", type=int, default=2)
+    return ap.parse_args()
+
+
+def make_scene(envs, seed):
+    from paper_2408_06506_b300 import synth
+    return synth.scene_objects(seed=seed, E=envs, P=2, depth_maps="cycled", n_distinct_maps=256)
+
+
+# ---------------------------------------------------------------------------
+# bytes the method must move per step (compulsory traffic)
+# ---------------------------------------------------------------------------
+
+def touched_sdf_bytes(sc):
+    """Unique 32-byte sectors of the SDF grids the step's stencils touch (bench accounting)."""
+    total = 0
+    from paper_2408_06506_b300.synth import quat_to_matrix
+    pts_by_obj = {}
+    for e in range(sc.E):
+        for p in range(sc.P):
+            pose = sc.pad_pose[e, p].astype(np.float64)
+            xo = sc.taxels.astype(np.float64) @ quat_to_matrix(pose[3:]).T + pose[:3]
+            pts_by_obj.setdefault(int(sc.obj_id[e]), []).append(xo)
+    for i, g in pts_by_obj.items():
+        grid = sc.grids[i]
+        n = np.array(grid.data.shape[::-1])
+        x = np.concatenate(g)
+        u = (x - grid.origin.astype(np.float64)) / grid.voxel
+        ok = np.all((u >= 0.5) & (u <= n - 1.5), axis=1)
+        b = np.minimum(np.floor(u[ok] - 0.5).astype(np.int64), n - 3)
+        mark = np.zeros(int(np.prod(n)) // 8 + 1, bool)
+        for dz in range(3):
+            for dy in range(3):
+                lin = ((b[:, 2] + dz) * n[1] + (b[:, 1] + dy)) * n[0] + b[:, 0]
+                mark[lin // 8] = True
+                mark[(lin + 2) // 8] = True
+        total += int(mark.sum()) * 32
+    return total
+
+
+def algorithmic_bytes(sc, sdf_bytes):
+    E, P, T, HW = sc.E, sc.P, sc.T, sc.H * sc.W
+    B = E * P
+    parts = {
+        "depth_map_read": 4 * B * HW,
+        "rgb_write": 3 * B * HW,
+        "taxel_outputs": 28 * B * T,
+        "wrench": 24 * B,
+        "pose_twist": 52 * B,
+        "params_ids": 20 * E + 4 * B,
+        "taxel_template": 12 * T,
+        "sdf_sectors_touched": sdf_bytes,
+        "shading_coeffs": sc.coeffs.nbytes,
+    }
+    return sum(parts.values()), parts
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU (FP64 oracle) timing on a bounded sample
+# ---------------------------------------------------------------------------
+
+def oracle_rate(sc, n_env, seconds_target, max_passes=1000):
+    """Run the oracle's step (forces + images) on the first n_env envs until about
+    seconds_target has elapsed; returns taxel-points/s, images/s, threads, passes."""
+    import oracle
+    oracle.build()
+    nt = oracle.default_threads()
+    E = n_env
+    sl = slice(0, E)
+    dm = sc.depth_map[sl].reshape(E * sc.P, sc.H, sc.W)
+    sid = sc.sensor_id[: E * sc.P]
+    kp = [v if v.shape[0] == 1 else v[sl] for v in (sc.k_n, sc.k_d, sc.k_t, sc.mu)]
+    t0 = time.perf_counter()
+    passes = 0
+    while True:
+        oracle.penalty_forces(sc.grids, sc.taxels, sc.obj_id[sl], sc.pad_pose[sl], sc.pad_twist[sl], *kp,
+                              nthreads=nt)
+        oracle.shade(sc.coeffs, sc.pitch_x, sc.pitch_y, sid, dm, nthreads=nt)
+        passes += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_target or passes >= max_passes:
+            break
+    return E * sc.P * sc.T * passes / el, E * sc.P * passes / el, nt, passes, el
+
+
+def run_reference(args, rank):
+    """Reference arm: the FP64 oracle as it stands, timed on the host cores."""
+    if rank != 0:
+        return
+    sc = make_scene(max(64, min(args.envs, 256)), args.seed)
+    import oracle
+    oracle.build()
+    nt = oracle.default_threads()
+    # size one step's sample so that warmup + steps fit in ~3 minutes
+    t0 = time.perf_counter()
+    oracle_rate(sc, 1, 0.0, max_passes=1)
+    per_env = max(time.perf_counter() - t0, 1e-4)
+    n_env = int(max(1, min(sc.E, 180.0 / (args.steps + args.warmup) / per_env)))
+    for _ in range(args.warmup):
+        oracle_rate(sc, n_env, 0.0, max_passes=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_rate(sc, n_env, 0.0, max_passes=1)
+    el = time.perf_counter() - t0
+    value = args.steps * n_env * sc.P * sc.T / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "taxel-points/s",
+        "images_per_s": args.steps * n_env * sc.P / el, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "envs_per_gpu": args.envs, "reference_sample_envs_per_step": n_env},
+        "cpu_baseline": {"value": value, "unit": "taxel-points/s", "cores": nt, "kind": "oracle",
+                         "sample": f"first {n_env} envs (x2 pads, their {2 * n_env} images) per step"},
+        "e2e": {"value": value, "unit": "taxel-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank, dist):
+    import torch
+
+    import paper_2408_06506_b300 as tacsl
+    from paper_2408_06506_b300 import build
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    tacsl.load()
+    sc = make_scene(args.envs, args.seed + rank)
+
+    def dev(a):
+        return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+    sdfs = tacsl.SdfSet.from_grids(sc.grids)
+    params = tacsl.ContactParams(dev(sc.k_n), dev(sc.k_d), dev(sc.k_t), dev(sc.mu))
+    shading = tacsl.Shading(dev(sc.coeffs), sc.pitch_x, sc.pitch_y)
+    taxels, obj_id, pose, twist = dev(sc.taxels), dev(sc.obj_id), dev(sc.pad_pose), dev(sc.pad_twist)
+    sensor_id, depth_map = dev(sc.sensor_id), dev(sc.depth_map)
+    E, P, T, HW = sc.E, sc.P, sc.T, sc.H * sc.W
+    outs = dict(depth=torch.empty(E, P, T, device="cuda"), f_n=torch.empty(E, P, T, 3, device="cuda"),
+                f_t=torch.empty(E, P, T, 3, device="cuda"), wrench=torch.empty(E, P, 6, device="cuda"),
+                rgb=torch.empty(E * P, sc.H, sc.W, 3, dtype=torch.uint8, device="cuda"))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        tacsl.tactile_step(sdfs, params, taxels, obj_id, pose, twist, shading, sensor_id, depth_map, **outs)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert tacsl.check_errors() == 0
+
+    # ---- device-timed region: K fused steps, inputs resident in HBM (4.4 GB > L2) ----
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(_smi_id(local_rank)) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    taxel_pts = world * E * P * T
+    images = world * E * P
+    value = taxel_pts / (ms_step * 1e-3)
+
+    # ---- end to end: pinned host inputs in, results back to pinned host, every step ----
+    e2e = None
+    if not args.no_e2e:
+        h_in = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory() for k, v in
+                (("pose", sc.pad_pose), ("twist", sc.pad_twist), ("depth_map", sc.depth_map),
+                 ("obj_id", sc.obj_id), ("sensor_id", sc.sensor_id))}
+        d_in = {"pose": pose, "twist": twist, "depth_map": depth_map, "obj_id": obj_id, "sensor_id": sensor_id}
+        h_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs.items()}
+        h2d = sum(t.numel() * t.element_size() for t in h_in.values())
+        d2h = sum(t.numel() * t.element_size() for t in h_out.values())
+
+        def e2e_step():
+            for k, t in h_in.items():
+                d_in[k].copy_(t, non_blocking=True)
+            tacsl.tactile_step(sdfs, params, taxels, d_in["obj_id"], d_in["pose"], d_in["twist"], shading,
+                               d_in["sensor_id"], d_in["depth_map"], **outs)
+            for k, t in outs.items():
+                h_out[k].copy_(t, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * E * P * T * args.e2e_steps / el, "unit": "taxel-points/s",
+               "images_per_s": world * E * P * args.e2e_steps / el, "ms_per_step": 1e3 * el / args.e2e_steps,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+               "path": "pinned host -> cudaMemcpyAsync -> tacsl_tactile_step -> pinned host, one stream"}
+
+    if rank != 0:
+        return
+    # ---- roofline of the step kernel (the only kernel of a step) ----
+    import json as _json
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak = float(_json.load(open(peaks_path))["hbm_gbs"])
+        peak_src = "measured"
+    else:
+        peak, peak_src = 6400.0, "fallback"
+    sdf_bytes = touched_sdf_bytes(sc)
+    alg, parts = algorithmic_bytes(sc, sdf_bytes)
+    achieved = alg / (ms_step * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if os.path.exists(tfile):
+        tj = _json.load(open(tfile))
+        if tj.get("source_hash") == _source_hash():
+            traffic = tj.get("dram_bytes_per_launch")
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        tp, ips, nt, passes, el = oracle_rate(sc, min(256, E), args.cpu_seconds)
+        cpu = {"value": tp, "unit": "taxel-points/s", "images_per_s": ips, "cores": nt, "kind": "oracle",
+               "sample": f"first {min(256, E)} envs x 2 pads and their {2 * min(256, E)} images, "
+                         f"{passes} passes in {el:.1f} s (FP64, OpenMP)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "taxel-points/s", "images_per_s": images / (ms_step * 1e-3),
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "envs_per_gpu": E, "pads": P, "taxels_per_pad": T,
+                   "image": [sc.H, sc.W], "n_sdf": len(sc.grids), "sdf_n": 128,
+                   "distinct_depth_maps": sc.meta["distinct_depth_maps"],
+                   "l2": f"no flush: every step streams {alg / 1e9:.2f} GB (> {L2_BYTES / 2**20:.0f} MiB L2)",
+                   "parallelism": f"env-shard x{world}, no collective"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "tacsl::step_kernel", "algorithmic_bytes": alg,
+                     "bytes": parts, "peak_source": f"{peak_src} hbm_gbs (copy)"},
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _smi_id(ordinal):
+    """nvidia-smi id of a CUDA ordinal (its UUID; ordinals differ under CUDA_VISIBLE_DEVICES)."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(ordinal).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(ordinal)
+
+
+def _source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2408_06506_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        dist = tdist
+    try:
+        run_ours(args, rank, world, local_rank, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

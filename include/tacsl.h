@@ -1,0 +1,194 @@
+/*
+ * tacsl.h -- C ABI of the B300 (sm_103a) tactile-step library (libtacsl.so).
+ *
+ * The batched tactile step of TacSL (arXiv 2408.06506): SDF queries with
+ * finite-difference gradients at every taxel of every sensor pad, penalty normal
+ * and friction-capped shear forces, per-pad net wrenches (Sec. III-C), and the
+ * depth map -> normals -> per-pixel shading -> uint8 RGB tactile image
+ * (Sec. III-B), over thousands of environments on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller, contiguous, with
+ *     natural alignment (4 bytes for float/int32); arguments that must be 16-byte
+ *     aligned say so.  Descriptor structs (tacsl_sdf_set, tacsl_contact_params,
+ *     tacsl_shading) are HOST memory read during the call; the device pointers
+ *     inside them are read by the kernels later, on the stream.
+ *   - Calls enqueue work on `stream` (NULL = the legacy default stream) and return
+ *     without synchronising.  They never allocate or free memory.
+ *   - Arguments are checked on the host before anything is launched; on failure the
+ *     call returns a nonzero status, launches nothing and writes no output, and
+ *     tacsl_last_error() describes the problem.
+ *   - A zero-sized batch (n, E, P, T or B equal to 0) returns TACSL_OK and launches
+ *     nothing.
+ *   - Values that only exist on the device (object ids, sensor ids) are checked by the
+ *     kernels: a bad one poisons the affected outputs as documented and sets a bit
+ *     in the device error word, read with tacsl_check_errors().
+ *
+ * Frames (shared with the inputs' producers):
+ *   object frame: the frame of the object's SDF grid;
+ *   pad frame: taxels lie on its z = 0 plane, +z is the pad's outward normal
+ *     pointing toward the object;
+ *   pad_pose[7] = (tx, ty, tz, qw, qx, qy, qz): x_obj = R(q) x_pad + t; q need not
+ *     be normalised (it is normalised in the kernel);
+ *   pad_twist[6] = (vx, vy, vz, wx, wy, wz): the pad's velocity relative to the
+ *     object, object frame, referenced at the object origin, so a pad point at
+ *     x_obj moves at v + w x x_obj.
+ */
+#ifndef TACSL_H
+#define TACSL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* tacsl_stream_t;
+
+/* Status codes. */
+#define TACSL_OK 0
+#define TACSL_ERR_INVALID_ARG 1 /* a host-checkable argument is wrong; nothing launched */
+#define TACSL_ERR_UNSUPPORTED 2 /* valid but beyond this build's limits; nothing launched */
+#define TACSL_ERR_CUDA 3        /* the CUDA runtime reported an error (launch or query) */
+#define TACSL_ERR_TIMEOUT 4     /* a bounded device wait gave up (see the error word) */
+
+/* Bits of the device error word. */
+#define TACSL_DEVERR_BAD_OBJ_ID 0x1u    /* an obj_id outside [0, n_sdf) was seen */
+#define TACSL_DEVERR_BAD_SENSOR_ID 0x2u /* a sensor_id outside [0, n_sensor) was seen */
+#define TACSL_DEVERR_TIMEOUT 0x4u       /* a kernel gave up on a bounded wait */
+
+/* Build limits. */
+#define TACSL_MAX_SDF 64      /* objects per call */
+#define TACSL_MAX_SENSOR 16   /* sensor models per call */
+#define TACSL_MAX_TAXELS 65536
+
+/* One object's signed-distance grid (Sec. III-C: "the SDF of the contacting object").
+ * Node (i, j, k) sits at origin + (i, j, k) * voxel; data is [n[2]][n[1]][n[0]],
+ * x fastest, negative inside the object.  n[k] >= 3; n0*n1*n2 < 2^31. */
+typedef struct {
+    int32_t n[3];
+    float origin[3];
+    float voxel;
+    const float* data; /* device */
+} tacsl_sdf;
+
+typedef struct {
+    const tacsl_sdf* sdfs; /* host array of n_sdf descriptors */
+    int32_t n_sdf;         /* 1 .. TACSL_MAX_SDF */
+} tacsl_sdf_set;
+
+/* Contact parameters of Sec. III-C: stiffness k_n, damping k_d, friction stiffness k_t
+ * and friction coefficient mu.  Each is a device array of `count` floats, count = 1
+ * (broadcast to every env) or count = E (one per env). */
+typedef struct {
+    const float* k_n;
+    const float* k_d;
+    const float* k_t;
+    const float* mu;
+    int32_t count;
+} tacsl_contact_params;
+
+/* Sensor shading model (Sec. III-B: I_rgb = F(I_depth) through a calibrated per-pixel
+ * table).  F is the per-pixel quadratic
+ *     I_c = sum_k A[s][k][c][y][x] m_k,   m = (1, n_x, n_y, n_x^2, n_y^2, n_x n_y),
+ * of the depth-map normal n; A[s][0] is the sensor's background image.
+ * coeffs: device, [n_sensor][6][3][H][W] float32, 16-byte aligned.
+ * W must be a multiple of 4; pitch_x, pitch_y are the pixel spacings in metres. */
+typedef struct {
+    int32_t H, W;
+    float pitch_x, pitch_y;
+    const float* coeffs;
+    int32_t n_sensor; /* 1 .. TACSL_MAX_SENSOR */
+} tacsl_shading;
+
+/* Thread-local description of the last failing call on this thread ("" if none). */
+const char* tacsl_last_error(void);
+
+/* ABI version of this header (increments on any signature change). */
+int32_t tacsl_abi_version(void);
+
+/* Reads the calling device's error word into *flags (TACSL_DEVERR_* bits) and, if
+ * `clear` is nonzero, resets it.  Synchronises `stream` first.  For tests/debugging. */
+int tacsl_check_errors(tacsl_stream_t stream, uint32_t* flags, int32_t clear);
+
+/*
+ * SDF query with gradient (Sec. III-C: d from "querying the SDF ... at the tactile
+ * points"; the gradient "calculated using finite differencing").
+ *   pts    [n][3] object-frame points;  obj_id [n] grid per point.
+ *   phi    [n]    trilinear interpolation of the grid at the point;
+ *   grad   [n][3] central difference of that interpolant with step voxel/2 per axis.
+ * A point is in the grid's domain iff every continuous index (x - origin)/voxel lies
+ * in [0.5, n-1.5]; outside it phi = +INFINITY and grad = 0.  A bad obj_id gives NaN
+ * phi and grad and sets TACSL_DEVERR_BAD_OBJ_ID.
+ */
+int tacsl_sdf_query(const tacsl_sdf_set* set, int64_t n, const float* pts,
+                    const int32_t* obj_id, float* phi, float* grad, tacsl_stream_t stream);
+
+/*
+ * Penalty force field (Sec. III-C) of E envs x P pads x T taxels.
+ *   taxels    [T][3]       rest taxel positions (pad frame), shared by all pads;
+ *   obj_id    [E]          SDF touched by env e (all its pads);
+ *   pad_pose  [E][P][7], pad_twist [E][P][6]   as in the frame conventions above.
+ * Per taxel, with x = R p + t, x' = v + w x x, (phi, g) the SDF query at x and
+ * n = g/|g|:
+ *   depth = max(-phi, 0);
+ *   if phi < 0 and |g| >= 1e-12:
+ *     d'  = n . x'                                  (chain rule)
+ *     f_n = max((-k_n + k_d d') phi, 0) n           (Sec. III-C law, clamped at 0, Eq. 3)
+ *     v_t = x' - d' n
+ *     f_t = -(v_t/|v_t|) min(k_t |v_t|, mu |f_n|)   (0 when |v_t| = 0)
+ *   else f_n = f_t = 0.
+ * Outputs (pad frame, R^T applied): depth [E][P][T], f_n [E][P][T][3],
+ * f_t [E][P][T][3]; wrench [E][P][6] = (sum f, sum p x f) with f = f_n + f_t about
+ * the pad origin, or NULL to skip it.  A bad obj_id fills that env's outputs with NaN
+ * and sets TACSL_DEVERR_BAD_OBJ_ID.
+ */
+int tacsl_penalty_forces(const tacsl_sdf_set* set, const tacsl_contact_params* params,
+                         int32_t E, int32_t P, int32_t T, const float* taxels,
+                         const int32_t* obj_id, const float* pad_pose, const float* pad_twist,
+                         float* depth, float* f_n, float* f_t, float* wrench,
+                         tacsl_stream_t stream);
+
+/*
+ * Net wrench per pad from given force fields.  The paper has no such formula; it
+ * feeds policies a per-finger net contact force (Sec. VI-B, privileged state) next to
+ * the force field, and this is that reduction of the field plus its moment about the
+ * pad origin.  f_n, f_t [B][T][3], taxels [T][3] ->
+ * wrench [B][6] = (sum_i f_i, sum_i p_i x f_i), f_i = f_n,i + f_t,i.
+ * Sums run in a fixed order: repeated calls give identical bits.
+ */
+int tacsl_pad_wrench(int64_t B, int32_t T, const float* taxels, const float* f_n,
+                     const float* f_t, float* wrench, tacsl_stream_t stream);
+
+/*
+ * Tactile RGB images from depth maps (Sec. III-B, I_rgb = F(I_depth)).
+ *   sensor_id [B]          shading model of image b;
+ *   depth_map [B][H][W]    camera-to-gel distance [m], 16-byte aligned;
+ *   rgb       [B][H][W][3] uint8, HWC.
+ * Per pixel: D_x, D_y by central differences inside and one-sided differences on the
+ * border (0 along an axis of length 1); n = (D_x, D_y, -1)/sqrt(1 + D_x^2 + D_y^2);
+ * I_c as in tacsl_shading; rgb_c = floor(clamp(I_c, 0, 255) + 0.5), NaN -> 0.
+ * An image whose sensor_id is outside [0, n_sensor) is left untouched and sets
+ * TACSL_DEVERR_BAD_SENSOR_ID.
+ */
+int tacsl_shade_image(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id,
+                      const float* depth_map, uint8_t* rgb, tacsl_stream_t stream);
+
+/*
+ * The whole tactile step in one launch: tacsl_penalty_forces on the E x P pads and
+ * tacsl_shade_image on their E*P depth maps (image b = e*P + p belongs to pad (e, p)).
+ * Arguments and results are exactly those of the two calls; shading may be NULL to
+ * skip the images (then sensor_id, depth_map and rgb are ignored).
+ */
+int tacsl_tactile_step(const tacsl_sdf_set* set, const tacsl_contact_params* params,
+                       int32_t E, int32_t P, int32_t T, const float* taxels,
+                       const int32_t* obj_id, const float* pad_pose, const float* pad_twist,
+                       float* depth, float* f_n, float* f_t, float* wrench,
+                       const tacsl_shading* shading, const int32_t* sensor_id,
+                       const float* depth_map, uint8_t* rgb, tacsl_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TACSL_H */

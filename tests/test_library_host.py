@@ -1,0 +1,203 @@
+"""CPU-only checks of the C-ABI library: it builds for sm_103a, loads, exports every
+function include/tacsl.h declares, and rejects bad host-visible arguments before
+touching the GPU (no CUDA call is reached on these paths)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_2408_06506_b300 as tacsl
+from paper_2408_06506_b300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+INVALID, UNSUPPORTED = 1, 2
+FAKE = 0x7F0000001000          # 16-byte aligned, never dereferenced on these paths
+FAKE_ODD = FAKE + 2
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return tacsl.load()
+
+
+def _declared_functions():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(tacsl_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for n in ("tacsl_sdf_query", "tacsl_penalty_forces", "tacsl_pad_wrench", "tacsl_shade_image",
+              "tacsl_tactile_step", "tacsl_last_error", "tacsl_check_errors"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in _declared_functions():
+        assert hasattr(lib, n), n
+
+
+def test_abi_version(lib):
+    assert lib.tacsl_abi_version() == 1
+
+
+def _sdf(n=(8, 8, 8), voxel=1e-3, data=FAKE):
+    s = tacsl._Sdf()
+    s.n[0], s.n[1], s.n[2] = n
+    for a in range(3):
+        s.origin[a] = 0.0
+    s.voxel = voxel
+    s.data = data
+    return s
+
+
+def _set(*sdfs):
+    arr = (tacsl._Sdf * len(sdfs))(*sdfs)
+    st = tacsl._SdfSet(C.cast(arr, C.POINTER(tacsl._Sdf)), len(sdfs))
+    st._keep = arr
+    return st
+
+
+def _params(count=1, k_n=FAKE):
+    return tacsl._Params(k_n, FAKE, FAKE, FAKE, count)
+
+
+def _forces(lib, st, prm, E=2, P=2, T=10, taxels=FAKE, ids=FAKE, pose=FAKE, twist=FAKE, depth=FAKE,
+            fn=FAKE, ft=FAKE, wrench=FAKE):
+    return lib.tacsl_penalty_forces(C.byref(st), C.byref(prm), E, P, T, taxels, ids, pose, twist, depth, fn, ft,
+                                    wrench, None)
+
+
+@pytest.mark.parametrize("case,code", [
+    ("null_set", INVALID), ("n_sdf_zero", INVALID), ("too_many_sdf", INVALID), ("null_grid", INVALID),
+    ("small_grid", INVALID), ("bad_voxel", INVALID), ("nan_voxel", INVALID), ("null_params", INVALID),
+    ("bad_count", INVALID), ("negative_E", INVALID), ("null_pose", INVALID), ("odd_pose", INVALID),
+    ("too_many_taxels", UNSUPPORTED), ("odd_wrench", INVALID), ("huge_grid", UNSUPPORTED),
+])
+def test_penalty_forces_rejects(lib, case, code):
+    st, prm, kw = _set(_sdf()), _params(), {}
+    if case == "null_set":
+        rc = lib.tacsl_penalty_forces(None, C.byref(prm), 2, 2, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE,
+                                      None)
+        assert rc == code and "sdf set" in lib.tacsl_last_error().decode()
+        return
+    if case == "n_sdf_zero":
+        st.n_sdf = 0
+    elif case == "too_many_sdf":
+        st = _set(*[_sdf() for _ in range(tacsl.MAX_SDF + 1)])
+    elif case == "null_grid":
+        st = _set(_sdf(), _sdf(data=0))
+    elif case == "small_grid":
+        st = _set(_sdf(n=(8, 2, 8)))
+    elif case == "bad_voxel":
+        st = _set(_sdf(voxel=-1.0))
+    elif case == "nan_voxel":
+        st = _set(_sdf(voxel=float("nan")))
+    elif case == "huge_grid":
+        st = _set(_sdf(n=(2048, 2048, 1024)))
+    elif case == "null_params":
+        rc = lib.tacsl_penalty_forces(C.byref(st), None, 2, 2, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE,
+                                      None)
+        assert rc == code
+        return
+    elif case == "bad_count":
+        prm = _params(count=3)
+    elif case == "negative_E":
+        kw["E"] = -1
+    elif case == "null_pose":
+        kw["pose"] = 0
+    elif case == "odd_pose":
+        kw["pose"] = FAKE_ODD
+    elif case == "too_many_taxels":
+        kw["T"] = 70000
+    elif case == "odd_wrench":
+        kw["wrench"] = FAKE_ODD
+    rc = _forces(lib, st, prm, **kw)
+    assert rc == code, lib.tacsl_last_error().decode()
+    assert lib.tacsl_last_error().decode() != ""
+
+
+def test_zero_sized_batches_are_noops(lib):
+    st, prm = _set(_sdf()), _params()
+    assert _forces(lib, st, prm, E=0) == 0
+    assert _forces(lib, st, prm, T=0, P=0) == 0
+    assert lib.tacsl_sdf_query(C.byref(st), 0, None, None, None, None, None) == 0
+    assert lib.tacsl_pad_wrench(0, 10, None, None, None, None, None) == 0
+    sh = tacsl._Shading(4, 8, 1e-4, 1e-4, FAKE, 1)
+    assert lib.tacsl_shade_image(C.byref(sh), 0, None, None, None, None) == 0
+
+
+def _shading(H=12, W=16, px=1e-4, py=1e-4, coeffs=FAKE, S=2):
+    return tacsl._Shading(H, W, px, py, coeffs, S)
+
+
+@pytest.mark.parametrize("case,code", [
+    ("w_not_mult4", INVALID), ("w_small", INVALID), ("h_zero", INVALID), ("pitch", INVALID),
+    ("sensors", INVALID), ("too_many_sensors", INVALID), ("coeff_align", INVALID), ("depth_align", INVALID),
+    ("null_rgb", INVALID), ("null_sid", INVALID), ("neg_B", INVALID), ("huge_image", UNSUPPORTED),
+])
+def test_shade_image_rejects(lib, case, code):
+    sh, B, sid, dep, rgb = _shading(), 4, FAKE, FAKE, FAKE
+    if case == "w_not_mult4":
+        sh = _shading(W=18)
+    elif case == "w_small":
+        sh = _shading(W=0)
+    elif case == "h_zero":
+        sh = _shading(H=0)
+    elif case == "pitch":
+        sh = _shading(px=0.0)
+    elif case == "sensors":
+        sh = _shading(S=0)
+    elif case == "too_many_sensors":
+        sh = _shading(S=17)
+    elif case == "coeff_align":
+        sh = _shading(coeffs=FAKE + 4)
+    elif case == "depth_align":
+        dep = FAKE + 4
+    elif case == "null_rgb":
+        rgb = 0
+    elif case == "null_sid":
+        sid = 0
+    elif case == "neg_B":
+        B = -1
+    elif case == "huge_image":
+        sh = _shading(H=1 << 15, W=1 << 14)
+    assert lib.tacsl_shade_image(C.byref(sh), B, sid, dep, rgb, None) == code
+    # the fused step applies the same image checks before any launch
+    st, prm = _set(_sdf()), _params()
+    if case != "neg_B":
+        rc = lib.tacsl_tactile_step(C.byref(st), C.byref(prm), 2, 2, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE,
+                                    FAKE, C.byref(sh), sid, dep, rgb, None)
+        assert rc == code
+
+
+def test_sdf_query_rejects(lib):
+    st = _set(_sdf())
+    assert lib.tacsl_sdf_query(C.byref(st), -1, FAKE, FAKE, FAKE, FAKE, None) == INVALID
+    assert lib.tacsl_sdf_query(C.byref(st), 5, FAKE, 0, FAKE, FAKE, None) == INVALID
+    assert lib.tacsl_sdf_query(C.byref(st), 5, FAKE_ODD, FAKE, FAKE, FAKE, None) == INVALID
+
+
+def test_pad_wrench_rejects(lib):
+    assert lib.tacsl_pad_wrench(-1, 3, FAKE, FAKE, FAKE, FAKE, None) == INVALID
+    assert lib.tacsl_pad_wrench(4, 3, FAKE, FAKE, FAKE, 0, None) == INVALID
+    assert lib.tacsl_pad_wrench(4, 3, 0, FAKE, FAKE, FAKE, None) == INVALID
+    assert lib.tacsl_pad_wrench(4, 70000, FAKE, FAKE, FAKE, FAKE, None) == UNSUPPORTED
+
+
+def test_check_errors_rejects_null(lib):
+    assert lib.tacsl_check_errors(None, None, 1) == INVALID
+
+
+def test_binding_refuses_cpu_tensors():
+    import torch
+    with pytest.raises(TypeError):
+        tacsl.sdf_query(None, torch.zeros(3, 3), torch.zeros(3, dtype=torch.int32))
