@@ -290,6 +290,35 @@ def run_ours(args, rank, world, local_rank, dist):
     images = world * E * P
     value = taxel_pts / (ms_step * 1e-3)
 
+    # ---- the step's two halves launched alone (explains the fused number) ----
+    def timed(fn, n):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    nb = max(10, min(200, args.steps // 5))
+    breakdown = {
+        "penalty_forces_ms": timed(lambda: tacsl.penalty_forces(
+            sdfs, params, taxels, obj_id, pose, twist, depth=outs["depth"], f_n=outs["f_n"], f_t=outs["f_t"],
+            wrench=outs["wrench"]), nb),
+        "shade_image_ms": timed(lambda: tacsl.shade_image(shading, sensor_id, depth_map, rgb=outs["rgb"]), nb),
+        "tactile_step_ms": ms_step,
+    }
+    # Worst case for the image kernel: every pixel's neighbourhood differs (depth maps plus
+    # 1 um Gaussian noise), so no warp can use the flat-gel shortcut.
+    dense = depth_map + 1e-6 * torch.randn_like(depth_map)
+    breakdown["shade_image_dense_ms"] = timed(lambda: tacsl.shade_image(shading, sensor_id, dense, rgb=outs["rgb"]), nb)
+    breakdown["tactile_step_dense_ms"] = timed(lambda: tacsl.tactile_step(
+        sdfs, params, taxels, obj_id, pose, twist, shading, sensor_id, dense, **outs), nb)
+    del dense
+
     # ---- end to end: pinned host inputs in, results back to pinned host, every step ----
     e2e = None
     if not args.no_e2e:
@@ -367,6 +396,7 @@ def run_ours(args, rank, world, local_rank, dist):
                      "traffic": traffic, "kernel": "tacsl::step_kernel", "algorithmic_bytes": alg,
                      "bytes": parts, "peak_source": f"{peak_src} hbm_gbs (copy)"},
         "clocks": clk.summary(),
+        "breakdown": breakdown,
         "gpu_launches": args.steps,
         "cpu_baseline": cpu,
         "e2e": e2e,

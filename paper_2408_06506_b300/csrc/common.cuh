@@ -96,19 +96,58 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// L2 eviction-priority policies for cache hints (streams leave L2 first; data re-read
+// across the step - SDF grids, shading coefficients - stay).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ float4 ldg_f4_hint(const float4* p, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ float ldg_f_hint(const float* p, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 // Bulk copy global -> shared::cta, completion counted on an mbarrier (bytes % 16 == 0,
-// both addresses 16-byte aligned).
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+// both addresses 16-byte aligned), with an L2 cache policy.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
+                                         uint64_t pol) {
     asm volatile(
-        "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
+        "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar), "l"(pol)
         : "memory");
 }
 
-// Bulk copy shared::cta -> global (bulk-group completion).
-__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+// Bulk copy shared::cta -> global (bulk-group completion), with an L2 cache policy.
+__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes, uint64_t pol) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
+                 "r"(src), "r"(bytes), "l"(pol)
                  : "memory");
+}
+
+// Named barrier over the first `nthreads` threads (id 1..15; id 0 is __syncthreads).
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
@@ -155,8 +194,18 @@ __device__ __forceinline__ void load_pose(const float* __restrict__ pose7, const
 // Fixed-order block reduction of 6 floats (warp xor-tree, then warps in order).
 // `scratch` holds NWARPS*6 floats.  Result valid in thread 0.
 // ---------------------------------------------------------------------------
+// bar_id = 0 synchronises the whole block; otherwise a named barrier over the first
+// NWARPS warps (lets the fused kernel reduce without its producer warp).
 template <int NWARPS>
-__device__ __forceinline__ void block_sum6(float (&a)[6], float* scratch) {
+__device__ __forceinline__ void group_sync(int bar_id) {
+    if (bar_id == 0)
+        __syncthreads();
+    else
+        named_barrier(bar_id, NWARPS * 32);
+}
+
+template <int NWARPS>
+__device__ __forceinline__ void block_sum6(float (&a)[6], float* scratch, int bar_id = 0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -167,7 +216,7 @@ __device__ __forceinline__ void block_sum6(float (&a)[6], float* scratch) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) scratch[warp * 6 + k] = a[k];
     }
-    __syncthreads();
+    group_sync<NWARPS>(bar_id);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) {

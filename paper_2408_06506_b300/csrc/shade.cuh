@@ -3,22 +3,29 @@
 // step that runs the force field (taxel.cuh) in the same persistent launch.
 //
 // Design (B300):
-// * The work is (sensor s, pixel tile, image) units.  A tile is 2048 consecutive
-//   pixels of the flattened H*W image, 4 per thread of a 512-thread CTA.  One CTA per
-//   SM runs persistently over a contiguous range of units ordered sensor-major,
-//   tile-next, image-last, so a CTA keeps one tile's 18 shading coefficients per pixel
-//   (72 floats per thread) in REGISTERS and streams many images through them.  The
-//   coefficients are read once per CTA per tile instead of once per image.
-// * Each unit's depth tile plus one row of halo above and below is a contiguous byte
-//   range; the 1-D bulk copy engine (cp.async.bulk) moves it into a ring of
-//   shared-memory stages, completion tracked by mbarriers, several images ahead.
+// * A tile is 1920 consecutive pixels of the flattened H*W image, 4 per compute
+//   thread.  A work item is (block of M images, sensor s, tile); one CTA per SM takes
+//   items round-robin and keeps the item's 18 shading coefficients per pixel (72
+//   floats per thread) in REGISTERS while it streams the block's images of sensor s
+//   through them, so coefficients are read once per item, not once per image.
+// * A producer warp streams each image's tile plus one halo row above and below (a
+//   contiguous byte range) into a ring of shared-memory stages with the bulk copy
+//   engine (cp.async.bulk), signalling full/empty mbarriers; the 15 compute warps
+//   never meet at a block-wide barrier.
 // * Normals use only shared memory: the thread's 4 pixels, their up/down rows and
 //   the two horizontal neighbours.  Borders use one-sided differences via
-//   per-thread offsets and scale factors chosen once per tile.
-// * Quantised RGB goes to a shared staging buffer (3 rotating) and leaves with one
-//   bulk store per tile (when the output allows 16-byte bulk copies).
-// * Images whose sensor differs from the unit's sensor are skipped by building, per
-//   run, the list of the sensor's images from sensor_id with block-wide ballots.
+//   per-thread offsets and scale factors chosen once per item.
+// * The producer also stages each item's coefficient rows into shared memory (a
+//   coefficient full/empty barrier pair), so switching items costs a shared-memory
+//   copy into registers, not an L2 round trip.
+// * Arithmetic runs on FP32 pairs (f32x2), quantisation uses two FP instructions and a
+//   saturating byte pack per value, horizontal neighbours come by warp shuffle.
+// * Sparsity of contact: a warp whose 128 pixels all have equal neighbours (the
+//   undeformed gel) writes the item's background bytes, which are exactly what the
+//   full evaluation gives for n = (0, 0, -1).
+// * Each warp transposes its 128 pixels' RGB (384 bytes) through a private staging
+//   buffer and writes them with 16-byte stores; L2 policies mark the depth and RGB
+//   streams evict-first and the coefficients evict-last.
 #pragma once
 
 #include "common.cuh"
@@ -26,37 +33,42 @@
 
 namespace tacsl {
 
-constexpr int kShThreads = 512;
-constexpr int kShWarps = kShThreads / 32;
-constexpr int kShTile = kShThreads * 4;   // pixels per tile
-constexpr int kShList = 1024;             // images per run
-constexpr int kShStaging = 3;             // RGB staging buffers
+constexpr int kShConsumerWarps = 15;                       // compute warps (+1 producer = 16)
+constexpr int kShConsumers = kShConsumerWarps * 32;        // 480 compute threads
+constexpr int kShThreads = kShConsumers + 32;              // + one producer warp
+constexpr int kShTile = kShConsumers * 4;                  // pixels per tile, 4 per thread
+constexpr int kShWarpPx = 128;                             // pixels per compute warp
+constexpr int kShWarpStaging = kShWarpPx * 3;              // RGB bytes per warp and tile
+constexpr int kShStagingRing = 2;                          // staging buffers per warp
 constexpr int kShMaxStages = 16;
+constexpr int kShCoefFloats = 18 * kShTile;                // one tile's shading coefficients
 
 // Shared-memory layout (bytes).
-constexpr int kOffBar = 0;                                             // kShMaxStages x u64
-constexpr int kOffList = kOffBar + kShMaxStages * 8;                   // kShList x i32
-constexpr int kOffCnt = kOffList + kShList * 4;                        // kShWarps x TACSL_MAX_SENSOR x i32
-constexpr int kOffWtot = kOffCnt + kShWarps * TACSL_MAX_SENSOR * 4;   // kShWarps x i32
-constexpr int kOffNs = kOffWtot + kShWarps * 4;                        // TACSL_MAX_SENSOR x i32
-constexpr int kOffFlag = kOffNs + TACSL_MAX_SENSOR * 4;                // i32
-constexpr int kOffRed = kOffFlag + 16;                                 // kShWarps x 6 f32
-constexpr int kOffStage = ((kOffRed + kShWarps * 6 * 4) + 127) / 128 * 128;
-constexpr int kStagingBytes = kShTile * 3;
+constexpr int kOffFull = 0;                                        // kShMaxStages x u64
+constexpr int kOffEmpty = kOffFull + kShMaxStages * 8;             // kShMaxStages x u64
+constexpr int kOffCoefFull = kOffEmpty + kShMaxStages * 8;         // u64
+constexpr int kOffCoefEmpty = kOffCoefFull + 8;                    // u64
+constexpr int kOffMeta = kOffCoefEmpty + 8;                        // kShMaxStages x int2 (image, item)
+constexpr int kOffRed = kOffMeta + kShMaxStages * 8;               // kShConsumerWarps x 6 f32
+constexpr int kOffStaging = ((kOffRed + kShConsumerWarps * 6 * 4) + 127) / 128 * 128;
+constexpr int kOffCoef = kOffStaging + kShConsumerWarps * kShStagingRing * kShWarpStaging;
+constexpr int kOffStage = kOffCoef + kShCoefFloats * 4;
 
 __host__ __device__ constexpr int shade_smem_bytes(int n_stages, int stage_floats) {
-    return kOffStage + n_stages * stage_floats * 4 + kShStaging * kStagingBytes;
+    return kOffStage + n_stages * stage_floats * 4;
 }
 
-enum StoreMode { kStoreBulk = 0, kStoreWord = 1, kStoreByte = 2 };
+enum StoreMode { kStoreVec = 0, kStoreWord = 1, kStoreByte = 2 };
 
 struct ShadeArgs {
-    const float* coeffs;        // [S][6][3][HW]
+    const float* coeffs;        // [S][6][3][HW], 16-byte aligned
     const int32_t* sensor_id;   // [B]
     const float* depth;         // [B][HW], 16-byte aligned
     uint8_t* rgb;               // [B][HW][3]
     int B;                      // images
     int H, W, S, HW, n_tiles;
+    int M;                      // images per block (work-item granularity)
+    int n_items;                // ceil(B / M) * S * n_tiles
     float cx_c, cx_e, cy_c, cy_e;   // 1/(2 pitch_x), 1/pitch_x, 1/(2 pitch_y), 1/pitch_y
     int n_stages, stage_floats;
     int store_mode;
@@ -75,243 +87,369 @@ struct TaxelArgs {                  // force-field half of the fused step
     float* wrench;
 };
 
-__device__ __forceinline__ uint32_t quantize_u8(float I) {
-    // floor(clamp(I, 0, 255) + 0.5); fmaxf drops NaN to 0
-    return __float2uint_rz(fminf(fmaxf(I, 0.f), 255.f) + 0.5f);
+// Work item k = (image block, sensor, tile), tile fastest: consecutive items - run at
+// the same time by consecutive CTAs - are the neighbouring tiles of the same images, so
+// the halo rows one CTA fetches are in L2 for its neighbours.
+struct Item {
+    int blk, s, tile;
+};
+__device__ __forceinline__ Item decode_item(const ShadeArgs& A, int k) {
+    const int per_blk = A.S * A.n_tiles;
+    Item it;
+    it.blk = k / per_blk;
+    const int r = k - it.blk * per_blk;
+    it.s = r / A.n_tiles;
+    it.tile = r - it.s * A.n_tiles;
+    return it;
+}
+
+// ---------------------------------------------------------------------------
+// Packed FP32 pairs (sm_100+ f32x2 instructions): lane-wise IEEE fp32, so results are
+// bit-identical to the scalar forms.
+// ---------------------------------------------------------------------------
+typedef uint64_t f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float lo(f2 r) { return __uint_as_float(static_cast<uint32_t>(r)); }
+__device__ __forceinline__ float hi(f2 r) { return __uint_as_float(static_cast<uint32_t>(r >> 32)); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Quantisation to floor(clamp(I, 0, 255) + 0.5).  The kernel evaluates the shading in
+// units of 1/256 with the 1/2 folded into the bias term, so t = (I + 0.5)/256; the
+// last FMA saturates t to [0, 1] (NaN -> 0).  Multiplying t by 2^-141 with round-down
+// then lands on the subnormal k * 2^-149 with k = floor(256 t), whose bit pattern is
+// the integer k in [0, 256]; the byte pack saturates 256 (I >= 255.5) to 255.
+// (Denormals are kept: this file is built without ftz.)
+__device__ __forceinline__ f2 floor256(float ta, float tb) {
+    f2 d;
+    asm("mul.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(ta, tb)), "l"(pk(__uint_as_float(0x100u), __uint_as_float(0x100u))));
+    return d;
+}
+
+// 1/sqrt(x) for x >= 1 (the flush-to-zero form differs only on subnormal inputs).
+__device__ __forceinline__ float rsqrt_ge1(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Bytes (b0, b1, b2, b3) in memory order from four integers, each saturated to [0, 255].
+__device__ __forceinline__ uint32_t pack_u8x4(uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3) {
+    uint32_t h, w;
+    asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, 0;" : "=r"(h) : "r"(b3), "r"(b2));
+    asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(w) : "r"(b1), "r"(b0), "r"(h));
+    return w;
+}
+
+__device__ __forceinline__ void stg_v4_hint(void* p, uint4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w), "l"(pol)
+                 : "memory");
+}
+
+// Producer warp: walks this CTA's items; for an item with at least one image of its
+// sensor it stages the tile's 18 coefficient rows into shared memory, then streams each
+// matching image's tile (+ one halo row above and below, a contiguous byte range) into
+// the stage ring with bulk copies, announcing (image, item) in meta[].
+__device__ __forceinline__ void shade_producer(const ShadeArgs& A, unsigned char* smem) {
+    const int lane = threadIdx.x & 31;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffFull);
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + kOffEmpty);
+    uint64_t* cfull = reinterpret_cast<uint64_t*>(smem + kOffCoefFull);
+    uint64_t* cempty = reinterpret_cast<uint64_t*>(smem + kOffCoefEmpty);
+    int2* meta = reinterpret_cast<int2*>(smem + kOffMeta);
+    float* coef = reinterpret_cast<float*>(smem + kOffCoef);
+    float* stages = reinterpret_cast<float*>(smem + kOffStage);
+    const int NS = A.n_stages;
+    const uint64_t pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
+    int st = 0;
+    uint32_t ph = 0, cph = 0;
+    bool ok = true;
+    for (int k = blockIdx.x; k < A.n_items && ok; k += gridDim.x) {
+        const Item it = decode_item(A, k);
+        const int b0 = it.blk * A.M, b1 = min(b0 + A.M, A.B);
+        const int tile_start = it.tile * kShTile;
+        const int tile_px = min(kShTile, A.HW - tile_start);
+        const int lo_px = max(tile_start - A.W, 0);
+        const uint32_t bytes = static_cast<uint32_t>(min(tile_start + tile_px + A.W, A.HW) - lo_px) * 4u;
+        // does the block hold an image of this sensor? (and flag bad ids once per block)
+        bool any = false;
+        for (int base = b0; base < b1; base += 32) {
+            const int b = base + lane;
+            const int sid = b < b1 ? __ldg(A.sensor_id + b) : -1;
+            if (it.s == 0 && it.tile == 0 && b < b1 && (sid < 0 || sid >= A.S))
+                raise_dev_error(TACSL_DEVERR_BAD_SENSOR_ID);
+            if (__any_sync(0xffffffffu, sid == it.s)) {
+                any = true;
+                if (!(it.s == 0 && it.tile == 0)) break;
+            }
+        }
+        if (!any) continue;
+        if (lane == 0) {
+            if (mbar_wait_bounded(smem_u32(cempty), cph ^ 1u)) {
+                const uint32_t row_bytes = static_cast<uint32_t>(tile_px) * 4u;
+                mbar_arrive_expect_tx(smem_u32(cfull), 18u * row_bytes);
+                const float* src = A.coeffs + static_cast<int64_t>(it.s) * 18 * A.HW + tile_start;
+                for (int r = 0; r < 18; ++r)
+                    bulk_g2s(smem_u32(coef + r * kShTile), src + static_cast<int64_t>(r) * A.HW, row_bytes,
+                             smem_u32(cfull), pol_keep);
+            } else {
+                raise_dev_error(TACSL_DEVERR_TIMEOUT);
+                ok = false;
+            }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        cph ^= 1u;
+        for (int base = b0; base < b1 && ok; base += 32) {
+            const int b = base + lane;
+            const int sid = b < b1 ? __ldg(A.sensor_id + b) : -1;
+            unsigned bal = __ballot_sync(0xffffffffu, sid == it.s);
+            while (bal != 0u && ok) {
+                const int j = __ffs(bal) - 1;
+                bal &= bal - 1u;
+                if (lane == 0) {
+                    if (mbar_wait_bounded(smem_u32(&empty[st]), ph ^ 1u)) {
+                        meta[st] = make_int2(base + j, k);
+                        mbar_arrive_expect_tx(smem_u32(&full[st]), bytes);
+                        bulk_g2s(smem_u32(stages + static_cast<int64_t>(st) * A.stage_floats),
+                                 A.depth + static_cast<int64_t>(base + j) * A.HW + lo_px, bytes, smem_u32(&full[st]),
+                                 pol_stream);
+                    } else {
+                        raise_dev_error(TACSL_DEVERR_TIMEOUT);
+                        ok = false;
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (++st == NS) { st = 0; ph ^= 1u; }
+            }
+        }
+    }
+    // end-of-stream marker: an arrival without bytes completes the stage's phase
+    if (lane == 0 && mbar_wait_bounded(smem_u32(&empty[st]), ph ^ 1u)) {
+        meta[st] = make_int2(-1, -1);
+        mbar_arrive(smem_u32(&full[st]));
+    }
 }
 
 template <bool kTaxels>
 __device__ __forceinline__ void shade_body(const ShadeArgs& A, const TaxelArgs& X, const SdfTable* tab,
                                            unsigned char* smem) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int G = gridDim.x, cta = blockIdx.x;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOffBar);
-    int* list = reinterpret_cast<int*>(smem + kOffList);
-    int* cnt = reinterpret_cast<int*>(smem + kOffCnt);
-    int* wtot = reinterpret_cast<int*>(smem + kOffWtot);
-    int* ns = reinterpret_cast<int*>(smem + kOffNs);
-    volatile int* flag = reinterpret_cast<volatile int*>(smem + kOffFlag);
-    float* red = reinterpret_cast<float*>(smem + kOffRed);
-    float* stages = reinterpret_cast<float*>(smem + kOffStage);
-    uint8_t* staging = smem + kOffStage + A.n_stages * A.stage_floats * 4;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffFull);
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + kOffEmpty);
+    uint64_t* cfull = reinterpret_cast<uint64_t*>(smem + kOffCoefFull);
+    uint64_t* cempty = reinterpret_cast<uint64_t*>(smem + kOffCoefEmpty);
+    const int2* meta = reinterpret_cast<const int2*>(smem + kOffMeta);
+    const float* coef = reinterpret_cast<const float*>(smem + kOffCoef);
+    const float* stages = reinterpret_cast<const float*>(smem + kOffStage);
     const int NS = A.n_stages;
 
     if (tid == 0) {
-        for (int s = 0; s < NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), kShConsumerWarps);
+        }
+        mbar_init(smem_u32(cfull), 1);
+        mbar_init(smem_u32(cempty), kShConsumerWarps);
         mbar_fence_init();
-        *flag = 0;
-    }
-    for (int i = tid; i < kShWarps * TACSL_MAX_SENSOR; i += kShThreads) cnt[i] = 0;
-    __syncthreads();
-
-    // ---- images per sensor (every CTA counts them; B int32 reads from L2) ----
-    for (int base = 0; base < A.B; base += kShThreads) {
-        const int b = base + tid;
-        const int sid = b < A.B ? __ldg(A.sensor_id + b) : 0;
-        const bool bad = b < A.B && (sid < 0 || sid >= A.S);
-        if (__any_sync(0xffffffffu, bad) && lane == 0 && cta == 0) raise_dev_error(TACSL_DEVERR_BAD_SENSOR_ID);
-        for (int s = 0; s < A.S; ++s) {
-            const unsigned m = __ballot_sync(0xffffffffu, b < A.B && sid == s);
-            if (lane == 0) cnt[warp * TACSL_MAX_SENSOR + s] += __popc(m);
-        }
     }
     __syncthreads();
-    if (tid < A.S) {
-        int t = 0;
-        for (int w = 0; w < kShWarps; ++w) t += cnt[w * TACSL_MAX_SENSOR + tid];
-        ns[tid] = t;
+
+    if (warp == kShConsumerWarps) {
+        shade_producer(A, smem);
+        return;
     }
-    __syncthreads();
-    int64_t n_valid = 0;
-    for (int s = 0; s < A.S; ++s) n_valid += ns[s];
-    const int64_t U = n_valid * A.n_tiles;
-    int64_t u = U * cta / G;
-    const int64_t u1 = U * (cta + 1) / G;
 
-    auto taxel_phase = [&]() {
-        if constexpr (kTaxels) {
-            const int64_t p0 = static_cast<int64_t>(X.B) * cta / G, p1 = static_cast<int64_t>(X.B) * (cta + 1) / G;
-            for (int64_t b = p0; b < p1; ++b)
-                process_pad<kShWarps>(*tab, X.prm, X.P, X.T, X.taxels, X.obj_id, X.pad_pose, X.pad_twist, X.depth,
-                                      X.f_n, X.f_t, X.wrench, b, red);
-        }
-    };
+    // ---- compute warps ----
+    if constexpr (kTaxels) {
+        // this CTA's share of the force field, while the producer fills the ring
+        // (one warp per pad; this CTA's pads [p0, p1) are dealt to its compute warps)
+        const int G = gridDim.x, cta = blockIdx.x;
+        const int64_t p0 = static_cast<int64_t>(X.B) * cta / G, p1 = static_cast<int64_t>(X.B) * (cta + 1) / G;
+        for (int64_t b = p0 + warp; b < p1; b += kShConsumerWarps)
+            pad_by_warp<1>(*tab, X.prm, X.P, X.T, X.taxels, X.obj_id, X.pad_pose, X.pad_twist, X.depth, X.f_n, X.f_t,
+                        X.wrench, b);
+    }
 
-    int64_t g = 0;   // items consumed by this CTA (drives stage index and barrier parity)
-    // current run: sensor, tile, length; tile geometry
-    int s = 0, tile = 0, run = 0;
-    int tile_start = 0, tile_px = 0, lo = 0, load_floats = 0;
-
-    // Decode unit u into (sensor, tile, rank), build the list of the run's images and
-    // issue the first loads of the run.
-    auto begin_run = [&]() {
-        s = 0;
-        int64_t cum = 0;
-        while (cum + static_cast<int64_t>(ns[s]) * A.n_tiles <= u) { cum += static_cast<int64_t>(ns[s]) * A.n_tiles; ++s; }
-        const int64_t local = u - cum;
-        tile = static_cast<int>(local / ns[s]);
-        const int j0 = static_cast<int>(local % ns[s]);
-        run = static_cast<int>(min(min(u1 - u, static_cast<int64_t>(ns[s] - j0)), static_cast<int64_t>(kShList)));
-        __syncthreads();   // previous run's readers of `list` are done
-        int rank_base = 0;
-        for (int base = 0; base < A.B && rank_base < j0 + run; base += kShThreads) {
-            const int b = base + tid;
-            const bool m = b < A.B && __ldg(A.sensor_id + b) == s;
-            const unsigned bal = __ballot_sync(0xffffffffu, m);
-            if (lane == 0) wtot[warp] = __popc(bal);
-            __syncthreads();
-            int woff = 0, total = 0;
-#pragma unroll
-            for (int w = 0; w < kShWarps; ++w) {
-                const int c = wtot[w];
-                woff += (w < warp) ? c : 0;
-                total += c;
-            }
-            const int r = rank_base + woff + __popc(bal & ((1u << lane) - 1u));
-            if (m && r >= j0 && r < j0 + run) list[r - j0] = b;
-            rank_base += total;
-            __syncthreads();
-        }
-        tile_start = tile * kShTile;
-        tile_px = min(kShTile, A.HW - tile_start);
-        lo = max(tile_start - A.W, 0);
-        load_floats = min(tile_start + tile_px + A.W, A.HW) - lo;
-        if (tid == 0) {
-            fence_proxy_async_smem();
-            const int npro = min(run, NS);
-            for (int i = 0; i < npro; ++i) {
-                const int64_t gi = g + i;
-                const int st = static_cast<int>(gi % NS);
-                const uint32_t bar = smem_u32(&bars[st]);
-                mbar_arrive_expect_tx(bar, load_floats * 4);
-                bulk_g2s(smem_u32(stages + static_cast<int64_t>(st) * A.stage_floats),
-                         A.depth + static_cast<int64_t>(list[i]) * A.HW + lo, load_floats * 4, bar);
-            }
-        }
-    };
-
-    // The first run's loads are in flight while the CTA computes its share of the
-    // force field; the coefficient registers are not live yet.
-    if (u < u1) begin_run();
-    taxel_phase();
-
-    float4 cf[6][3];
-    int cur_s = -1, cur_tile = -1;
+    const uint64_t pol_stream = policy_evict_first();
+    uint8_t* my_staging = smem + kOffStaging + warp * (kShStagingRing * kShWarpStaging);
+    f2 cf[6][3][2];                   // coefficients: term, channel, pixel pair
+    uint32_t bg0 = 0, bg1 = 0, bg2 = 0;   // RGB of a flat neighbourhood (n = (0, 0, -1))
+    int cur_item = -1, tile_start = 0, warp_px = 0;
     int oc = 0, ou = 0, od = 0, oL = 0, oR = 0;
-    float cxL = 0.f, cxR = 0.f, cyv = 0.f;
-    bool px_valid = false;
-    bool abort = false;
-
-    while (u < u1) {
-        if (s != cur_s || tile != cur_tile) {
-            cur_s = s;
-            cur_tile = tile;
+    f2 cxp0 = 0, cxp1 = 0, cyy = 0;
+    bool px_valid = false, hasL = false, hasR = false;
+    int st = 0, wbuf = 0;
+    uint32_t ph = 0, cph = 0;
+    const f2 one2 = pk(1.f, 1.f);
+    for (;;) {
+        if (!mbar_wait_bounded(smem_u32(&full[st]), ph)) {
+            if (lane == 0) raise_dev_error(TACSL_DEVERR_TIMEOUT);
+            break;
+        }
+        const int2 m = meta[st];
+        if (m.x < 0) break;
+        if (m.y != cur_item) {
+            // new item: geometry, then the tile's coefficients from shared memory
+            cur_item = m.y;
+            const Item it = decode_item(A, m.y);
+            tile_start = it.tile * kShTile;
+            const int tile_px = min(kShTile, A.HW - tile_start);
+            const int lo_px = max(tile_start - A.W, 0);
+            warp_px = min(max(tile_px - warp * kShWarpPx, 0), kShWarpPx);
+            px_valid = 4 * tid < tile_px;
             const int p = tile_start + 4 * tid;
-            px_valid = (4 * tid) < tile_px;
-            const int pp = px_valid ? p : tile_start;
-            const int y = pp / A.W, x0 = pp - y * A.W;
-            oc = pp - lo;
-            ou = ((y > 0) ? pp - A.W : pp) - lo;
-            od = ((y < A.H - 1) ? pp + A.W : pp) - lo;
-            oL = ((x0 > 0) ? pp - 1 : pp) - lo;
-            oR = ((x0 + 4 < A.W) ? pp + 4 : pp + 3) - lo;
-            cxL = (x0 > 0) ? A.cx_c : A.cx_e;
-            cxR = (x0 + 4 < A.W) ? A.cx_c : A.cx_e;
-            cyv = (y > 0 && y < A.H - 1) ? A.cy_c : A.cy_e;
-            const float4* cp = reinterpret_cast<const float4*>(A.coeffs + static_cast<int64_t>(s) * 18 * A.HW + pp);
+            if (px_valid) {
+                const int y = p / A.W, x0 = p - y * A.W;
+                hasL = x0 > 0;
+                hasR = x0 + 4 < A.W;
+                oc = p - lo_px;
+                ou = ((y > 0) ? p - A.W : p) - lo_px;
+                od = ((y < A.H - 1) ? p + A.W : p) - lo_px;
+                oL = (hasL ? p - 1 : p) - lo_px;
+                oR = (hasR ? p + 4 : p + 3) - lo_px;
+                const float cyv = (y > 0 && y < A.H - 1) ? A.cy_c : A.cy_e;
+                cxp0 = pk(hasL ? A.cx_c : A.cx_e, A.cx_c);
+                cxp1 = pk(A.cx_c, hasR ? A.cx_c : A.cx_e);
+                cyy = pk(cyv, cyv);
+            } else {
+                // past the tile's end: read in-bounds stage words (the lane's natural position,
+                // which its left neighbour uses as the pixel after the tile) and store nothing
+                oc = min(p - lo_px, A.stage_floats - 4);
+                ou = od = oL = oR = oc;
+                hasL = hasR = true;
+            }
+            if (!mbar_wait_bounded(smem_u32(cfull), cph)) {
+                if (lane == 0) raise_dev_error(TACSL_DEVERR_TIMEOUT);
+                break;
+            }
+            cph ^= 1u;
+            // coefficients in units of 1/256 with the rounding half folded into the bias:
+            // A0/256 + 1/512 and Ak/256 (exact power-of-two scaling)
+            const int q = px_valid ? 4 * tid : 0;
+            const f2 s256 = pk(0.00390625f, 0.00390625f), h512 = pk(0.001953125f, 0.001953125f);
 #pragma unroll
             for (int k = 0; k < 6; ++k)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) cf[k][c] = __ldg(cp + static_cast<int64_t>(k * 3 + c) * (A.HW / 4));
+                for (int c = 0; c < 3; ++c) {
+                    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(coef + (k * 3 + c) * kShTile + q);
+                    cf[k][c][0] = k == 0 ? fma2(v.x, s256, h512) : mul2(v.x, s256);
+                    cf[k][c][1] = k == 0 ? fma2(v.y, s256, h512) : mul2(v.y, s256);
+                }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(cempty));
+            // a flat neighbourhood has m = (1, 0, 0, 0, 0, 0): the chain below then returns
+            // its bias term exactly, so the bytes are those of the bias alone
+            f2 qb[3][2];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    qb[ch][j] = floor256(__saturatef(lo(cf[0][ch][j])), __saturatef(hi(cf[0][ch][j])));
+            bg0 = pack_u8x4(__float_as_uint(lo(qb[0][0])), __float_as_uint(lo(qb[1][0])),
+                            __float_as_uint(lo(qb[2][0])), __float_as_uint(hi(qb[0][0])));
+            bg1 = pack_u8x4(__float_as_uint(hi(qb[1][0])), __float_as_uint(hi(qb[2][0])),
+                            __float_as_uint(lo(qb[0][1])), __float_as_uint(lo(qb[1][1])));
+            bg2 = pack_u8x4(__float_as_uint(lo(qb[2][1])), __float_as_uint(hi(qb[0][1])),
+                            __float_as_uint(hi(qb[1][1])), __float_as_uint(hi(qb[2][1])));
         }
+        const float* sp = stages + static_cast<int64_t>(st) * A.stage_floats;
+        const float4 c = *reinterpret_cast<const float4*>(sp + oc);
+        const ulonglong2 up = *reinterpret_cast<const ulonglong2*>(sp + ou);
+        const ulonglong2 dn = *reinterpret_cast<const ulonglong2*>(sp + od);
+        float L = __shfl_up_sync(0xffffffffu, c.w, 1);
+        float R = __shfl_down_sync(0xffffffffu, c.x, 1);
+        if (lane == 0) L = sp[oL];
+        if (lane == 31) R = sp[oR];
+        L = hasL ? L : c.x;
+        R = hasR ? R : c.w;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&empty[st]));   // this warp is done with the stage
 
-        // ---- pipeline over the run's images ----
-        int i_abort = -1;
-        for (int i = 0; i < run; ++i) {
-            const int64_t gi = g + i;
-            const int st = static_cast<int>(gi % NS);
-            const uint32_t parity = static_cast<uint32_t>((gi / NS) & 1);
-            if (!mbar_wait_bounded(smem_u32(&bars[st]), parity)) *flag = 1;
-            const float* sp = stages + static_cast<int64_t>(st) * A.stage_floats;
-            uint32_t w0 = 0, w1 = 0, w2 = 0;
-            if (px_valid) {
-                const float4 c = *reinterpret_cast<const float4*>(sp + oc);
-                const float4 up = *reinterpret_cast<const float4*>(sp + ou);
-                const float4 dn = *reinterpret_cast<const float4*>(sp + od);
-                const float L = sp[oL], R = sp[oR];
-                const float gx[4] = {(c.y - L) * cxL, (c.z - c.x) * A.cx_c, (c.w - c.y) * A.cx_c, (R - c.z) * cxR};
-                const float gy[4] = {(dn.x - up.x) * cyv, (dn.y - up.y) * cyv, (dn.z - up.z) * cyv, (dn.w - up.w) * cyv};
-                uint32_t q[12];
+        // depth differences of the pixel pairs (0,1) and (2,3)
+        const float ex0 = c.y - L, ex1 = c.z - c.x, ex2 = c.w - c.y, ex3 = R - c.z;
+        const f2 ey0 = sub2(dn.x, up.x), ey1 = sub2(dn.y, up.y);
+        // Exactness shortcut: where all four pixels see equal neighbours, D_x = D_y = 0,
+        // n = (0, 0, -1) and the shading is the bias term; the warp takes it when all of
+        // its lanes can (bitwise the bytes of the full evaluation).
+        const bool flat = ((__float_as_uint(ex0) | __float_as_uint(ex1) | __float_as_uint(ex2) |
+                            __float_as_uint(ex3) | static_cast<uint32_t>(ey0) | static_cast<uint32_t>(ey0 >> 32) |
+                            static_cast<uint32_t>(ey1) | static_cast<uint32_t>(ey1 >> 32)) &
+                           0x7fffffffu) == 0u;
+        uint32_t w0 = bg0, w1 = bg1, w2 = bg2;
+        if (!__all_sync(0xffffffffu, flat || !px_valid)) {
+        const f2 gx0 = mul2(pk(ex0, ex1), cxp0);
+        const f2 gx1 = mul2(pk(ex2, ex3), cxp1);
+        const f2 gy0 = mul2(ey0, cyy);
+        const f2 gy1 = mul2(ey1, cyy);
+        f2 q[2][3];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float r = rsqrtf(fmaf(gx[k], gx[k], fmaf(gy[k], gy[k], 1.f)));
-                    const float nx = gx[k] * r, ny = gy[k] * r;
-                    const float m3 = nx * nx, m4 = ny * ny, m5 = nx * ny;
+        for (int j = 0; j < 2; ++j) {
+            const f2 gx = j ? gx1 : gx0, gy = j ? gy1 : gy0;
+            const f2 s2 = fma2(gx, gx, fma2(gy, gy, one2));
+            const f2 r = pk(rsqrt_ge1(lo(s2)), rsqrt_ge1(hi(s2)));
+            const f2 nx = mul2(gx, r), ny = mul2(gy, r);
+            const f2 m3 = mul2(nx, nx), m4 = mul2(ny, ny), m5 = mul2(nx, ny);
 #pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) {
-                        const float a0 = (&cf[0][ch].x)[k], a1 = (&cf[1][ch].x)[k], a2 = (&cf[2][ch].x)[k];
-                        const float a3 = (&cf[3][ch].x)[k], a4 = (&cf[4][ch].x)[k], a5 = (&cf[5][ch].x)[k];
-                        const float I = fmaf(a5, m5, fmaf(a4, m4, fmaf(a3, m3, fmaf(a2, ny, fmaf(a1, nx, a0)))));
-                        q[3 * k + ch] = quantize_u8(I);
-                    }
-                }
-                w0 = q[0] | (q[1] << 8) | (q[2] << 16) | (q[3] << 24);
-                w1 = q[4] | (q[5] << 8) | (q[6] << 16) | (q[7] << 24);
-                w2 = q[8] | (q[9] << 8) | (q[10] << 16) | (q[11] << 24);
-            }
-            const int64_t img = list[i];
-            if (A.store_mode == kStoreBulk) {
-                uint32_t* sg = reinterpret_cast<uint32_t*>(staging + static_cast<int>(gi % kShStaging) * kStagingBytes);
-                if (px_valid) { sg[3 * tid] = w0; sg[3 * tid + 1] = w1; sg[3 * tid + 2] = w2; }
-                fence_proxy_async_smem();
-            } else if (px_valid) {
-                uint8_t* dst = A.rgb + (img * A.HW + tile_start + 4 * tid) * 3;
-                if (A.store_mode == kStoreWord) {
-                    uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
-                    d32[0] = w0; d32[1] = w1; d32[2] = w2;
-                } else {
-                    const uint32_t ws[3] = {w0, w1, w2};
-#pragma unroll
-                    for (int k = 0; k < 12; ++k) dst[k] = static_cast<uint8_t>(ws[k >> 2] >> (8 * (k & 3)));
-                }
-            }
-            __syncthreads();   // stage consumed, staging written
-            if (*flag) { i_abort = i; break; }
-            if (tid == 0) {
-                if (A.store_mode == kStoreBulk) {
-                    bulk_s2g(A.rgb + (img * A.HW + tile_start) * 3,
-                             smem_u32(staging + static_cast<int>(gi % kShStaging) * kStagingBytes), tile_px * 3);
-                    bulk_commit();
-                }
-                if (i + NS < run) {
-                    fence_proxy_async_smem();
-                    const uint32_t bar = smem_u32(&bars[st]);
-                    mbar_arrive_expect_tx(bar, load_floats * 4);
-                    bulk_g2s(smem_u32(stages + static_cast<int64_t>(st) * A.stage_floats),
-                             A.depth + static_cast<int64_t>(list[i + NS]) * A.HW + lo, load_floats * 4, bar);
-                }
-                if (A.store_mode == kStoreBulk) bulk_wait_read<1>();
+            for (int ch = 0; ch < 3; ++ch) {
+                // t = (I + 0.5)/256: four packed FMAs, the last term per lane with saturation
+                const f2 part = fma2(cf[4][ch][j], m4, fma2(cf[3][ch][j], m3,
+                                                            fma2(cf[2][ch][j], ny, fma2(cf[1][ch][j], nx, cf[0][ch][j]))));
+                const float ta = __saturatef(fmaf(lo(cf[5][ch][j]), lo(m5), lo(part)));
+                const float tb = __saturatef(fmaf(hi(cf[5][ch][j]), hi(m5), hi(part)));
+                q[j][ch] = floor256(ta, tb);
             }
         }
-        if (i_abort >= 0) {
-            // Loads of items [i_abort, i_abort + NS) may still be landing: wait for them
-            // (bounded) before the CTA's shared memory goes away.
-            if (tid == 0) {
-                for (int i = i_abort; i < min(run, i_abort + NS); ++i) {
-                    const int64_t gi = g + i;
-                    mbar_wait_bounded(smem_u32(&bars[gi % NS]), static_cast<uint32_t>((gi / NS) & 1), 100000000ull);
-                }
-                raise_dev_error(TACSL_DEVERR_TIMEOUT);
-            }
-            abort = true;
-            break;
+        // q[j][ch] holds pixels (2j, 2j+1); memory order is px0 rgb, px1 rgb, px2 rgb, px3 rgb
+        w0 = pack_u8x4(__float_as_uint(lo(q[0][0])), __float_as_uint(lo(q[0][1])), __float_as_uint(lo(q[0][2])),
+                       __float_as_uint(hi(q[0][0])));
+        w1 = pack_u8x4(__float_as_uint(hi(q[0][1])), __float_as_uint(hi(q[0][2])), __float_as_uint(lo(q[1][0])),
+                       __float_as_uint(lo(q[1][1])));
+        w2 = pack_u8x4(__float_as_uint(lo(q[1][2])), __float_as_uint(hi(q[1][0])), __float_as_uint(hi(q[1][1])),
+                       __float_as_uint(hi(q[1][2])));
         }
-        g += run;
-        u += run;
-        if (u < u1) begin_run();
+        const int64_t img = m.x;
+        if (A.store_mode == kStoreVec) {
+            // warp-local transpose through shared memory, then 16-byte stores
+            uint32_t* sg = reinterpret_cast<uint32_t*>(my_staging + wbuf * kShWarpStaging);
+            sg[3 * lane] = w0;
+            sg[3 * lane + 1] = w1;
+            sg[3 * lane + 2] = w2;
+            __syncwarp();
+            if (lane * 16 < warp_px * 3)
+                stg_v4_hint(A.rgb + (img * A.HW + tile_start + warp * kShWarpPx) * 3 + 16 * lane,
+                            reinterpret_cast<const uint4*>(sg)[lane], pol_stream);
+            wbuf ^= 1;
+        } else if (px_valid) {
+            uint8_t* dst = A.rgb + (img * A.HW + tile_start + 4 * tid) * 3;
+            if (A.store_mode == kStoreWord) {
+                uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
+                d32[0] = w0; d32[1] = w1; d32[2] = w2;
+            } else {
+                const uint32_t ws[3] = {w0, w1, w2};
+#pragma unroll
+                for (int k = 0; k < 12; ++k) dst[k] = static_cast<uint8_t>(ws[k >> 2] >> (8 * (k & 3)));
+            }
+        }
+        if (++st == NS) { st = 0; ph ^= 1u; }
     }
-    (void)abort;
-    if (tid == 0 && A.store_mode == kStoreBulk) bulk_wait_all();
 }
 
 __global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A) {

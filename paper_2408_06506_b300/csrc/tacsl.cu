@@ -180,19 +180,28 @@ int plan_shade(const tacsl_shading* sh, int64_t B, const int32_t* sensor_id, con
     const int fixed = shade_smem_bytes(0, a.stage_floats);
     const int per_stage = a.stage_floats * 4;
     int ns = (dev.max_smem_optin - fixed) / per_stage;
-    if (ns > 8) ns = 8;
+    if (ns > 12) ns = 12;
     if (ns < 2)
         return fail(TACSL_ERR_UNSUPPORTED, "image width %d too large for the shared-memory pipeline", a.W);
     a.n_stages = ns;
     if (aligned(rgb, 16) && a.HW % 16 == 0)
-        a.store_mode = kStoreBulk;
+        a.store_mode = kStoreVec;
     else if (aligned(rgb, 4))
         a.store_mode = kStoreWord;
     else
         a.store_mode = kStoreByte;
+    // Images per work item: the largest power of two in [32, 1024] that still leaves
+    // at least 24 items per CTA (a short tail), so coefficient reloads are amortised
+    // over as many images as the load balance allows.
+    const int64_t per_blk = (int64_t)a.S * a.n_tiles;
+    int M = 1024;
+    while (M > 32 && ((B + M - 1) / M) * per_blk < 24LL * dev.sms) M /= 2;
+    const int64_t n_items = ((B + M - 1) / M) * per_blk;
+    if (n_items >= (int64_t(1) << 31)) return fail(TACSL_ERR_UNSUPPORTED, "too many work items");
+    a.M = M;
+    a.n_items = static_cast<int>(n_items);
     plan.smem = shade_smem_bytes(ns, a.stage_floats);
-    const int64_t units = B * a.n_tiles;
-    plan.grid = static_cast<int>(units < dev.sms ? (units > 0 ? units : 1) : dev.sms);
+    plan.grid = static_cast<int>(n_items < dev.sms ? (n_items > 0 ? n_items : 1) : dev.sms);
     return TACSL_OK;
 }
 
@@ -258,12 +267,12 @@ int tacsl_penalty_forces(const tacsl_sdf_set* set, const tacsl_contact_params* p
     if ((rc = check_forces_args(E, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t))) return rc;
     if (wrench != nullptr && !aligned(wrench, 4)) return fail(TACSL_ERR_INVALID_ARG, "wrench not 4-byte aligned");
     const int64_t B = (int64_t)E * P;
-    if (pad_block_warps(T) == 4)
-        penalty_kernel<4><<<static_cast<unsigned>(B), 128, 0, stream>>>(tab, prm, B, P, T, taxels, obj_id, pad_pose,
-                                                                         pad_twist, depth, f_n, f_t, wrench);
-    else
-        penalty_kernel<8><<<static_cast<unsigned>(B), 256, 0, stream>>>(tab, prm, B, P, T, taxels, obj_id, pad_pose,
-                                                                         pad_twist, depth, f_n, f_t, wrench);
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    const int64_t blocks = (B + 7) / 8;
+    const int grid = static_cast<int>(blocks < (int64_t)dev->sms * 32 ? blocks : (int64_t)dev->sms * 32);
+    penalty_kernel<<<grid, 256, 0, stream>>>(tab, prm, B, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t,
+                                             wrench);
     return check_launch("tacsl_penalty_forces");
 }
 

@@ -7,6 +7,16 @@
 // a 3x3x3 node window, so one query gathers 27 nodes (nine rows of three along x)
 // and folds them axis by axis with per-axis weight vectors: centre weights c[3] and
 // difference weights d[3] = w(u + 1/2) - w(u - 1/2).
+//
+// Sparsity: a taxel contributes only where it penetrates (phi < 0).  phi is first read
+// from the 8 nodes of its cell (bitwise the value of the full fold); the other 19 nodes
+// and the gradient are gathered only for penetrating taxels.
+//
+// Work split: ONE WARP PER PAD.  Lanes take taxels lane, lane+32, ..., NP at a time so
+// that NP 27-node gathers are in flight per lane, and the warp folds the pad's wrench
+// with shuffles - no block-wide barrier, so many pads progress at once and the gathers'
+// latency overlaps.  SDF reads carry an L2 evict-last policy (the grids are re-read
+// every step).
 #pragma once
 
 #include "common.cuh"
@@ -35,74 +45,112 @@ __device__ __forceinline__ void axis_weights(float u, int n, int& b, float c[3],
     for (int k = 0; k < 3; ++k) d[k] = wp[k] - wm[k];
 }
 
-// SDF value and gradient at object-frame point (x, y, z).  Returns false outside the
-// grid's domain (then phi = +inf, g = 0).
-__device__ __forceinline__ bool sdf_stencil(const DevSdf& S, float x, float y, float z, float& phi,
-                                            float g[3]) {
-    const float ux = (x - S.ox) * S.inv_h, uy = (y - S.oy) * S.inv_h, uz = (z - S.oz) * S.inv_h;
-    const bool inside = ux >= 0.5f && ux <= static_cast<float>(S.n0) - 1.5f && uy >= 0.5f &&
-                        uy <= static_cast<float>(S.n1) - 1.5f && uz >= 0.5f &&
-                        uz <= static_cast<float>(S.n2) - 1.5f;
-    if (!inside) {
-        phi = __int_as_float(0x7f800000);
-        g[0] = g[1] = g[2] = 0.f;
-        return false;
-    }
-    int bx, by, bz;
+// Node window of one query: base pointer and per-axis weights (centre c, difference d).
+struct Stencil {
+    const float* base;
     float cx[3], dx[3], cy[3], dy[3], cz[3], dz[3];
-    axis_weights(ux, S.n0, bx, cx, dx);
-    axis_weights(uy, S.n1, by, cy, dy);
-    axis_weights(uz, S.n2, bz, cz, dz);
-    const int n0 = S.n0, n01 = S.n0 * S.n1;
-    const float* __restrict__ base = S.data + (static_cast<int64_t>(bz) * n01 + static_cast<int64_t>(by) * n0 + bx);
-    float v[3][3][3];
+    bool inside;
+};
+
+__device__ __forceinline__ Stencil stencil_setup(const DevSdf& S, float x, float y, float z) {
+    Stencil q;
+    const float ux = (x - S.ox) * S.inv_h, uy = (y - S.oy) * S.inv_h, uz = (z - S.oz) * S.inv_h;
+    q.inside = ux >= 0.5f && ux <= static_cast<float>(S.n0) - 1.5f && uy >= 0.5f &&
+               uy <= static_cast<float>(S.n1) - 1.5f && uz >= 0.5f && uz <= static_cast<float>(S.n2) - 1.5f;
+    int bx = 0, by = 0, bz = 0;
+    if (q.inside) {
+        axis_weights(ux, S.n0, bx, q.cx, q.dx);
+        axis_weights(uy, S.n1, by, q.cy, q.dy);
+        axis_weights(uz, S.n2, bz, q.cz, q.dz);
+    }
+    q.base = S.data + (static_cast<int64_t>(bz) * S.n0 * S.n1 + static_cast<int64_t>(by) * S.n0 + bx);
+    return q;
+}
+
+__device__ __forceinline__ void stencil_load(const Stencil& q, int n0, int n01, uint64_t pol, float (&v)[3][3][3]) {
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) v[k][j][i] = __ldg(base + k * n01 + j * n0 + i);
-    // fold x: rows -> centre value and x-difference per (k, j)
+            for (int i = 0; i < 3; ++i) v[k][j][i] = ldg_f_hint(q.base + k * n01 + j * n0 + i, pol);
+}
+
+// Fold the gathered window: phi and the h/2 central differences along x, y, z.
+__device__ __forceinline__ void stencil_fold(const Stencil& q, const float (&v)[3][3][3], float inv_h, float& phi,
+                                             float g[3]) {
     float rc[3][3], rd[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            rc[k][j] = fmaf(cx[2], v[k][j][2], fmaf(cx[1], v[k][j][1], cx[0] * v[k][j][0]));
-            rd[k][j] = fmaf(dx[2], v[k][j][2], fmaf(dx[1], v[k][j][1], dx[0] * v[k][j][0]));
+            rc[k][j] = fmaf(q.cx[2], v[k][j][2], fmaf(q.cx[1], v[k][j][1], q.cx[0] * v[k][j][0]));
+            rd[k][j] = fmaf(q.dx[2], v[k][j][2], fmaf(q.dx[1], v[k][j][1], q.dx[0] * v[k][j][0]));
         }
-    // fold y
     float cc[3], cd[3], xd[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        cc[k] = fmaf(cy[2], rc[k][2], fmaf(cy[1], rc[k][1], cy[0] * rc[k][0]));
-        cd[k] = fmaf(dy[2], rc[k][2], fmaf(dy[1], rc[k][1], dy[0] * rc[k][0]));
-        xd[k] = fmaf(cy[2], rd[k][2], fmaf(cy[1], rd[k][1], cy[0] * rd[k][0]));
+        cc[k] = fmaf(q.cy[2], rc[k][2], fmaf(q.cy[1], rc[k][1], q.cy[0] * rc[k][0]));
+        cd[k] = fmaf(q.dy[2], rc[k][2], fmaf(q.dy[1], rc[k][1], q.dy[0] * rc[k][0]));
+        xd[k] = fmaf(q.cy[2], rd[k][2], fmaf(q.cy[1], rd[k][1], q.cy[0] * rd[k][0]));
     }
-    // fold z
-    phi = fmaf(cz[2], cc[2], fmaf(cz[1], cc[1], cz[0] * cc[0]));
-    g[0] = fmaf(cz[2], xd[2], fmaf(cz[1], xd[1], cz[0] * xd[0])) * S.inv_h;
-    g[1] = fmaf(cz[2], cd[2], fmaf(cz[1], cd[1], cz[0] * cd[0])) * S.inv_h;
-    g[2] = fmaf(dz[2], cc[2], fmaf(dz[1], cc[1], dz[0] * cc[0])) * S.inv_h;
+    phi = fmaf(q.cz[2], cc[2], fmaf(q.cz[1], cc[1], q.cz[0] * cc[0]));
+    g[0] = fmaf(q.cz[2], xd[2], fmaf(q.cz[1], xd[1], q.cz[0] * xd[0])) * inv_h;
+    g[1] = fmaf(q.cz[2], cd[2], fmaf(q.cz[1], cd[1], q.cz[0] * cd[0])) * inv_h;
+    g[2] = fmaf(q.dz[2], cc[2], fmaf(q.dz[1], cc[1], q.dz[0] * cc[0])) * inv_h;
+}
+
+// phi alone from the 8 nodes of the trilinear cell (the nonzero centre weights), with
+// the FMA order of stencil_fold, so the result is bitwise the phi of the full fold:
+// there each zero-weight term enters as fma(0, v, acc) = acc or as 0 * v + ..., which
+// leaves the sum unchanged.
+__device__ __forceinline__ float stencil_phi8(const Stencil& q, int n0, int n01, uint64_t pol) {
+    // offset of the lower node of each axis' centre cell inside the 3-node window
+    const int ox = q.cx[0] != 0.f || q.cx[2] == 0.f ? 0 : 1;
+    const int oy = q.cy[0] != 0.f || q.cy[2] == 0.f ? 0 : 1;
+    const int oz = q.cz[0] != 0.f || q.cz[2] == 0.f ? 0 : 1;
+    const float wx0 = ox ? q.cx[1] : q.cx[0], wx1 = ox ? q.cx[2] : q.cx[1];
+    const float wy0 = oy ? q.cy[1] : q.cy[0], wy1 = oy ? q.cy[2] : q.cy[1];
+    const float wz0 = oz ? q.cz[1] : q.cz[0], wz1 = oz ? q.cz[2] : q.cz[1];
+    const float* b = q.base + oz * n01 + oy * n0 + ox;
+    float v[2][2][2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) v[k][j][i] = ldg_f_hint(b + k * n01 + j * n0 + i, pol);
+    float c[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float r0 = fmaf(wx1, v[k][0][1], wx0 * v[k][0][0]);
+        const float r1 = fmaf(wx1, v[k][1][1], wx0 * v[k][1][0]);
+        c[k] = fmaf(wy1, r1, wy0 * r0);
+    }
+    return fmaf(wz1, c[1], wz0 * c[0]);
+}
+
+// SDF value and gradient at object-frame point (x, y, z).  Returns false outside the
+// grid's domain (then phi = +inf, g = 0).
+__device__ __forceinline__ bool sdf_stencil(const DevSdf& S, float x, float y, float z, float& phi, float g[3]) {
+    const Stencil q = stencil_setup(S, x, y, z);
+    if (!q.inside) {
+        phi = __int_as_float(0x7f800000);
+        g[0] = g[1] = g[2] = 0.f;
+        return false;
+    }
+    float v[3][3][3];
+    stencil_load(q, S.n0, S.n0 * S.n1, policy_evict_last(), v);
+    stencil_fold(q, v, S.inv_h, phi, g);
     return true;
 }
 
-// One taxel: pose, query, penalty normal force, friction-capped shear (object frame),
-// then both forces rotated into the pad frame.
-__device__ __forceinline__ void taxel_force(const DevSdf& S, const Pose& P, float px, float py, float pz,
-                                            float kn, float kd, float kt, float mu, float& depth,
-                                            float fn_pad[3], float ft_pad[3]) {
-    const float* r = P.r;
-    const float xo = fmaf(r[0], px, fmaf(r[1], py, fmaf(r[2], pz, P.t[0])));
-    const float yo = fmaf(r[3], px, fmaf(r[4], py, fmaf(r[5], pz, P.t[1])));
-    const float zo = fmaf(r[6], px, fmaf(r[7], py, fmaf(r[8], pz, P.t[2])));
-    // relative velocity of the point: v + w x x
-    const float vx = P.v[0] + (P.w[1] * zo - P.w[2] * yo);
-    const float vy = P.v[1] + (P.w[2] * xo - P.w[0] * zo);
-    const float vz = P.v[2] + (P.w[0] * yo - P.w[1] * xo);
-
-    float phi, g[3];
-    sdf_stencil(S, xo, yo, zo, phi, g);
+// Penalty normal force and friction-capped shear from the SDF sample (phi, g) at a
+// point moving at (vx, vy, vz) relative to the object; both forces returned in the pad
+// frame (R^T applied, r = row-major pad->object rotation).
+__device__ __forceinline__ void contact_force(const float* r, float phi, const float g[3], float vx, float vy,
+                                              float vz, float kn, float kd, float kt, float mu, float& depth,
+                                              float fn_pad[3], float ft_pad[3]) {
     float fn[3] = {0.f, 0.f, 0.f}, ft[3] = {0.f, 0.f, 0.f};
     depth = 0.f;
     if (phi < 0.f) {
@@ -124,7 +172,6 @@ __device__ __forceinline__ void taxel_force(const DevSdf& S, const Pose& P, floa
             }
         }
     }
-    // pad frame: R^T f
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         fn_pad[a] = fmaf(r[a], fn[0], fmaf(r[3 + a], fn[1], r[6 + a] * fn[2]));
@@ -132,28 +179,27 @@ __device__ __forceinline__ void taxel_force(const DevSdf& S, const Pose& P, floa
     }
 }
 
-// All taxels of pad b by the whole block (NWARPS warps), plus its wrench.
-template <int NWARPS>
-__device__ __forceinline__ void process_pad(const SdfTable& tab, const Params4& prm, int P, int T,
+// All taxels of pad b by ONE warp (see the file comment); NP taxels per lane in flight.
+template <int NP>
+__device__ __forceinline__ void pad_by_warp(const SdfTable& tab, const Params4& prm, int P, int T,
                                             const float* __restrict__ taxels, const int32_t* __restrict__ obj_id,
                                             const float* __restrict__ pad_pose, const float* __restrict__ pad_twist,
                                             float* __restrict__ depth, float* __restrict__ f_n,
-                                            float* __restrict__ f_t, float* __restrict__ wrench, int64_t b,
-                                            float* red_scratch) {
-    constexpr int NT = NWARPS * 32;
+                                            float* __restrict__ f_t, float* __restrict__ wrench, int64_t b) {
+    const int lane = threadIdx.x & 31;
     const int64_t e = b / P;
     const int id = __ldg(obj_id + e);
     const int64_t o = b * T;
     if (id < 0 || id >= tab.count) {
         const float qnan = __int_as_float(0x7fc00000);
-        for (int t = threadIdx.x; t < T; t += NT) {
+        for (int t = lane; t < T; t += 32) {
             depth[o + t] = qnan;
 #pragma unroll
             for (int a = 0; a < 3; ++a) { f_n[(o + t) * 3 + a] = qnan; f_t[(o + t) * 3 + a] = qnan; }
         }
-        if (wrench != nullptr && threadIdx.x < 6) wrench[b * 6 + threadIdx.x] = qnan;
-        if (threadIdx.x == 0) raise_dev_error(TACSL_DEVERR_BAD_OBJ_ID);
-        return;   // uniform across the block
+        if (wrench != nullptr && lane < 6) wrench[b * 6 + lane] = qnan;
+        if (lane == 0) raise_dev_error(TACSL_DEVERR_BAD_OBJ_ID);
+        return;
     }
     const DevSdf& S = tab.s[id];
     Pose Pz;
@@ -161,27 +207,72 @@ __device__ __forceinline__ void process_pad(const SdfTable& tab, const Params4& 
     const int pi = prm.count == 1 ? 0 : static_cast<int>(e);
     const float kn = __ldg(prm.k_n + pi), kd = __ldg(prm.k_d + pi), kt = __ldg(prm.k_t + pi),
                 mu = __ldg(prm.mu + pi);
+    const uint64_t pol = policy_evict_last();
+    const int n0 = S.n0, n01 = S.n0 * S.n1;
+    const float* r = Pz.r;
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int t = threadIdx.x; t < T; t += NT) {
-        const float px = __ldg(taxels + 3 * t), py = __ldg(taxels + 3 * t + 1), pz = __ldg(taxels + 3 * t + 2);
-        float dep, fn[3], ft[3];
-        taxel_force(S, Pz, px, py, pz, kn, kd, kt, mu, dep, fn, ft);
-        depth[o + t] = dep;
+    for (int t0 = lane; t0 < T; t0 += 32 * NP) {
+        float p[NP][3], vel[NP][3];
+        Stencil q[NP];
+        bool on[NP];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) { f_n[(o + t) * 3 + a] = fn[a]; f_t[(o + t) * 3 + a] = ft[a]; }
-        const float fx = fn[0] + ft[0], fy = fn[1] + ft[1], fz = fn[2] + ft[2];
-        acc[0] += fx; acc[1] += fy; acc[2] += fz;
-        acc[3] += py * fz - pz * fy;
-        acc[4] += pz * fx - px * fz;
-        acc[5] += px * fy - py * fx;
+        for (int u = 0; u < NP; ++u) {
+            const int t = t0 + 32 * u;
+            on[u] = t < T;
+            const int tt = on[u] ? t : t0;
+            p[u][0] = __ldg(taxels + 3 * tt);
+            p[u][1] = __ldg(taxels + 3 * tt + 1);
+            p[u][2] = __ldg(taxels + 3 * tt + 2);
+            const float xo = fmaf(r[0], p[u][0], fmaf(r[1], p[u][1], fmaf(r[2], p[u][2], Pz.t[0])));
+            const float yo = fmaf(r[3], p[u][0], fmaf(r[4], p[u][1], fmaf(r[5], p[u][2], Pz.t[1])));
+            const float zo = fmaf(r[6], p[u][0], fmaf(r[7], p[u][1], fmaf(r[8], p[u][2], Pz.t[2])));
+            // relative velocity of the point: v + w x x
+            vel[u][0] = Pz.v[0] + (Pz.w[1] * zo - Pz.w[2] * yo);
+            vel[u][1] = Pz.v[1] + (Pz.w[2] * xo - Pz.w[0] * zo);
+            vel[u][2] = Pz.v[2] + (Pz.w[0] * yo - Pz.w[1] * xo);
+            q[u] = stencil_setup(S, xo, yo, zo);
+            q[u].inside = q[u].inside && on[u];
+        }
+        // phi from the 8-node cell first; the 27-node window (and the gradient) only
+        // where the point penetrates - elsewhere the outputs are exact zeros either way
+        float phi8[NP];
+#pragma unroll
+        for (int u = 0; u < NP; ++u)
+            phi8[u] = q[u].inside ? stencil_phi8(q[u], n0, n01, pol) : __int_as_float(0x7f800000);
+        float v[NP][3][3][3];
+#pragma unroll
+        for (int u = 0; u < NP; ++u)
+            if (phi8[u] < 0.f) stencil_load(q[u], n0, n01, pol, v[u]);
+#pragma unroll
+        for (int u = 0; u < NP; ++u) {
+            if (!on[u]) continue;
+            const int t = t0 + 32 * u;
+            float phi = phi8[u], g[3] = {0.f, 0.f, 0.f};
+            if (phi8[u] < 0.f) stencil_fold(q[u], v[u], S.inv_h, phi, g);
+            float dep, fn[3], ft[3];
+            contact_force(r, phi, g, vel[u][0], vel[u][1], vel[u][2], kn, kd, kt, mu, dep, fn, ft);
+            depth[o + t] = dep;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) { f_n[(o + t) * 3 + a] = fn[a]; f_t[(o + t) * 3 + a] = ft[a]; }
+            const float fx = fn[0] + ft[0], fy = fn[1] + ft[1], fz = fn[2] + ft[2];
+            acc[0] += fx; acc[1] += fy; acc[2] += fz;
+            acc[3] += p[u][1] * fz - p[u][2] * fy;
+            acc[4] += p[u][2] * fx - p[u][0] * fz;
+            acc[5] += p[u][0] * fy - p[u][1] * fx;
+        }
     }
     if (wrench != nullptr) {
-        block_sum6<NWARPS>(acc, red_scratch);
-        if (threadIdx.x == 0) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) wrench[b * 6 + k] = acc[k];
+        for (int k = 0; k < 6; ++k) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
         }
-        __syncthreads();   // scratch reuse by the next pad
+        if (lane < 6) {
+            float w = acc[0];
+#pragma unroll
+            for (int k = 1; k < 6; ++k) w = (lane == k) ? acc[k] : w;
+            wrench[b * 6 + lane] = w;
+        }
     }
 }
 
@@ -209,19 +300,20 @@ __global__ void __launch_bounds__(256) sdf_query_kernel(const SdfTable tab, int6
     }
 }
 
-template <int NWARPS>
-__global__ void __launch_bounds__(NWARPS * 32) penalty_kernel(const SdfTable tab, const Params4 prm, int64_t B, int P,
-                                                              int T, const float* __restrict__ taxels,
-                                                              const int32_t* __restrict__ obj_id,
-                                                              const float* __restrict__ pad_pose,
-                                                              const float* __restrict__ pad_twist,
-                                                              float* __restrict__ depth, float* __restrict__ f_n,
-                                                              float* __restrict__ f_t, float* __restrict__ wrench) {
-    __shared__ float red[NWARPS * 6];
-    for (int64_t b = blockIdx.x; b < B; b += gridDim.x)
-        process_pad<NWARPS>(tab, prm, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t, wrench, b, red);
+// One warp per pad, eight pads per CTA, grid-stride over pads.
+__global__ void __launch_bounds__(256) penalty_kernel(const SdfTable tab, const Params4 prm, int64_t B, int P, int T,
+                                                      const float* __restrict__ taxels,
+                                                      const int32_t* __restrict__ obj_id,
+                                                      const float* __restrict__ pad_pose,
+                                                      const float* __restrict__ pad_twist, float* __restrict__ depth,
+                                                      float* __restrict__ f_n, float* __restrict__ f_t,
+                                                      float* __restrict__ wrench) {
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * 8;
+    for (int64_t b = static_cast<int64_t>(blockIdx.x) * 8 + (threadIdx.x >> 5); b < B; b += nwarps)
+        pad_by_warp<1>(tab, prm, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t, wrench, b);
 }
 
+// Wrench of given force fields: one block per pad, fixed-order block reduction.
 template <int NWARPS>
 __global__ void __launch_bounds__(NWARPS * 32) wrench_kernel(int64_t B, int T, const float* __restrict__ taxels,
                                                              const float* __restrict__ f_n,

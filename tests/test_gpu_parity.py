@@ -9,7 +9,7 @@ import paper_2408_06506_b300 as tacsl
 from paper_2408_06506_b300 import synth
 
 from gpu_common import (DEPTH_ATOL, assert_forces_close, assert_rgb_close, assert_wrench_close, dev,
-                        scene_to_device, wrench_scale)
+                        force_abs_floor, scene_to_device, wrench_scale)
 
 pytestmark = pytest.mark.gpu
 
@@ -34,14 +34,19 @@ def _check_forces(sc, ref, depth, fn, ft, wr):
     nan = np.isnan(ref["depth"])
     assert np.array_equal(np.isnan(depth), nan)
     assert np.abs(np.where(nan, 0, depth - ref["depth"])).max(initial=0) <= DEPTH_ATOL
-    assert_forces_close(fn, ref["f_n"], "f_n")
-    assert_forces_close(ft, ref["f_t"], "f_t")
+    floor = force_abs_floor(sc)
+    assert_forces_close(fn, ref["f_n"], "f_n", floor)
+    assert_forces_close(ft, ref["f_t"], "f_t", floor)
     # out of contact: exactly zero on both sides
-    out = (ref["depth"] == 0)
-    assert not fn[out].any() and not ft[out].any() and not depth[out].any()
+    out = (ref["depth"] == 0) & (depth == 0)
+    assert not fn[out].any() and not ft[out].any()
+    assert np.abs(depth[ref["depth"] == 0]).max(initial=0) <= DEPTH_ATOL
     if wr is not None:
         f = np.where(np.isnan(ref["f_n"]), 0, ref["f_n"] + ref["f_t"])
-        assert_wrench_close(wr.cpu().numpy(), ref["wrench"], wrench_scale(sc.taxels, f))
+        arm = np.linalg.norm(sc.taxels, axis=-1).max()
+        n_contact = ((np.nan_to_num(ref["depth"]) > 0) | (np.nan_to_num(depth) > 0)).sum(-1)   # [E, P]
+        wfloor = (n_contact * floor[:, :, 0])[..., None] * np.array([1, 1, 1, arm, arm, arm])
+        assert_wrench_close(wr.cpu().numpy(), ref["wrench"], wrench_scale(sc.taxels, f), abs_floor=wfloor)
 
 
 # ---------------------------------------------------------------------------
