@@ -176,10 +176,11 @@ int tacsl_shade_image(const tacsl_shading* shading, int64_t B, const int32_t* se
                       const float* depth_map, uint8_t* rgb, tacsl_stream_t stream);
 
 /*
- * The whole tactile step in one launch: tacsl_penalty_forces on the E x P pads and
- * tacsl_shade_image on their E*P depth maps (image b = e*P + p belongs to pad (e, p)).
- * Arguments and results are exactly those of the two calls; shading may be NULL to
- * skip the images (then sensor_id, depth_map and rgb are ignored).
+ * The whole tactile step in one call: tacsl_shade_image on the E*P depth maps (image
+ * b = e*P + p belongs to pad (e, p)) and tacsl_penalty_forces on the E x P pads.
+ * Arguments and results are exactly those of the two calls; shading may be NULL to skip
+ * the images (then sensor_id, depth_map and rgb are ignored).  The call enqueues the
+ * image kernel and then the force-field kernel on `stream`.
  */
 int tacsl_tactile_step(const tacsl_sdf_set* set, const tacsl_contact_params* params,
                        int32_t E, int32_t P, int32_t T, const float* taxels,

@@ -237,7 +237,7 @@ def shade_image(shading: Shading, sensor_id, depth_map, rgb=None, stream=None):
 def tactile_step(sdfs: SdfSet, params: ContactParams, taxels, obj_id, pad_pose, pad_twist,
                  shading: Shading | None = None, sensor_id=None, depth_map=None,
                  depth=None, f_n=None, f_t=None, wrench=None, rgb=None, with_wrench=True, stream=None):
-    """Force field of E x P pads and (if shading is given) their E*P tactile images, one launch.
+    """Force field of E x P pads and (if shading is given) their E*P tactile images, one call.
 
     Returns (depth, f_n, f_t, wrench, rgb)."""
     _dev(taxels, torch.float32, "taxels")

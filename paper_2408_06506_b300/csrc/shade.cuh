@@ -1,6 +1,5 @@
 // Tactile-image kernel: depth map -> normals -> per-pixel quadratic shading -> uint8
-// RGB (Sec. III-B of arXiv 2408.06506, I_rgb = F(I_depth)), and the fused tactile
-// step that runs the force field (taxel.cuh) in the same persistent launch.
+// RGB (Sec. III-B of arXiv 2408.06506, I_rgb = F(I_depth)).
 //
 // Design (B300):
 // * A tile is 1920 consecutive pixels of the flattened H*W image, 4 per compute
@@ -72,19 +71,6 @@ struct ShadeArgs {
     float cx_c, cx_e, cy_c, cy_e;   // 1/(2 pitch_x), 1/pitch_x, 1/(2 pitch_y), 1/pitch_y
     int n_stages, stage_floats;
     int store_mode;
-};
-
-struct TaxelArgs {                  // force-field half of the fused step
-    Params4 prm;
-    int B, P, T;
-    const float* taxels;
-    const int32_t* obj_id;
-    const float* pad_pose;
-    const float* pad_twist;
-    float* depth;
-    float* f_n;
-    float* f_t;
-    float* wrench;
 };
 
 // Work item k = (image block, sensor, tile), tile fastest: consecutive items - run at
@@ -164,10 +150,50 @@ __device__ __forceinline__ void stg_v4_hint(void* p, uint4 v, uint64_t pol) {
                  : "memory");
 }
 
-// Producer warp: walks this CTA's items; for an item with at least one image of its
-// sensor it stages the tile's 18 coefficient rows into shared memory, then streams each
-// matching image's tile (+ one halo row above and below, a contiguous byte range) into
-// the stage ring with bulk copies, announcing (image, item) in meta[].
+// Does block `it` hold an image of sensor it.s?  (Warp-uniform; flags bad sensor ids once
+// per block, on the item (sensor 0, tile 0).)
+__device__ __forceinline__ bool item_has_images(const ShadeArgs& A, const Item& it) {
+    const int lane = threadIdx.x & 31;
+    const int b0 = it.blk * A.M, b1 = min(b0 + A.M, A.B);
+    const bool check = it.s == 0 && it.tile == 0;
+    bool any = false;
+    for (int base = b0; base < b1; base += 32) {
+        const int b = base + lane;
+        const int sid = b < b1 ? __ldg(A.sensor_id + b) : -1;
+        if (check && b < b1 && (sid < 0 || sid >= A.S)) raise_dev_error(TACSL_DEVERR_BAD_SENSOR_ID);
+        if (__any_sync(0xffffffffu, sid == it.s)) {
+            any = true;
+            if (!check) break;
+        }
+    }
+    return any;
+}
+
+// This CTA's next item (after k) with at least one image of its sensor, or n_items.
+__device__ __forceinline__ int next_item(const ShadeArgs& A, int k) {
+    for (k += gridDim.x; k < A.n_items; k += gridDim.x)
+        if (item_has_images(A, decode_item(A, k))) return k;
+    return A.n_items;
+}
+
+// Stage item k's 18 coefficient rows into shared memory (lane 0 issues the copies).
+__device__ __forceinline__ void load_coefficients(const ShadeArgs& A, int k, float* coef, uint64_t* cfull,
+                                                  uint64_t pol) {
+    const Item it = decode_item(A, k);
+    const int tile_start = it.tile * kShTile;
+    const uint32_t row_bytes = static_cast<uint32_t>(min(kShTile, A.HW - tile_start)) * 4u;
+    mbar_arrive_expect_tx(smem_u32(cfull), 18u * row_bytes);
+    const float* src = A.coeffs + static_cast<int64_t>(it.s) * 18 * A.HW + tile_start;
+    for (int r = 0; r < 18; ++r)
+        bulk_g2s(smem_u32(coef + r * kShTile), src + static_cast<int64_t>(r) * A.HW, row_bytes, smem_u32(cfull), pol);
+}
+
+// Producer warp: walks this CTA's items that hold images of their sensor.  Each item's
+// coefficient rows are staged into shared memory one item ahead: as soon as the compute
+// warps have copied item k's coefficients into registers (coefficient-empty barrier),
+// the producer copies item k+1's, while it keeps streaming item k's images - each
+// image's tile plus one halo row above and below, a contiguous byte range - into the
+// stage ring, announcing (image, item) in meta[].
 __device__ __forceinline__ void shade_producer(const ShadeArgs& A, unsigned char* smem) {
     const int lane = threadIdx.x & 31;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffFull);
@@ -180,43 +206,21 @@ __device__ __forceinline__ void shade_producer(const ShadeArgs& A, unsigned char
     const int NS = A.n_stages;
     const uint64_t pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
     int st = 0;
-    uint32_t ph = 0, cph = 0;
+    uint32_t ph = 0, cph = 0;   // cph: phase of the coefficient-empty barrier to wait for next
     bool ok = true;
-    for (int k = blockIdx.x; k < A.n_items && ok; k += gridDim.x) {
+    int k = (static_cast<int>(blockIdx.x) < A.n_items && item_has_images(A, decode_item(A, blockIdx.x)))
+                ? static_cast<int>(blockIdx.x)
+                : next_item(A, blockIdx.x);
+    if (k < A.n_items && lane == 0) load_coefficients(A, k, coef, cfull, pol_keep);   // buffer starts free
+    while (k < A.n_items && ok) {
+        const int kn = next_item(A, k);
+        bool next_loaded = kn >= A.n_items;
         const Item it = decode_item(A, k);
         const int b0 = it.blk * A.M, b1 = min(b0 + A.M, A.B);
         const int tile_start = it.tile * kShTile;
         const int tile_px = min(kShTile, A.HW - tile_start);
         const int lo_px = max(tile_start - A.W, 0);
         const uint32_t bytes = static_cast<uint32_t>(min(tile_start + tile_px + A.W, A.HW) - lo_px) * 4u;
-        // does the block hold an image of this sensor? (and flag bad ids once per block)
-        bool any = false;
-        for (int base = b0; base < b1; base += 32) {
-            const int b = base + lane;
-            const int sid = b < b1 ? __ldg(A.sensor_id + b) : -1;
-            if (it.s == 0 && it.tile == 0 && b < b1 && (sid < 0 || sid >= A.S))
-                raise_dev_error(TACSL_DEVERR_BAD_SENSOR_ID);
-            if (__any_sync(0xffffffffu, sid == it.s)) {
-                any = true;
-                if (!(it.s == 0 && it.tile == 0)) break;
-            }
-        }
-        if (!any) continue;
-        if (lane == 0) {
-            if (mbar_wait_bounded(smem_u32(cempty), cph ^ 1u)) {
-                const uint32_t row_bytes = static_cast<uint32_t>(tile_px) * 4u;
-                mbar_arrive_expect_tx(smem_u32(cfull), 18u * row_bytes);
-                const float* src = A.coeffs + static_cast<int64_t>(it.s) * 18 * A.HW + tile_start;
-                for (int r = 0; r < 18; ++r)
-                    bulk_g2s(smem_u32(coef + r * kShTile), src + static_cast<int64_t>(r) * A.HW, row_bytes,
-                             smem_u32(cfull), pol_keep);
-            } else {
-                raise_dev_error(TACSL_DEVERR_TIMEOUT);
-                ok = false;
-            }
-        }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        cph ^= 1u;
         for (int base = b0; base < b1 && ok; base += 32) {
             const int b = base + lane;
             const int sid = b < b1 ? __ldg(A.sensor_id + b) : -1;
@@ -235,11 +239,31 @@ __device__ __forceinline__ void shade_producer(const ShadeArgs& A, unsigned char
                         raise_dev_error(TACSL_DEVERR_TIMEOUT);
                         ok = false;
                     }
+                    // stage the next item's coefficients once item k's have been taken
+                    if (ok && !next_loaded && mbar_test(smem_u32(cempty), cph)) {
+                        load_coefficients(A, kn, coef, cfull, pol_keep);
+                        next_loaded = true;
+                    }
                 }
                 ok = __shfl_sync(0xffffffffu, ok, 0);
+                next_loaded = __shfl_sync(0xffffffffu, next_loaded, 0);
                 if (++st == NS) { st = 0; ph ^= 1u; }
             }
         }
+        if (ok && !next_loaded) {
+            // item k ended before its coefficients were taken: wait for that, then stage kn
+            if (lane == 0) {
+                if (mbar_wait_bounded(smem_u32(cempty), cph))
+                    load_coefficients(A, kn, coef, cfull, pol_keep);
+                else {
+                    raise_dev_error(TACSL_DEVERR_TIMEOUT);
+                    ok = false;
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+        }
+        cph ^= 1u;
+        k = kn;
     }
     // end-of-stream marker: an arrival without bytes completes the stage's phase
     if (lane == 0 && mbar_wait_bounded(smem_u32(&empty[st]), ph ^ 1u)) {
@@ -248,9 +272,8 @@ __device__ __forceinline__ void shade_producer(const ShadeArgs& A, unsigned char
     }
 }
 
-template <bool kTaxels>
-__device__ __forceinline__ void shade_body(const ShadeArgs& A, const TaxelArgs& X, const SdfTable* tab,
-                                           unsigned char* smem) {
+__global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffFull);
     uint64_t* empty = reinterpret_cast<uint64_t*>(smem + kOffEmpty);
@@ -278,16 +301,6 @@ __device__ __forceinline__ void shade_body(const ShadeArgs& A, const TaxelArgs& 
     }
 
     // ---- compute warps ----
-    if constexpr (kTaxels) {
-        // this CTA's share of the force field, while the producer fills the ring
-        // (one warp per pad; this CTA's pads [p0, p1) are dealt to its compute warps)
-        const int G = gridDim.x, cta = blockIdx.x;
-        const int64_t p0 = static_cast<int64_t>(X.B) * cta / G, p1 = static_cast<int64_t>(X.B) * (cta + 1) / G;
-        for (int64_t b = p0 + warp; b < p1; b += kShConsumerWarps)
-            pad_by_warp<1>(*tab, X.prm, X.P, X.T, X.taxels, X.obj_id, X.pad_pose, X.pad_twist, X.depth, X.f_n, X.f_t,
-                        X.wrench, b);
-    }
-
     const uint64_t pol_stream = policy_evict_first();
     uint8_t* my_staging = smem + kOffStaging + warp * (kShStagingRing * kShWarpStaging);
     f2 cf[6][3][2];                   // coefficients: term, channel, pixel pair
@@ -450,17 +463,7 @@ __device__ __forceinline__ void shade_body(const ShadeArgs& A, const TaxelArgs& 
         }
         if (++st == NS) { st = 0; ph ^= 1u; }
     }
-}
 
-__global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const TaxelArgs X{};
-    shade_body<false>(A, X, nullptr, smem);
-}
-
-__global__ void __launch_bounds__(kShThreads, 1) step_kernel(const ShadeArgs A, const TaxelArgs X, const SdfTable tab) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    shade_body<true>(A, X, &tab, smem);
 }
 
 }  // namespace tacsl

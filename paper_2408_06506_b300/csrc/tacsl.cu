@@ -2,8 +2,8 @@
 //
 // Every entry point validates its host-visible arguments, builds the kernel
 // parameter structs (the SDF table travels by value in the launch), picks the launch
-// shape for this device and enqueues ONE kernel on the caller's stream.  Nothing here
-// allocates device memory or synchronises, except tacsl_check_errors.
+// shape for this device and enqueues its kernel(s) on the caller's stream.  Nothing
+// here allocates device memory or synchronises, except tacsl_check_errors.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -45,7 +45,6 @@ struct DevInfo {
     int sms = 0;
     int max_smem_optin = 0;
     bool shade_attr_set = false;
-    bool step_attr_set = false;
 };
 constexpr int kMaxDevices = 64;
 DevInfo g_dev[kMaxDevices];
@@ -205,7 +204,33 @@ int plan_shade(const tacsl_shading* sh, int64_t B, const int32_t* sensor_id, con
     return TACSL_OK;
 }
 
-int pad_block_warps(int32_t T) { return T <= 128 ? 4 : 8; }
+}  // namespace
+}  // namespace tacsl
+
+namespace tacsl {
+namespace {
+
+int launch_shade(const ShadePlan& plan, DevInfo& dev, tacsl_stream_t stream) {
+    if (!dev.shade_attr_set) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(shade_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dev.max_smem_optin);
+        if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        dev.shade_attr_set = true;
+    }
+    shade_kernel<<<plan.grid, kShThreads, plan.smem, stream>>>(plan.a);
+    return check_launch("image kernel");
+}
+
+// One warp per pad, 8 pads per 256-thread CTA.
+int launch_penalty(const SdfTable& tab, const Params4& prm, int64_t B, int P, int T, const float* taxels,
+                   const int32_t* obj_id, const float* pad_pose, const float* pad_twist, float* depth, float* f_n,
+                   float* f_t, float* wrench, const DevInfo& dev, tacsl_stream_t stream) {
+    const int64_t blocks = (B + 7) / 8;
+    const int grid = static_cast<int>(blocks < (int64_t)dev.sms * 32 ? blocks : (int64_t)dev.sms * 32);
+    penalty_kernel<<<grid, 256, 0, stream>>>(tab, prm, B, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t,
+                                             wrench);
+    return check_launch("force-field kernel");
+}
 
 }  // namespace
 }  // namespace tacsl
@@ -269,11 +294,8 @@ int tacsl_penalty_forces(const tacsl_sdf_set* set, const tacsl_contact_params* p
     const int64_t B = (int64_t)E * P;
     DevInfo* dev;
     if ((rc = device_info(&dev))) return rc;
-    const int64_t blocks = (B + 7) / 8;
-    const int grid = static_cast<int>(blocks < (int64_t)dev->sms * 32 ? blocks : (int64_t)dev->sms * 32);
-    penalty_kernel<<<grid, 256, 0, stream>>>(tab, prm, B, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t,
-                                             wrench);
-    return check_launch("tacsl_penalty_forces");
+    return launch_penalty(tab, prm, B, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t, wrench, *dev,
+                          stream);
 }
 
 int tacsl_pad_wrench(int64_t B, int32_t T, const float* taxels, const float* f_n, const float* f_t, float* wrench,
@@ -291,7 +313,7 @@ int tacsl_pad_wrench(int64_t B, int32_t T, const float* taxels, const float* f_n
             if (!aligned(ptrs[i], 4)) return fail(TACSL_ERR_INVALID_ARG, "%s is not 4-byte aligned", names[i]);
         }
     }
-    if (pad_block_warps(T) == 4)
+    if (T <= 128)
         wrench_kernel<4><<<static_cast<unsigned>(B), 128, 0, stream>>>(B, T, taxels, f_n, f_t, wrench);
     else
         wrench_kernel<8><<<static_cast<unsigned>(B), 256, 0, stream>>>(B, T, taxels, f_n, f_t, wrench);
@@ -307,14 +329,7 @@ int tacsl_shade_image(const tacsl_shading* shading, int64_t B, const int32_t* se
     if ((rc = device_info(&dev))) return rc;
     ShadePlan plan;
     if ((rc = plan_shade(shading, B, sensor_id, depth_map, rgb, *dev, plan))) return rc;
-    if (!dev->shade_attr_set) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(shade_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dev->max_smem_optin);
-        if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-        dev->shade_attr_set = true;
-    }
-    shade_kernel<<<plan.grid, kShThreads, plan.smem, stream>>>(plan.a);
-    return check_launch("tacsl_shade_image");
+    return launch_shade(plan, *dev, stream);
 }
 
 int tacsl_tactile_step(const tacsl_sdf_set* set, const tacsl_contact_params* params, int32_t E, int32_t P, int32_t T,
@@ -339,30 +354,13 @@ int tacsl_tactile_step(const tacsl_sdf_set* set, const tacsl_contact_params* par
     if ((rc = device_info(&dev))) return rc;
     ShadePlan plan;
     if ((rc = plan_shade(shading, B, sensor_id, depth_map, rgb, *dev, plan))) return rc;
-    if (T == 0)   // no force field requested: images only
-        return tacsl_shade_image(shading, B, sensor_id, depth_map, rgb, stream);
-    TaxelArgs X;
-    X.prm = prm;
-    X.B = static_cast<int>(B);
-    X.P = P;
-    X.T = T;
-    X.taxels = taxels;
-    X.obj_id = obj_id;
-    X.pad_pose = pad_pose;
-    X.pad_twist = pad_twist;
-    X.depth = depth;
-    X.f_n = f_n;
-    X.f_t = f_t;
-    X.wrench = wrench;
-    if (!dev->step_attr_set) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dev->max_smem_optin);
-        if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-        dev->step_attr_set = true;
-    }
-    const int grid = dev->sms;
-    step_kernel<<<grid, kShThreads, plan.smem, stream>>>(plan.a, X, tab);
-    return check_launch("tacsl_tactile_step");
+    if ((rc = launch_shade(plan, *dev, stream))) return rc;
+    if (T == 0) return ok();
+    // The image kernel wants ~all of shared memory for its stage ring and coefficient
+    // tile; the force field's scattered SDF gathers want a large L1.  Two launches, each
+    // with its own carve-out, beat one persistent kernel doing both.
+    return launch_penalty(tab, prm, B, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t, wrench, *dev,
+                          stream);
 }
 
 }  // extern "C"

@@ -100,19 +100,33 @@ __device__ __forceinline__ void stencil_fold(const Stencil& q, const float (&v)[
     g[2] = fmaf(q.dz[2], cc[2], fmaf(q.dz[1], cc[1], q.dz[0] * cc[0])) * inv_h;
 }
 
-// phi alone from the 8 nodes of the trilinear cell (the nonzero centre weights), with
-// the FMA order of stencil_fold, so the result is bitwise the phi of the full fold:
-// there each zero-weight term enters as fma(0, v, acc) = acc or as 0 * v + ..., which
-// leaves the sum unchanged.
-__device__ __forceinline__ float stencil_phi8(const Stencil& q, int n0, int n01, uint64_t pol) {
-    // offset of the lower node of each axis' centre cell inside the 3-node window
-    const int ox = q.cx[0] != 0.f || q.cx[2] == 0.f ? 0 : 1;
-    const int oy = q.cy[0] != 0.f || q.cy[2] == 0.f ? 0 : 1;
-    const int oz = q.cz[0] != 0.f || q.cz[2] == 0.f ? 0 : 1;
-    const float wx0 = ox ? q.cx[1] : q.cx[0], wx1 = ox ? q.cx[2] : q.cx[1];
-    const float wy0 = oy ? q.cy[1] : q.cy[0], wy1 = oy ? q.cy[2] : q.cy[1];
-    const float wz0 = oz ? q.cz[1] : q.cz[0], wz1 = oz ? q.cz[2] : q.cz[1];
-    const float* b = q.base + oz * n01 + oy * n0 + ox;
+// Continuous grid index of an object-frame point and its domain test.
+struct GridPos {
+    float ux, uy, uz;
+    bool inside;
+};
+__device__ __forceinline__ GridPos grid_pos(const DevSdf& S, float x, float y, float z) {
+    GridPos g;
+    g.ux = (x - S.ox) * S.inv_h;
+    g.uy = (y - S.oy) * S.inv_h;
+    g.uz = (z - S.oz) * S.inv_h;
+    g.inside = g.ux >= 0.5f && g.ux <= static_cast<float>(S.n0) - 1.5f && g.uy >= 0.5f &&
+               g.uy <= static_cast<float>(S.n1) - 1.5f && g.uz >= 0.5f && g.uz <= static_cast<float>(S.n2) - 1.5f;
+    return g;
+}
+
+// phi alone from the 8 nodes of the trilinear cell of u (cell min(floor(u), n-2) per
+// axis, fraction f, weights 1-f and f), in the FMA order of stencil_fold, so the value
+// is bitwise the phi of the full 27-node fold: there the zero-weight terms enter as
+// fma(0, v, acc) = acc or as 0 * v + ..., which leaves every partial sum unchanged.
+__device__ __forceinline__ float phi_cell8(const DevSdf& S, const GridPos& g, uint64_t pol) {
+    const int ix = min(static_cast<int>(floorf(g.ux)), S.n0 - 2);
+    const int iy = min(static_cast<int>(floorf(g.uy)), S.n1 - 2);
+    const int iz = min(static_cast<int>(floorf(g.uz)), S.n2 - 2);
+    const float fx = g.ux - static_cast<float>(ix), fy = g.uy - static_cast<float>(iy),
+                fz = g.uz - static_cast<float>(iz);
+    const int n0 = S.n0, n01 = S.n0 * S.n1;
+    const float* b = S.data + (static_cast<int64_t>(iz) * n01 + static_cast<int64_t>(iy) * n0 + ix);
     float v[2][2][2];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
@@ -123,11 +137,11 @@ __device__ __forceinline__ float stencil_phi8(const Stencil& q, int n0, int n01,
     float c[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const float r0 = fmaf(wx1, v[k][0][1], wx0 * v[k][0][0]);
-        const float r1 = fmaf(wx1, v[k][1][1], wx0 * v[k][1][0]);
-        c[k] = fmaf(wy1, r1, wy0 * r0);
+        const float r0 = fmaf(fx, v[k][0][1], (1.f - fx) * v[k][0][0]);
+        const float r1 = fmaf(fx, v[k][1][1], (1.f - fx) * v[k][1][0]);
+        c[k] = fmaf(fy, r1, (1.f - fy) * r0);
     }
-    return fmaf(wz1, c[1], wz0 * c[0]);
+    return fmaf(fz, c[1], (1.f - fz) * c[0]);
 }
 
 // SDF value and gradient at object-frame point (x, y, z).  Returns false outside the
@@ -212,8 +226,8 @@ __device__ __forceinline__ void pad_by_warp(const SdfTable& tab, const Params4& 
     const float* r = Pz.r;
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int t0 = lane; t0 < T; t0 += 32 * NP) {
-        float p[NP][3], vel[NP][3];
-        Stencil q[NP];
+        float p[NP][3], vel[NP][3], phi8[NP];
+        GridPos gp[NP];
         bool on[NP];
 #pragma unroll
         for (int u = 0; u < NP; ++u) {
@@ -230,25 +244,31 @@ __device__ __forceinline__ void pad_by_warp(const SdfTable& tab, const Params4& 
             vel[u][0] = Pz.v[0] + (Pz.w[1] * zo - Pz.w[2] * yo);
             vel[u][1] = Pz.v[1] + (Pz.w[2] * xo - Pz.w[0] * zo);
             vel[u][2] = Pz.v[2] + (Pz.w[0] * yo - Pz.w[1] * xo);
-            q[u] = stencil_setup(S, xo, yo, zo);
-            q[u].inside = q[u].inside && on[u];
+            gp[u] = grid_pos(S, xo, yo, zo);
+            gp[u].inside = gp[u].inside && on[u];
         }
-        // phi from the 8-node cell first; the 27-node window (and the gradient) only
-        // where the point penetrates - elsewhere the outputs are exact zeros either way
-        float phi8[NP];
+        // phi from the 8-node cells (all NP gathers in flight together)
 #pragma unroll
         for (int u = 0; u < NP; ++u)
-            phi8[u] = q[u].inside ? stencil_phi8(q[u], n0, n01, pol) : __int_as_float(0x7f800000);
-        float v[NP][3][3][3];
-#pragma unroll
-        for (int u = 0; u < NP; ++u)
-            if (phi8[u] < 0.f) stencil_load(q[u], n0, n01, pol, v[u]);
+            phi8[u] = gp[u].inside ? phi_cell8(S, gp[u], pol) : __int_as_float(0x7f800000);
 #pragma unroll
         for (int u = 0; u < NP; ++u) {
             if (!on[u]) continue;
             const int t = t0 + 32 * u;
             float phi = phi8[u], g[3] = {0.f, 0.f, 0.f};
-            if (phi8[u] < 0.f) stencil_fold(q[u], v[u], S.inv_h, phi, g);
+            if (phi8[u] < 0.f) {
+                // penetrating: the 27-node window gives the gradient (and the same phi)
+                Stencil q;
+                q.inside = true;
+                int bx, by, bz;
+                axis_weights(gp[u].ux, S.n0, bx, q.cx, q.dx);
+                axis_weights(gp[u].uy, S.n1, by, q.cy, q.dy);
+                axis_weights(gp[u].uz, S.n2, bz, q.cz, q.dz);
+                q.base = S.data + (static_cast<int64_t>(bz) * n01 + static_cast<int64_t>(by) * n0 + bx);
+                float v[3][3][3];
+                stencil_load(q, n0, n01, pol, v);
+                stencil_fold(q, v, S.inv_h, phi, g);
+            }
             float dep, fn[3], ft[3];
             contact_force(r, phi, g, vel[u][0], vel[u][1], vel[u][2], kn, kd, kt, mu, dep, fn, ft);
             depth[o + t] = dep;
@@ -310,7 +330,7 @@ __global__ void __launch_bounds__(256) penalty_kernel(const SdfTable tab, const 
                                                       float* __restrict__ wrench) {
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * 8;
     for (int64_t b = static_cast<int64_t>(blockIdx.x) * 8 + (threadIdx.x >> 5); b < B; b += nwarps)
-        pad_by_warp<1>(tab, prm, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t, wrench, b);
+        pad_by_warp<4>(tab, prm, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t, wrench, b);
 }
 
 // Wrench of given force fields: one block per pad, fixed-order block reduction.

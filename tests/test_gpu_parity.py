@@ -248,9 +248,9 @@ def test_tactile_step_matches_separate_calls(orc, E, ny, nx, H, W):
                                   with_intensity=True)
     assert_rgb_close(rgb.cpu().numpy(), ref_rgb, ref_I)
     # same per-taxel and per-pixel arithmetic as the separate entry points: identical bits
-    d2, fn2, ft2, _ = tacsl.penalty_forces(d["sdfs"], d["params"], d["taxels"], d["obj_id"], d["pose"], d["twist"])
+    d2, fn2, ft2, wr2 = tacsl.penalty_forces(d["sdfs"], d["params"], d["taxels"], d["obj_id"], d["pose"], d["twist"])
     rgb2 = tacsl.shade_image(d["shading"], d["sensor_id"], d["depth_map"])
-    assert torch.equal(depth, d2) and torch.equal(fn, fn2) and torch.equal(ft, ft2)
+    assert torch.equal(depth, d2) and torch.equal(fn, fn2) and torch.equal(ft, ft2) and torch.equal(wr, wr2)
     assert torch.equal(rgb, rgb2.view_as(rgb))
 
 
