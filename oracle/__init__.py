@@ -66,6 +66,10 @@ def _bind(lib):
                               P, P, P, P, C.c_int32]
     lib.orc_quantize.restype = C.c_uint8
     lib.orc_quantize.argtypes = [C.c_double]
+    lib.orc_render_depth.restype = C.c_int64
+    lib.orc_render_depth.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, C.c_int32]
+    lib.orc_column_phi.restype = C.c_double
+    lib.orc_column_phi.argtypes = [P, P, C.c_double, C.c_double, C.c_double]
     return lib
 
 
@@ -222,3 +226,28 @@ def shade(coeffs, pitch_x, pitch_y, sensor_id, depth, with_intensity=False, rgb_
 
 def quantize(v: float) -> int:
     return int(_load().orc_quantize(float(v)))
+
+
+class _Camera(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("pitch_x", C.c_float), ("pitch_y", C.c_float),
+                ("x0", C.c_float), ("y0", C.c_float), ("d0", C.c_float), ("z_max", C.c_float)]
+
+
+def render_depth(grids, obj_id, pad_pose, H, W, pitch_x, pitch_y, x0, y0, d0, z_max, nthreads=None):
+    """Depth maps [E, P, H, W] (float64) of the orthographic column camera."""
+    pad_pose = _f32(pad_pose)
+    E, P = pad_pose.shape[0], pad_pose.shape[1]
+    obj_id = _i32(obj_id).reshape(E)
+    cam = _Camera(H, W, pitch_x, pitch_y, x0, y0, d0, z_max)
+    out = np.empty((E, P, H, W))
+    arr, keep = _sdf_array(grids)
+    bad = _load().orc_render_depth(arr, len(grids), E, P, _ptr(obj_id), _ptr(pad_pose), C.byref(cam), _ptr(out),
+                                   nthreads or default_threads())
+    return out, int(bad)
+
+
+def column_phi(grid, pose7, x, y, z) -> float:
+    """The SDF value the column march sees at pad-frame point (x, y, z)."""
+    arr, keep = _sdf_array([grid])
+    pose7 = _f32(pose7).reshape(7)
+    return float(_load().orc_column_phi(C.byref(arr[0]), _ptr(pose7), float(x), float(y), float(z)))

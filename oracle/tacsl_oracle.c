@@ -312,3 +312,119 @@ int64_t orc_shade(const float* coeffs, int32_t S, int32_t H, int32_t W, float pi
     }
     return bad;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Depth-map rendering (Sec. III-B: a camera behind the gel renders the depth  */
+/* of the indenting object).                                                   */
+/* ------------------------------------------------------------------------- */
+
+/* Reading: an orthographic camera looks along the pad normal; pixel (i, j)'s ray is
+ * the pad-frame column (x_i, y_j, z).  The gel surface is z = 0 at distance d0; where
+ * the object reaches below it, the camera sees the object's first point on the column,
+ * so D = d0 - max(0, -z_hit).  The column is searched over [-z_max, 0] from below. */
+
+#define ORC_MARCH_MAX 1024
+#define ORC_BISECT 24
+
+/* Distance from object-frame point x to the grid's domain box (0 inside). */
+static double domain_box_distance(const orc_sdf* s, const double x[3]) {
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double lo = (double)s->origin[a] + 0.5 * (double)s->voxel;
+        const double hi = (double)s->origin[a] + ((double)s->n[a] - 1.5) * (double)s->voxel;
+        double e = 0.0;
+        if (x[a] < lo) e = lo - x[a];
+        else if (x[a] > hi) e = x[a] - hi;
+        d2 += e * e;
+    }
+    return sqrt(d2);
+}
+
+/* phi seen by the march: trilinear inside the domain; outside, the distance to the
+ * domain box (the object lies inside the domain, so that bounds the distance to it). */
+static double column_phi_obj(const orc_sdf* s, const double x[3], int* inside) {
+    double phi, g[3];
+    *inside = orc_sdf_eval(s, x, &phi, g);
+    return *inside ? phi : domain_box_distance(s, x);
+}
+
+double orc_column_phi(const orc_sdf* s, const float* pose7, double x, double y, double z) {
+    double R[3][3];
+    quat_to_rot(pose7 + 3, R);
+    double xo[3];
+    for (int a = 0; a < 3; ++a) xo[a] = R[a][0] * x + R[a][1] * y + R[a][2] * z + (double)pose7[a];
+    int inside;
+    return column_phi_obj(s, xo, &inside);
+}
+
+/* z_hit of one column (returns 1 on a hit).  March: from z = -z_max step up by
+ * kappa*phi inside the domain (kappa = 1/sqrt(3): the trilinear interpolant of a
+ * 1-Lipschitz field is at most sqrt(3)-Lipschitz, so the step cannot pass the surface)
+ * or by the box distance outside it, never less than voxel/8; the first sample with
+ * phi <= 0 closes a bracket that ORC_BISECT halvings shrink; z_hit is its upper end. */
+static int column_hit(const orc_sdf* s, const double R[3][3], const double t[3], double px, double py,
+                      double z_max, double* z_hit) {
+    const double dmin = (double)s->voxel / 8.0;
+    const double kappa = 1.0 / sqrt(3.0);
+    double x[3];
+    int inside;
+#define COLUMN_POINT(zz)                                                         \
+    for (int a = 0; a < 3; ++a) x[a] = R[a][0] * px + R[a][1] * py + R[a][2] * (zz) + t[a];
+    double z = -z_max;
+    COLUMN_POINT(z);
+    double phi = column_phi_obj(s, x, &inside);
+    if (phi <= 0.0) { *z_hit = z; return 1; }   /* the object reaches below -z_max */
+    for (int it = 0; it < ORC_MARCH_MAX; ++it) {
+        double step = inside ? kappa * phi : phi;
+        if (step < dmin) step = dmin;
+        double zn = z + step;
+        if (zn > 0.0) zn = 0.0;
+        COLUMN_POINT(zn);
+        int inside_n;
+        const double phin = column_phi_obj(s, x, &inside_n);
+        if (phin <= 0.0) {
+            double lo = z, hi = zn;
+            for (int k = 0; k < ORC_BISECT; ++k) {
+                const double mid = 0.5 * (lo + hi);
+                COLUMN_POINT(mid);
+                int im;
+                if (column_phi_obj(s, x, &im) <= 0.0) hi = mid; else lo = mid;
+            }
+            *z_hit = hi;
+            return 1;
+        }
+        if (zn >= 0.0) return 0;
+        z = zn; phi = phin; inside = inside_n;
+    }
+#undef COLUMN_POINT
+    return 0;
+}
+
+int64_t orc_render_depth(const orc_sdf* sdfs, int32_t n_sdf, int32_t E, int32_t P, const int32_t* obj_id,
+                         const float* pad_pose, const orc_camera* cam, double* depth, int32_t nthreads) {
+    int64_t bad = 0;
+    const int64_t B = (int64_t)E * P, HW = (int64_t)cam->H * cam->W;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int64_t b = 0; b < B; ++b) {
+        double* D = depth + b * HW;
+        const int32_t id = obj_id[b / P];
+        if (id < 0 || id >= n_sdf) {
+            for (int64_t k = 0; k < HW; ++k) D[k] = NAN;
+            ++bad;
+            continue;
+        }
+        const float* pose = pad_pose + b * 7;
+        double R[3][3];
+        quat_to_rot(pose + 3, R);
+        const double t[3] = {pose[0], pose[1], pose[2]};
+        for (int32_t j = 0; j < cam->H; ++j)
+            for (int32_t i = 0; i < cam->W; ++i) {
+                const double px = (double)cam->x0 + (double)i * (double)cam->pitch_x;
+                const double py = (double)cam->y0 + (double)j * (double)cam->pitch_y;
+                double zh;
+                const int hit = column_hit(&sdfs[id], R, t, px, py, (double)cam->z_max, &zh);
+                D[(int64_t)j * cam->W + i] = (double)cam->d0 - (hit && zh < 0.0 ? -zh : 0.0);
+            }
+    }
+    return bad;
+}

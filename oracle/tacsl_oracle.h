@@ -80,6 +80,27 @@ int64_t orc_shade(const float* coeffs, int32_t S, int32_t H, int32_t W, float pi
                   float pitch_y, int64_t B, const int32_t* sensor_id, const float* depth,
                   double* intensity, uint8_t* rgb, int32_t nthreads);
 
+/* Orthographic tactile camera along the pad normal (stand-in for the in-sensor camera
+ * of Sec. III-B).  Pixel (i, j) looks along +z of the pad frame through the pad-frame
+ * point (x0 + i*pitch_x, y0 + j*pitch_y, 0); the undeformed gel reads d0. */
+typedef struct {
+    int32_t H, W;
+    float pitch_x, pitch_y;
+    float x0, y0;
+    float d0;
+    float z_max;
+} orc_camera;
+
+/* Depth maps [E][P][H][W]: D = d0 - max(0, -z_hit), z_hit the first point of the object
+ * met by the column z in [-z_max, 0] (marching up from -z_max), else no hit (D = d0).
+ * Returns the number of pads whose obj id is bad (their maps are NaN). */
+int64_t orc_render_depth(const orc_sdf* sdfs, int32_t n_sdf, int32_t E, int32_t P, const int32_t* obj_id,
+                         const float* pad_pose, const orc_camera* cam, double* depth, int32_t nthreads);
+
+/* The SDF value the column march sees at pad-frame point (x, y, z) of a pad posed by
+ * pose7 (inside the grid domain: trilinear; outside: distance to the domain box). */
+double orc_column_phi(const orc_sdf* sdf, const float* pose7, double x, double y, double z);
+
 /* Quantisation of one intensity: clamp to [0, 255], round half up; NaN -> 0. */
 uint8_t orc_quantize(double v);
 

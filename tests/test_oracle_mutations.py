@@ -47,6 +47,12 @@ MUTATIONS = {
                       "const double m[6] = {1.0, n[1], n[0], n[0] * n[0], n[1] * n[1], n[0] * n[1]};"),
     "coeff_channel_index": ("(double)A[(int64_t)(k * 3 + c) * HW + px]", "(double)A[(int64_t)(c * 6 + k) * HW + px]"),
     "quantise_truncates": ("return (uint8_t)floor(v + 0.5);", "return (uint8_t)floor(v);"),
+    "render_pixel_axes_swapped": ("const double px = (double)cam->x0 + (double)i * (double)cam->pitch_x;",
+                                  "const double px = (double)cam->x0 + (double)j * (double)cam->pitch_x;"),
+    "render_depth_sign": ("D[(int64_t)j * cam->W + i] = (double)cam->d0 - (hit && zh < 0.0 ? -zh : 0.0);",
+                          "D[(int64_t)j * cam->W + i] = (double)cam->d0 + (hit && zh < 0.0 ? -zh : 0.0);"),
+    "render_bisection_reversed": ("if (column_phi_obj(s, x, &im) <= 0.0) hi = mid; else lo = mid;",
+                                  "if (column_phi_obj(s, x, &im) > 0.0) hi = mid; else lo = mid;"),
 }
 
 PINS = os.path.join(os.path.dirname(__file__), "test_oracle_pins.py")

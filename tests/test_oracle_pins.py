@@ -475,3 +475,79 @@ def test_single_row_and_column_maps(orc):
     n = orc.depth_normals(D, 2.0 ** -14, 1e-4)
     assert not n[..., 1].any()
     np.testing.assert_allclose(n[0, :, 0], 0.125 / math.sqrt(1 + 0.125 ** 2), rtol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Depth rendering (Sec. III-B: the in-sensor camera sees the indenting object)
+# ---------------------------------------------------------------------------
+
+def _render(orc, grid, pose, H=9, W=11, pitch=0.5e-3, d0=0.02, z_max=3e-3):
+    x0, y0 = -(W - 1) / 2 * pitch, -(H - 1) / 2 * pitch
+    D, bad = orc.render_depth([grid], [0], np.asarray(pose, np.float32).reshape(1, 1, 7), H, W, pitch, pitch,
+                              x0, y0, d0, z_max)
+    xs = x0 + np.arange(W) * pitch
+    ys = y0 + np.arange(H) * pitch
+    return D[0, 0], xs, ys, bad
+
+
+def test_render_parallel_plane_closed_form(orc):
+    """A half-space cut delta into the pad: every column meets it at z = -delta."""
+    grid, nrm = _plane_grid([0.2, -0.3, 1.0], n=48, h=0.5e-3)
+    pose, R = _pad_facing_plane(nrm, 4e-4, synth.quat_from_axis_angle([0, 0, 1], 0.4))
+    D, xs, ys, bad = _render(orc, grid, pose)
+    assert bad == 0
+    np.testing.assert_allclose(D, 0.02 - 4e-4, atol=2e-9)
+
+
+def test_render_tilted_plane_closed_form(orc):
+    """A half-space tilted against the pad: phi along a column is phi(0) + z (n . d), so
+    the first point inside is z = -phi(0) / (n . d); this also pins the pixel order."""
+    grid, nrm = _plane_grid([0.0, 0.0, 1.0], n=64, h=0.5e-3)
+    q = synth.quat_multiply([0.0, 1.0, 0.0, 0.0], synth.quat_from_axis_angle([1.0, 0.5, 0.0], 0.3))
+    R = synth.quat_to_matrix(q)
+    pose = _pose(-3e-4 * np.array([0, 0, 1.0]) @ np.eye(3), q)    # pad origin 0.3 mm inside the plane
+    D, xs, ys, bad = _render(orc, grid, pose)
+    d = R[:, 2]
+    assert nrm @ d < 0
+    for j, y in enumerate(ys):
+        for i, x in enumerate(xs):
+            p0 = R @ np.array([x, y, 0.0]) + pose[:3].astype(np.float64)
+            zh = -(nrm @ p0) / (nrm @ d)
+            want = 0.02 - max(0.0, -zh) if zh >= -3e-3 else 0.02 - 3e-3
+            assert D[j, i] == pytest.approx(want, abs=3e-9)
+    assert np.ptp(D[:, 0]) > 1e-5 and np.ptp(D[0, :]) > 1e-5    # varies along both image axes
+
+
+def test_render_sphere_within_interpolation_bound(orc):
+    """Sphere R indenting by delta: the column at radius r meets it at c - sqrt(R^2 - r^2)
+    (pad frame); away from near-tangent columns the interpolation error h^2/(4 rho),
+    divided by the column's |d phi/dz| >= 0.3, bounds the difference."""
+    Rs, delta, h = 5e-3, 8e-4, 0.25e-3
+    grid = synth.bake(synth.Shape("sphere", (Rs,)), 64, h)
+    pose = synth.place_pad(synth.Shape("sphere", (Rs,)), np.array([1.0, 0, 0, 0]), delta, (0.4e-3, -0.7e-3))
+    D, xs, ys, bad = _render(orc, grid, pose, H=21, W=25, pitch=0.2e-3)
+    c = -pose[:3].astype(np.float64)          # sphere centre in the pad frame (R = I)
+    bound = h * h / 8 * 2 / (Rs - 1e-3) / 0.3 + 1e-8
+    checked = 0
+    for j, y in enumerate(ys):
+        for i, x in enumerate(xs):
+            r2 = (x - c[0]) ** 2 + (y - c[1]) ** 2
+            if r2 >= Rs * Rs:
+                continue
+            zh = c[2] - np.sqrt(Rs * Rs - r2)
+            if (c[2] - zh) / Rs < 0.3 or zh > -1e-6:
+                continue
+            assert abs(D[j, i] - (0.02 + zh)) <= bound
+            checked += 1
+    assert checked > 50
+    assert D.min() == pytest.approx(0.02 - delta, abs=bound)
+
+
+def test_render_miss_is_exactly_d0_and_deep_object_clamps(orc):
+    grid, nrm = _plane_grid([0.0, 0.0, 1.0], n=48, h=0.5e-3)
+    pose, R = _pad_facing_plane(nrm, -5e-4, np.array([1.0, 0, 0, 0]))     # 0.5 mm gap
+    D, *_ = _render(orc, grid, pose)
+    assert (D == np.float64(np.float32(0.02))).all()
+    pose, R = _pad_facing_plane(nrm, 5e-3, np.array([1.0, 0, 0, 0]))      # 5 mm deep > z_max
+    D, *_ = _render(orc, grid, pose, z_max=3e-3)
+    np.testing.assert_allclose(D, np.float64(np.float32(0.02)) - np.float64(np.float32(3e-3)), atol=1e-12)
