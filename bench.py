@@ -54,6 +54,11 @@ def parse():
     return ap.parse_args()
 
 
+def synth_d0():
+    from paper_2408_06506_b300 import synth
+    return synth.D0
+
+
 def make_scene(envs, seed):
     from paper_2408_06506_b300 import synth
     return synth.scene_objects(seed=seed, E=envs, P=2, depth_maps="cycled", n_distinct_maps=256)
@@ -318,6 +323,45 @@ def run_ours(args, rank, world, local_rank, dist):
         sdfs, params, taxels, obj_id, pose, twist, shading, sensor_id, dense, **outs), nb)
     del dense
 
+    # ---- depth maps rendered from the poses (column march of the in-sensor camera) ----
+    cam = tacsl.Camera(sc.H, sc.W, sc.pitch_x, sc.pitch_y, -sc.pitch_x * sc.W / 2 + 0.5 * sc.pitch_x,
+                       -sc.pitch_y * sc.H / 2 + 0.5 * sc.pitch_y, synth_d0(), 3e-3)
+    dmap = torch.empty_like(depth_map)
+    breakdown["render_depth_ms"] = timed(lambda: tacsl.render_depth(sdfs, cam, obj_id, pose, depth_map=dmap), nb)
+    breakdown["render_step_ms"] = timed(lambda: tacsl.render_step(
+        sdfs, params, taxels, obj_id, pose, twist, shading, cam, sensor_id, depth_map=dmap, **outs), nb)
+    render = {"ms_per_step": breakdown["render_step_ms"],
+              "taxel_points_per_s": world * E * P * T / (breakdown["render_step_ms"] * 1e-3),
+              "images_per_s": world * E * P / (breakdown["render_step_ms"] * 1e-3)}
+    if not args.no_e2e:
+        # the RL loop: pose/twist of this step in from pinned host memory, observations stay on
+        # the device, the per-pad wrench comes back to the host
+        h_pose = torch.as_tensor(sc.pad_pose).pin_memory()
+        h_twist = torch.as_tensor(sc.pad_twist).pin_memory()
+        h_wr = torch.empty(outs["wrench"].shape, dtype=torch.float32).pin_memory()
+
+        def render_e2e_step():
+            pose.copy_(h_pose, non_blocking=True)
+            twist.copy_(h_twist, non_blocking=True)
+            tacsl.render_step(sdfs, params, taxels, obj_id, pose, twist, shading, cam, sensor_id, depth_map=dmap,
+                              **outs)
+            h_wr.copy_(outs["wrench"], non_blocking=True)
+
+        for _ in range(3):
+            render_e2e_step()
+        torch.cuda.synchronize()
+        n_r = max(20, args.steps // 10)
+        t0 = time.perf_counter()
+        for _ in range(n_r):
+            render_e2e_step()
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
+        render["e2e"] = {"value": world * E * P * T * n_r / el, "unit": "taxel-points/s",
+                         "images_per_s": world * E * P * n_r / el, "ms_per_step": 1e3 * el / n_r,
+                         "h2d_bytes_per_step": h_pose.numel() * 4 + h_twist.numel() * 4,
+                         "d2h_bytes_per_step": h_wr.numel() * 4, "steps": n_r,
+                         "path": "pinned pose+twist -> tacsl_render_step -> pinned wrench; images stay on device"}
+
     # ---- end to end: pinned host inputs in, results back to pinned host, every step ----
     e2e = None
     if not args.no_e2e:
@@ -399,6 +443,7 @@ def run_ours(args, rank, world, local_rank, dist):
                           "kernels": ["tacsl::shade_kernel", "tacsl::penalty_kernel"]},
         "clocks": clk.summary(),
         "breakdown": breakdown,
+        "render_step": render,
         "gpu_launches": 2 * args.steps,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -102,6 +102,19 @@ typedef struct {
     int32_t n_sensor; /* 1 .. TACSL_MAX_SENSOR */
 } tacsl_shading;
 
+/* Orthographic tactile camera looking along the pad normal: the stand-in for the
+ * in-sensor camera of Sec. III-B.  Pixel (i, j) sees the pad-frame column
+ * (x0 + i*pitch_x, y0 + j*pitch_y, z); the undeformed gel (z = 0) reads d0; the column is
+ * searched for the indenting object over z in [-z_max, 0].  H >= 1, W >= 4 and W % 4 = 0
+ * (the image kernel's layout), pitches > 0, z_max > 0. */
+typedef struct {
+    int32_t H, W;
+    float pitch_x, pitch_y;
+    float x0, y0;
+    float d0;
+    float z_max;
+} tacsl_camera;
+
 /* Thread-local description of the last failing call on this thread ("" if none). */
 const char* tacsl_last_error(void);
 
@@ -188,6 +201,35 @@ int tacsl_tactile_step(const tacsl_sdf_set* set, const tacsl_contact_params* par
                        float* depth, float* f_n, float* f_t, float* wrench,
                        const tacsl_shading* shading, const int32_t* sensor_id,
                        const float* depth_map, uint8_t* rgb, tacsl_stream_t stream);
+
+/*
+ * Depth maps of the E x P pads (Sec. III-B: "render a depth image I_depth showing the
+ * indenting object" from a camera inside the sensor; the paper does this with a graphics
+ * render, here it is a CUDA column march against the posed SDF).
+ *   depth_map [E][P][H][W] float32 (16-byte aligned):
+ *     D = d0 - max(0, -z_hit), z_hit = the first point of the object on the pixel's column
+ *     over [-z_max, 0] (marching up from -z_max), D = d0 where the column misses it.
+ * The march: steps of phi/sqrt(3) where the column is inside the grid's domain (phi = the
+ * trilinear SDF), the distance to the domain box outside it, never below voxel/8; the
+ * first step that lands inside the object (in the domain with phi <= 0; outside the domain
+ * the SDF is undefined and never counts) closes a bracket that is halved until it is at
+ * most voxel * 2^-16 wide; z_hit is its upper end.  A bad obj_id gives NaN maps and sets TACSL_DEVERR_BAD_OBJ_ID.
+ */
+int tacsl_render_depth(const tacsl_sdf_set* set, int32_t E, int32_t P, const int32_t* obj_id,
+                       const float* pad_pose, const tacsl_camera* camera, float* depth_map,
+                       tacsl_stream_t stream);
+
+/*
+ * The tactile step from poses alone: tacsl_render_depth into depth_map (a caller buffer,
+ * [E][P][H][W]), then tacsl_shade_image on it and tacsl_penalty_forces, in that order on
+ * `stream`.  The camera's H and W must equal the shading model's.
+ */
+int tacsl_render_step(const tacsl_sdf_set* set, const tacsl_contact_params* params, int32_t E,
+                      int32_t P, int32_t T, const float* taxels, const int32_t* obj_id,
+                      const float* pad_pose, const float* pad_twist, float* depth, float* f_n,
+                      float* f_t, float* wrench, const tacsl_shading* shading,
+                      const tacsl_camera* camera, const int32_t* sensor_id, float* depth_map,
+                      uint8_t* rgb, tacsl_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -324,7 +324,7 @@ int64_t orc_shade(const float* coeffs, int32_t S, int32_t H, int32_t W, float pi
  * so D = d0 - max(0, -z_hit).  The column is searched over [-z_max, 0] from below. */
 
 #define ORC_MARCH_MAX 1024
-#define ORC_BISECT 24
+#define ORC_BISECT_MAX 40
 
 /* Distance from object-frame point x to the grid's domain box (0 inside). */
 static double domain_box_distance(const orc_sdf* s, const double x[3]) {
@@ -341,7 +341,9 @@ static double domain_box_distance(const orc_sdf* s, const double x[3]) {
 }
 
 /* phi seen by the march: trilinear inside the domain; outside, the distance to the
- * domain box (the object lies inside the domain, so that bounds the distance to it). */
+ * domain box (the object lies inside the domain, so that bounds the distance to it).
+ * Outside the domain the SDF is undefined (phi = +inf there, as for the force field), so
+ * a point there is never inside the object; the box distance only sizes the step. */
 static double column_phi_obj(const orc_sdf* s, const double x[3], int* inside) {
     double phi, g[3];
     *inside = orc_sdf_eval(s, x, &phi, g);
@@ -360,8 +362,9 @@ double orc_column_phi(const orc_sdf* s, const float* pose7, double x, double y, 
 /* z_hit of one column (returns 1 on a hit).  March: from z = -z_max step up by
  * kappa*phi inside the domain (kappa = 1/sqrt(3): the trilinear interpolant of a
  * 1-Lipschitz field is at most sqrt(3)-Lipschitz, so the step cannot pass the surface)
- * or by the box distance outside it, never less than voxel/8; the first sample with
- * phi <= 0 closes a bracket that ORC_BISECT halvings shrink; z_hit is its upper end. */
+ * or by the box distance outside it, never less than voxel/8; the first sample inside
+ * the object closes a bracket that is halved until it is at most voxel * 2^-16 wide;
+ * z_hit is its upper end. */
 static int column_hit(const orc_sdf* s, const double R[3][3], const double t[3], double px, double py,
                       double z_max, double* z_hit) {
     const double dmin = (double)s->voxel / 8.0;
@@ -373,7 +376,7 @@ static int column_hit(const orc_sdf* s, const double R[3][3], const double t[3],
     double z = -z_max;
     COLUMN_POINT(z);
     double phi = column_phi_obj(s, x, &inside);
-    if (phi <= 0.0) { *z_hit = z; return 1; }   /* the object reaches below -z_max */
+    if (inside && phi <= 0.0) { *z_hit = z; return 1; }   /* the object reaches below -z_max */
     for (int it = 0; it < ORC_MARCH_MAX; ++it) {
         double step = inside ? kappa * phi : phi;
         if (step < dmin) step = dmin;
@@ -382,13 +385,15 @@ static int column_hit(const orc_sdf* s, const double R[3][3], const double t[3],
         COLUMN_POINT(zn);
         int inside_n;
         const double phin = column_phi_obj(s, x, &inside_n);
-        if (phin <= 0.0) {
+        if (inside_n && phin <= 0.0) {
             double lo = z, hi = zn;
-            for (int k = 0; k < ORC_BISECT; ++k) {
+            const double eps = (double)s->voxel / 65536.0;
+            for (int k = 0; k < ORC_BISECT_MAX && hi - lo > eps; ++k) {
                 const double mid = 0.5 * (lo + hi);
                 COLUMN_POINT(mid);
                 int im;
-                if (column_phi_obj(s, x, &im) <= 0.0) hi = mid; else lo = mid;
+                const double pm = column_phi_obj(s, x, &im);
+                if (im && pm <= 0.0) hi = mid; else lo = mid;
             }
             *z_hit = hi;
             return 1;

@@ -9,7 +9,7 @@ module raises instead of falling back.
 
 Entry points (same names as the C ABI, without the ``tacsl_`` prefix):
 ``sdf_query``, ``penalty_forces``, ``pad_wrench``, ``shade_image``, ``tactile_step``,
-``check_errors``.
+``render_depth``, ``render_step``, ``check_errors``.
 """
 from __future__ import annotations
 
@@ -18,8 +18,9 @@ import os
 
 import torch
 
-__all__ = ["SdfSet", "ContactParams", "Shading", "TacslError", "sdf_query", "penalty_forces",
-           "pad_wrench", "shade_image", "tactile_step", "check_errors", "library_path", "load"]
+__all__ = ["SdfSet", "ContactParams", "Shading", "Camera", "TacslError", "sdf_query", "penalty_forces",
+           "pad_wrench", "shade_image", "tactile_step", "render_depth", "render_step", "check_errors",
+           "library_path", "load"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "libtacsl.so")
@@ -50,6 +51,11 @@ class _SdfSet(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("k_n", C.c_void_p), ("k_d", C.c_void_p), ("k_t", C.c_void_p), ("mu", C.c_void_p),
                 ("count", C.c_int32)]
+
+
+class _Camera(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("pitch_x", C.c_float), ("pitch_y", C.c_float),
+                ("x0", C.c_float), ("y0", C.c_float), ("d0", C.c_float), ("z_max", C.c_float)]
 
 
 class _Shading(C.Structure):
@@ -87,6 +93,11 @@ def load():
         lib.tacsl_tactile_step.restype = C.c_int
         lib.tacsl_tactile_step.argtypes = [C.POINTER(_SdfSet), C.POINTER(_Params), I32, I32, I32, P, P, P, P,
                                            P, P, P, P, C.POINTER(_Shading), P, P, P, P]
+        lib.tacsl_render_depth.restype = C.c_int
+        lib.tacsl_render_depth.argtypes = [C.POINTER(_SdfSet), I32, I32, P, P, C.POINTER(_Camera), P, P]
+        lib.tacsl_render_step.restype = C.c_int
+        lib.tacsl_render_step.argtypes = [C.POINTER(_SdfSet), C.POINTER(_Params), I32, I32, I32, P, P, P, P,
+                                          P, P, P, P, C.POINTER(_Shading), C.POINTER(_Camera), P, P, P, P]
         _lib = lib
     return _lib
 
@@ -259,3 +270,48 @@ def tactile_step(sdfs: SdfSet, params: ContactParams, taxels, obj_id, pad_pose, 
                                      _ptr(depth_map) if shading is not None else None,
                                      _ptr(rgb) if shading is not None else None, _stream(stream)))
     return depth, f_n, f_t, wrench, rgb
+
+
+class Camera:
+    """Orthographic column camera of the depth renderer (see tacsl_camera)."""
+
+    def __init__(self, H, W, pitch_x, pitch_y, x0, y0, d0, z_max):
+        self.H, self.W = int(H), int(W)
+        self.c = _Camera(self.H, self.W, float(pitch_x), float(pitch_y), float(x0), float(y0), float(d0),
+                         float(z_max))
+
+
+def render_depth(sdfs: SdfSet, camera: Camera, obj_id, pad_pose, depth_map=None, stream=None):
+    """Depth maps [E, P, H, W] of E x P pads."""
+    _dev(obj_id, torch.int32, "obj_id")
+    _dev(pad_pose, torch.float32, "pad_pose")
+    E, P = pad_pose.shape[0], pad_pose.shape[1]
+    if depth_map is None:
+        depth_map = torch.empty(E, P, camera.H, camera.W, dtype=torch.float32, device=pad_pose.device)
+    _check(load().tacsl_render_depth(C.byref(sdfs.c), E, P, _ptr(obj_id), _ptr(pad_pose), C.byref(camera.c),
+                                     _ptr(depth_map), _stream(stream)))
+    return depth_map
+
+
+def render_step(sdfs: SdfSet, params: ContactParams, taxels, obj_id, pad_pose, pad_twist, shading: Shading,
+                camera: Camera, sensor_id, depth_map=None, depth=None, f_n=None, f_t=None, wrench=None, rgb=None,
+                with_wrench=True, stream=None):
+    """Depth maps rendered from the poses, their RGB images and the force field, one call.
+
+    Returns (depth, f_n, f_t, wrench, depth_map, rgb)."""
+    for t, n, dt in ((taxels, "taxels", torch.float32), (obj_id, "obj_id", torch.int32),
+                     (pad_pose, "pad_pose", torch.float32), (pad_twist, "pad_twist", torch.float32),
+                     (sensor_id, "sensor_id", torch.int32)):
+        _dev(t, dt, n)
+    E, P = pad_pose.shape[0], pad_pose.shape[1]
+    T = taxels.shape[0]
+    depth, f_n, f_t, wrench = _force_outputs(E, P, T, pad_pose.device, depth, f_n, f_t, wrench, with_wrench)
+    if depth_map is None:
+        depth_map = torch.empty(E, P, camera.H, camera.W, dtype=torch.float32, device=pad_pose.device)
+    if rgb is None:
+        rgb = torch.empty(E * P, shading.H, shading.W, 3, dtype=torch.uint8, device=pad_pose.device)
+    _check(load().tacsl_render_step(C.byref(sdfs.c), C.byref(params.c), E, P, T, _ptr(taxels), _ptr(obj_id),
+                                    _ptr(pad_pose), _ptr(pad_twist), _ptr(depth), _ptr(f_n), _ptr(f_t), _ptr(wrench),
+                                    C.byref(shading.c), C.byref(camera.c), _ptr(sensor_id), _ptr(depth_map),
+                                    _ptr(rgb), _stream(stream)))
+    return depth, f_n, f_t, wrench, depth_map, rgb

@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "render.cuh"
 #include "shade.cuh"
 #include "taxel.cuh"
 
@@ -235,6 +236,35 @@ int launch_penalty(const SdfTable& tab, const Params4& prm, int64_t B, int P, in
 }  // namespace
 }  // namespace tacsl
 
+namespace tacsl {
+namespace {
+
+int check_camera(const tacsl_camera* cam, CameraArgs& c) {
+    if (cam == nullptr) return fail(TACSL_ERR_INVALID_ARG, "camera is NULL");
+    if (cam->H < 1 || cam->W < 4 || cam->W % 4 != 0)
+        return fail(TACSL_ERR_INVALID_ARG, "camera %d x %d: need H >= 1 and W a positive multiple of 4", cam->H, cam->W);
+    if ((int64_t)cam->H * cam->W >= (int64_t(1) << 28)) return fail(TACSL_ERR_UNSUPPORTED, "camera image too large");
+    const float v[] = {cam->pitch_x, cam->pitch_y, cam->x0, cam->y0, cam->d0, cam->z_max};
+    for (float x : v)
+        if (!std::isfinite(x)) return fail(TACSL_ERR_INVALID_ARG, "camera parameters must be finite");
+    if (!(cam->pitch_x > 0.f) || !(cam->pitch_y > 0.f) || !(cam->z_max > 0.f))
+        return fail(TACSL_ERR_INVALID_ARG, "camera pitches and z_max must be positive");
+    c = CameraArgs{cam->H, cam->W, cam->pitch_x, cam->pitch_y, cam->x0, cam->y0, cam->d0, cam->z_max};
+    return TACSL_OK;
+}
+
+int launch_render(const SdfTable& tab, int64_t B, int P, const int32_t* obj_id, const float* pad_pose,
+                  const CameraArgs& c, float* depth_map, const DevInfo& dev, tacsl_stream_t stream) {
+    const int64_t n = B * c.H * c.W;
+    const int64_t blocks = (n + 255) / 256;
+    const int grid = static_cast<int>(blocks < (int64_t)dev.sms * 64 ? blocks : (int64_t)dev.sms * 64);
+    render_kernel<<<grid, 256, 0, stream>>>(tab, B, P, obj_id, pad_pose, c, depth_map);
+    return check_launch("render kernel");
+}
+
+}  // namespace
+}  // namespace tacsl
+
 using namespace tacsl;
 
 extern "C" {
@@ -359,6 +389,58 @@ int tacsl_tactile_step(const tacsl_sdf_set* set, const tacsl_contact_params* par
     // The image kernel wants ~all of shared memory for its stage ring and coefficient
     // tile; the force field's scattered SDF gathers want a large L1.  Two launches, each
     // with its own carve-out, beat one persistent kernel doing both.
+    return launch_penalty(tab, prm, B, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t, wrench, *dev,
+                          stream);
+}
+
+int tacsl_render_depth(const tacsl_sdf_set* set, int32_t E, int32_t P, const int32_t* obj_id, const float* pad_pose,
+                       const tacsl_camera* camera, float* depth_map, tacsl_stream_t stream) {
+    SdfTable tab;
+    int rc = build_table(set, tab);
+    if (rc) return rc;
+    CameraArgs c;
+    if ((rc = check_camera(camera, c))) return rc;
+    if (E < 0 || P < 0) return fail(TACSL_ERR_INVALID_ARG, "negative size (E=%d P=%d)", E, P);
+    if ((int64_t)E * P == 0) return ok();
+    if ((int64_t)E * P >= (int64_t(1) << 31)) return fail(TACSL_ERR_UNSUPPORTED, "E*P >= 2^31 pads");
+    if (obj_id == nullptr || !aligned(obj_id, 4) || pad_pose == nullptr || !aligned(pad_pose, 4))
+        return fail(TACSL_ERR_INVALID_ARG, "obj_id and pad_pose must be non-NULL and 4-byte aligned");
+    if (depth_map == nullptr || !aligned(depth_map, 16))
+        return fail(TACSL_ERR_INVALID_ARG, "depth_map must be non-NULL and 16-byte aligned");
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    return launch_render(tab, (int64_t)E * P, P, obj_id, pad_pose, c, depth_map, *dev, stream);
+}
+
+int tacsl_render_step(const tacsl_sdf_set* set, const tacsl_contact_params* params, int32_t E, int32_t P, int32_t T,
+                      const float* taxels, const int32_t* obj_id, const float* pad_pose, const float* pad_twist,
+                      float* depth, float* f_n, float* f_t, float* wrench, const tacsl_shading* shading,
+                      const tacsl_camera* camera, const int32_t* sensor_id, float* depth_map, uint8_t* rgb,
+                      tacsl_stream_t stream) {
+    SdfTable tab;
+    Params4 prm;
+    int rc = build_table(set, tab);
+    if (rc) return rc;
+    if ((rc = build_params(params, E, prm))) return rc;
+    CameraArgs c;
+    if ((rc = check_camera(camera, c))) return rc;
+    if (E < 0 || P < 0 || T < 0) return fail(TACSL_ERR_INVALID_ARG, "negative size (E=%d P=%d T=%d)", E, P, T);
+    if ((int64_t)E * P == 0) return ok();
+    if (T > 0 && (rc = check_forces_args(E, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t))) return rc;
+    if (wrench != nullptr && !aligned(wrench, 4)) return fail(TACSL_ERR_INVALID_ARG, "wrench not 4-byte aligned");
+    if (obj_id == nullptr || pad_pose == nullptr) return fail(TACSL_ERR_INVALID_ARG, "obj_id / pad_pose is NULL");
+    const int64_t B = (int64_t)E * P;
+    if ((rc = check_shade_args(shading, B, sensor_id, depth_map, rgb))) return rc;
+    if (shading->H != c.H || shading->W != c.W)
+        return fail(TACSL_ERR_INVALID_ARG, "camera %d x %d differs from the shading model %d x %d", c.H, c.W,
+                    shading->H, shading->W);
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    ShadePlan plan;
+    if ((rc = plan_shade(shading, B, sensor_id, depth_map, rgb, *dev, plan))) return rc;
+    if ((rc = launch_render(tab, B, P, obj_id, pad_pose, c, depth_map, *dev, stream))) return rc;
+    if ((rc = launch_shade(plan, *dev, stream))) return rc;
+    if (T == 0) return ok();
     return launch_penalty(tab, prm, B, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t, wrench, *dev,
                           stream);
 }

@@ -1,0 +1,117 @@
+"""GPU parity of depth-map rendering (the column march of the in-sensor camera,
+Sec. III-B) against the FP64 oracle, and of the render-from-poses step."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2408_06506_b300 as tacsl
+from paper_2408_06506_b300 import synth
+
+from gpu_common import DEPTH_ATOL, dev, scene_to_device
+
+pytestmark = pytest.mark.gpu
+TANGENT_PHI = 2e-6     # a column this close to the surface may flip hit/miss or move the hit
+MAX_TANGENT_FRAC = 5e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_06506_b300 import build
+    build.build()
+    tacsl.load()
+    tacsl.check_errors(clear=True)
+
+
+def _camera(sc, z_max=3e-3):
+    ext_x, ext_y = sc.pitch_x * sc.W, sc.pitch_y * sc.H
+    return dict(H=sc.H, W=sc.W, pitch_x=sc.pitch_x, pitch_y=sc.pitch_y, x0=-ext_x / 2 + 0.5 * sc.pitch_x,
+                y0=-ext_y / 2 + 0.5 * sc.pitch_y, d0=synth.D0, z_max=z_max)
+
+
+def _gpu_phi_at(sdfs, sc, b, zs, ii, jj, cam):
+    """phi the GPU sees at pad-frame column points (x_i, y_j, z) of pad b."""
+    e = b // sc.P
+    pose = sc.pad_pose.reshape(-1, 7)[b].astype(np.float64)
+    R = synth.quat_to_matrix(pose[3:])
+    p = np.stack([cam["x0"] + ii * cam["pitch_x"], cam["y0"] + jj * cam["pitch_y"], zs], -1) @ R.T + pose[:3]
+    ids = np.full(len(zs), sc.obj_id[e], np.int32)
+    phi, _ = tacsl.sdf_query(sdfs, dev(p.astype(np.float32)), dev(ids))
+    return phi.cpu().numpy().astype(np.float64)
+
+
+def _check_render(orc, sc, sdfs, D_gpu, cam):
+    D_ref, bad = orc.render_depth(sc.grids, sc.obj_id, sc.pad_pose, cam["H"], cam["W"], cam["pitch_x"],
+                                  cam["pitch_y"], cam["x0"], cam["y0"], cam["d0"], cam["z_max"])
+    D_gpu = D_gpu.reshape(D_ref.shape).astype(np.float64)
+    nan = np.isnan(D_ref)
+    assert np.array_equal(np.isnan(D_gpu), nan)
+    diff = np.abs(np.where(nan, 0, D_gpu - D_ref))
+    off = diff > DEPTH_ATOL
+    n_off = int(off.sum())
+    assert n_off <= MAX_TANGENT_FRAC * D_ref.size, f"{n_off} pixels off"
+    # every disagreement must be a near-tangent column: each side's hit point lies on the
+    # surface as seen by the other side
+    d0 = np.float64(np.float32(cam["d0"]))
+    for idx in zip(*np.nonzero(off.reshape(-1, cam["H"], cam["W"]))):
+        b, j, i = (int(v) for v in idx)
+        e = b // sc.P
+        grid = sc.grids[sc.obj_id[e]]
+        pose = sc.pad_pose.reshape(-1, 7)[b]
+        zg = -(d0 - D_gpu.reshape(-1, cam["H"], cam["W"])[b, j, i])
+        zr = -(d0 - D_ref.reshape(-1, cam["H"], cam["W"])[b, j, i])
+        x, y = cam["x0"] + i * cam["pitch_x"], cam["y0"] + j * cam["pitch_y"]
+        if zg < 0:
+            assert orc.column_phi(grid, pose, x, y, zg) <= TANGENT_PHI
+        if zr < 0:
+            assert _gpu_phi_at(sdfs, sc, b, np.array([zr]), np.array([i]), np.array([j]), cam)[0] <= TANGENT_PHI
+    return n_off
+
+
+def test_render_sphere_pads(orc):
+    sc = synth.scene_sphere_pad(seed=11, E=16)
+    d = scene_to_device(sc)
+    cam = _camera(sc)
+    D = tacsl.render_depth(d["sdfs"], tacsl.Camera(**cam), d["obj_id"], d["pose"])
+    _check_render(orc, sc, d["sdfs"], D.cpu().numpy(), cam)
+    assert tacsl.check_errors() == 0
+
+
+@pytest.mark.parametrize("H,W", [(24, 32), (1, 64), (7, 4), (60, 80)])
+def test_render_objects(orc, H, W):
+    sc = synth.scene_objects(seed=12, E=24, P=2, n=48, H=H, W=W)
+    d = scene_to_device(sc)
+    cam = _camera(sc, z_max=2.5e-3)
+    D = tacsl.render_depth(d["sdfs"], tacsl.Camera(**cam), d["obj_id"], d["pose"])
+    _check_render(orc, sc, d["sdfs"], D.cpu().numpy(), cam)
+
+
+def test_render_bad_obj_id(orc):
+    sc = synth.scene_objects(seed=13, E=4, P=2, n=32, H=8, W=12)
+    ids = sc.obj_id.copy()
+    ids[2] = -7
+    d = scene_to_device(sc)
+    cam = _camera(sc)
+    D = tacsl.render_depth(d["sdfs"], tacsl.Camera(**cam), dev(ids), d["pose"]).cpu().numpy()
+    assert np.isnan(D[2]).all() and not np.isnan(D[1]).any()
+    assert tacsl.check_errors() == tacsl.DEVERR_BAD_OBJ_ID
+
+
+def test_render_step_equals_render_then_step(orc):
+    sc = synth.scene_objects(seed=14, E=40, P=2, n=48, H=24, W=32)
+    d = scene_to_device(sc)
+    cam = tacsl.Camera(**_camera(sc))
+    depth, fn, ft, wr, dmap, rgb = tacsl.render_step(d["sdfs"], d["params"], d["taxels"], d["obj_id"], d["pose"],
+                                                     d["twist"], d["shading"], cam, d["sensor_id"])
+    dmap2 = tacsl.render_depth(d["sdfs"], cam, d["obj_id"], d["pose"])
+    o = tacsl.tactile_step(d["sdfs"], d["params"], d["taxels"], d["obj_id"], d["pose"], d["twist"], d["shading"],
+                           d["sensor_id"], dmap2)
+    assert torch.equal(dmap, dmap2)
+    for a, b in zip((depth, fn, ft, wr, rgb), o):
+        assert torch.equal(a, b.view_as(a))
+    # and the rendered images shade like the oracle's shading of the same maps
+    from gpu_common import assert_rgb_close
+    ref_rgb, ref_I, _ = orc.shade(sc.coeffs, sc.pitch_x, sc.pitch_y, sc.sensor_id, dmap.cpu().numpy(),
+                                  with_intensity=True)
+    assert_rgb_close(rgb.cpu().numpy(), ref_rgb, ref_I)

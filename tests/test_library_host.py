@@ -201,3 +201,32 @@ def test_binding_refuses_cpu_tensors():
     import torch
     with pytest.raises(TypeError):
         tacsl.sdf_query(None, torch.zeros(3, 3), torch.zeros(3, dtype=torch.int32))
+
+
+def _camera(H=8, W=16, px=1e-4, py=1e-4, z_max=3e-3, d0=0.02):
+    return tacsl._Camera(H, W, px, py, -8e-4, -4e-4, d0, z_max)
+
+
+@pytest.mark.parametrize("cam_kw,code", [
+    (dict(W=18), INVALID), (dict(H=0), INVALID), (dict(px=0.0), INVALID), (dict(z_max=0.0), INVALID),
+    (dict(d0=float("inf")), INVALID), (dict(H=1 << 15, W=1 << 14), UNSUPPORTED),
+])
+def test_render_depth_rejects(lib, cam_kw, code):
+    st, cam = _set(_sdf()), _camera(**cam_kw)
+    assert lib.tacsl_render_depth(C.byref(st), 2, 2, FAKE, FAKE, C.byref(cam), FAKE, None) == code
+
+
+def test_render_depth_rejects_pointers(lib):
+    st, cam = _set(_sdf()), _camera()
+    assert lib.tacsl_render_depth(C.byref(st), 2, 2, FAKE, FAKE, C.byref(cam), FAKE + 4, None) == INVALID
+    assert lib.tacsl_render_depth(C.byref(st), 2, 2, 0, FAKE, C.byref(cam), FAKE, None) == INVALID
+    assert lib.tacsl_render_depth(C.byref(st), 2, 2, FAKE, FAKE, None, FAKE, None) == INVALID
+    assert lib.tacsl_render_depth(C.byref(st), 0, 2, FAKE, FAKE, C.byref(cam), FAKE, None) == 0
+
+
+def test_render_step_requires_matching_camera(lib):
+    st, prm, cam = _set(_sdf()), _params(), _camera(H=8, W=16)
+    sh = _shading(H=12, W=16)
+    rc = lib.tacsl_render_step(C.byref(st), C.byref(prm), 2, 2, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE,
+                               C.byref(sh), C.byref(cam), FAKE, FAKE, FAKE, None)
+    assert rc == INVALID and "camera" in lib.tacsl_last_error().decode()

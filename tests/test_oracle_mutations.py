@@ -51,8 +51,8 @@ MUTATIONS = {
                                   "const double px = (double)cam->x0 + (double)j * (double)cam->pitch_x;"),
     "render_depth_sign": ("D[(int64_t)j * cam->W + i] = (double)cam->d0 - (hit && zh < 0.0 ? -zh : 0.0);",
                           "D[(int64_t)j * cam->W + i] = (double)cam->d0 + (hit && zh < 0.0 ? -zh : 0.0);"),
-    "render_bisection_reversed": ("if (column_phi_obj(s, x, &im) <= 0.0) hi = mid; else lo = mid;",
-                                  "if (column_phi_obj(s, x, &im) > 0.0) hi = mid; else lo = mid;"),
+    "render_bisection_reversed": ("if (im && pm <= 0.0) hi = mid; else lo = mid;",
+                                  "if (im && pm > 0.0) hi = mid; else lo = mid;"),
 }
 
 PINS = os.path.join(os.path.dirname(__file__), "test_oracle_pins.py")
