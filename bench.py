@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--batch-envs", type=int, default=16384)
+    ap.add_argument("--batch-steps", type=int, default=100)
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -395,6 +398,8 @@ def run_ours(args, rank, world, local_rank, dist):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                "path": "pinned host -> cudaMemcpyAsync -> tacsl_tactile_step -> pinned host, one stream"}
 
+    batch = None if args.no_batch else run_batch(args, rank, world, local_rank, dist)
+
     if rank != 0:
         return
     # ---- roofline of the step kernel (the only kernel of a step) ----
@@ -444,11 +449,171 @@ def run_ours(args, rank, world, local_rank, dist):
         "clocks": clk.summary(),
         "breakdown": breakdown,
         "render_step": render,
+        "batch": batch,
         "gpu_launches": 2 * args.steps,
         "cpu_baseline": cpu,
         "e2e": e2e,
     }
     print(json.dumps(line), flush=True)
+
+
+BATCH_WORKLOAD = ("16384 envs x 2 pads; pad resolution 10x12..40x50, SDF from a pool of 32 grids 32^3..256^3, "
+                  "image 160x120..640x480 (16 size classes x left/right models), all log-uniform per env")
+
+
+def run_batch(args, rank, world, local_rank, dist):
+    """The uneven workload: every env with its own pad resolution, object grid and image
+    size, as one autotuned two-launch step replayed from a CUDA graph; the same work
+    through the uniform entry points, one launch per homogeneous group, beside it."""
+    import torch
+
+    import paper_2408_06506_b300 as tacsl
+    from paper_2408_06506_b300 import batch as tb
+    from paper_2408_06506_b300 import synth
+    from paper_2408_06506_b300.dist import max_over_ranks
+
+    t_gen = time.perf_counter()
+    grids = synth.grid_pool(args.seed + 101, 32, 32, 256)
+    sc = synth.scene_batch(seed=args.seed + 100 + rank, E=args.batch_envs, P=2, grids=grids, depth_maps="cycled",
+                           n_distinct_maps=4)
+    t_gen = time.perf_counter() - t_gen
+
+    def dev(a):
+        return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+    sdfs = tacsl.SdfSet.from_grids(sc.grids)
+    params = tacsl.ContactParams(dev(sc.k_n), dev(sc.k_d), dev(sc.k_t), dev(sc.mu))
+    sensors = tb.SensorSet([(dev(co), px, py) for co, px, py in sc.models])
+    plan = tb.BatchPlan(sc.obj_id, sc.layout, sc.sensor, sc.layout_first, sc.layout_count, sensors)
+    taxels, pose, twist = dev(sc.taxels), dev(sc.pad_pose), dev(sc.pad_twist)
+    depth_map = torch.empty(plan.n_pixel_out, dtype=torch.float32, device="cuda")
+    distinct = {}
+    for b in range(sc.n_pad):
+        m = sc.depth_maps[b]
+        if m is not None:
+            src = distinct.setdefault(id(m), dev(m.reshape(-1)))
+            q = int(plan.pixel_offset[b])
+            depth_map[q:q + m.size].copy_(src)
+    out = plan.outputs()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n, warm=2):
+        for _ in range(warm):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    default_ms = timed(lambda: plan.step(sdfs, params, taxels, pose, twist, depth_map, out=out), 10)
+    t_tune = time.perf_counter()
+    tuned_ms = plan.autotune(sdfs, params, taxels, pose, twist, depth_map, out=out, reps=3)
+    t_tune = time.perf_counter() - t_tune
+    graph = plan.graph(sdfs, params, taxels, pose, twist, depth_map, out)
+    for _ in range(max(3, args.warmup)):
+        graph.launch()
+    torch.cuda.synchronize()
+    assert tacsl.check_errors() == 0
+    K = args.batch_steps
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(_smi_id(local_rank)) as clk:
+        ev0.record(stream)
+        for _ in range(K):
+            graph.launch()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1), dist, device="cuda") / K
+    graph.close()
+    shade_ms = timed(lambda: plan.shade(depth_map, rgb=out["rgb"]), 20)
+    forces_ms = timed(lambda: plan.forces(sdfs, params, taxels, pose, twist, out=out), 20)
+
+    # ---- the same work through the uniform entry points: one launch per pad resolution
+    # (forces) and per sensor model (images), inputs regrouped before timing ----
+    groups = []
+    for l in range(len(sc.layout_count)):
+        pads = np.flatnonzero(sc.layout == l)
+        if len(pads) == 0:
+            continue
+        T = int(sc.layout_count[l])
+        first = int(sc.layout_first[l])
+        n = len(pads)
+        idx = torch.as_tensor(pads, device="cuda")
+        prm = tacsl.ContactParams(*[dev(v[pads]) for v in (sc.k_n, sc.k_d, sc.k_t, sc.mu)])
+        groups.append(dict(tax=taxels[first:first + T], obj=dev(sc.obj_id[pads]), prm=prm,
+                           pose=pose[idx].reshape(n, 1, 7).contiguous(), twist=twist[idx].reshape(n, 1, 6).contiguous(),
+                           depth=torch.empty(n, 1, T, device="cuda"), f_n=torch.empty(n, 1, T, 3, device="cuda"),
+                           f_t=torch.empty(n, 1, T, 3, device="cuda"), wrench=torch.empty(n, 1, 6, device="cuda")))
+    img_groups = []
+    for m, (co, px, py) in enumerate(sc.models):
+        pads = np.flatnonzero(sc.sensor == m)
+        if len(pads) == 0:
+            continue
+        H, W = co.shape[2], co.shape[3]
+        dm = torch.empty(len(pads), H, W, device="cuda")
+        for i, b in enumerate(pads):
+            q = int(plan.pixel_offset[b])
+            dm[i].view(-1).copy_(depth_map[q:q + H * W])
+        img_groups.append(dict(sh=tacsl.Shading(sensors.tensors[m][None], px, py),
+                               sid=torch.zeros(len(pads), dtype=torch.int32, device="cuda"), dm=dm,
+                               rgb=torch.empty(len(pads), H, W, 3, dtype=torch.uint8, device="cuda")))
+
+    def grouped_step():
+        for g in img_groups:
+            tacsl.shade_image(g["sh"], g["sid"], g["dm"], rgb=g["rgb"])
+        for g in groups:
+            tacsl.penalty_forces(sdfs, g["prm"], g["tax"], g["obj"], g["pose"], g["twist"], depth=g["depth"],
+                                 f_n=g["f_n"], f_t=g["f_t"], wrench=g["wrench"])
+
+    grouped_ms = timed(grouped_step, 5, warm=1)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        grouped_step()
+    torch.cuda.synchronize()
+    grouped_wall_ms = 1e3 * (time.perf_counter() - t0) / 3
+    del img_groups, groups
+
+    # ---- roofline of the dominant launch (the batched image kernel) ----
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = float(json.load(open(peaks_path))["hbm_gbs"]) if os.path.exists(peaks_path) else 6400.0
+    npx = plan.n_pixel_out
+    coef_bytes = sum(72 * co.shape[2] * co.shape[3] for co, _, _ in sc.models)
+    img_bytes = 7 * npx + coef_bytes
+    nt = plan.n_taxel_out
+    force_bytes = 28 * nt + 12 * nt + 52 * sc.n_pad + 24 * sc.n_pad + 16 * sc.n_pad   # outputs, taxel reads, pads
+    taxel_pts = world * nt
+    images = world * plan.plan.n_image
+    return {
+        "workload": BATCH_WORKLOAD, "envs_per_gpu": args.batch_envs, "pads_per_gpu": sc.n_pad,
+        "taxel_points_per_gpu": int(nt), "images_per_gpu": int(plan.plan.n_image), "pixels_per_gpu": int(npx),
+        "distinct_layouts": len(sc.layout_count), "sensor_models": len(sc.models),
+        "sdf_sides": sorted(int(g.data.shape[0]) for g in sc.grids),
+        "steps": K, "ms_per_step": ms_step, "launch": "CUDA graph of tacsl_batch_step (2 kernels)",
+        "value": taxel_pts / (ms_step * 1e-3), "unit": "taxel-points/s",
+        "images_per_s": images / (ms_step * 1e-3), "pixels_per_s": world * npx / (ms_step * 1e-3),
+        "default_config_ms": default_ms, "tuned_config": plan.config(), "autotune_estimate_ms": tuned_ms,
+        "autotune_s": t_tune, "generation_s": t_gen,
+        "kernel_ms": {"batch_shade_kernel": shade_ms, "batch_force_kernel": forces_ms},
+        "roofline": {"bound": "hbm", "kernel": "tacsl::batch_shade_kernel", "algorithmic_bytes": img_bytes,
+                     "achieved": img_bytes / (shade_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": img_bytes / (shade_ms * 1e-3) / 1e9 / peak},
+        "roofline_step": {"algorithmic_bytes": img_bytes + force_bytes,
+                          "frac": (img_bytes + force_bytes) / (ms_step * 1e-3) / 1e9 / peak},
+        "plain_grouped": {"launches_per_step": len(sc.models) + len(sc.layout_count), "ms_per_step": grouped_ms,
+                          "wall_ms_per_step": grouped_wall_ms,
+                          "value": taxel_pts / (grouped_ms * 1e-3), "speedup_of_batch": grouped_ms / ms_step,
+                          "path": "tacsl_shade_image per sensor model + tacsl_penalty_forces per pad resolution"},
+        "clocks": clk.summary(),
+        "l2": f"no flush: every step streams {(img_bytes + force_bytes) / 1e9:.1f} GB",
+    }
 
 
 def _smi_id(ordinal):

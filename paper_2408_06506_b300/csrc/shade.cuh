@@ -272,6 +272,178 @@ __device__ __forceinline__ void shade_producer(const ShadeArgs& A, unsigned char
     }
 }
 
+// ---------------------------------------------------------------------------
+// Compute-warp building blocks (shared by the uniform and the batched kernel)
+// ---------------------------------------------------------------------------
+
+// Where this thread's four pixels of one tile and their neighbours sit in a stage
+// buffer (the tile plus one halo row above and below), and the derivative scales at
+// those pixels: central differences inside, one-sided ones on the image border.
+struct TileGeom {
+    int tile_start, warp_px;
+    int oc, ou, od, oL, oR;
+    f2 cxp0, cxp1, cyy;
+    bool px_valid, hasL, hasR;
+};
+
+__device__ __forceinline__ void tile_geometry(int H, int W, int HW, int tile, float cx_c, float cx_e, float cy_c,
+                                              float cy_e, int stage_floats, int tid, int warp, TileGeom& g) {
+    g.tile_start = tile * kShTile;
+    const int tile_px = min(kShTile, HW - g.tile_start);
+    const int lo_px = max(g.tile_start - W, 0);
+    g.warp_px = min(max(tile_px - warp * kShWarpPx, 0), kShWarpPx);
+    g.px_valid = 4 * tid < tile_px;
+    const int p = g.tile_start + 4 * tid;
+    if (g.px_valid) {
+        const int y = p / W, x0 = p - y * W;
+        g.hasL = x0 > 0;
+        g.hasR = x0 + 4 < W;
+        g.oc = p - lo_px;
+        g.ou = ((y > 0) ? p - W : p) - lo_px;
+        g.od = ((y < H - 1) ? p + W : p) - lo_px;
+        g.oL = (g.hasL ? p - 1 : p) - lo_px;
+        g.oR = (g.hasR ? p + 4 : p + 3) - lo_px;
+        const float cyv = (y > 0 && y < H - 1) ? cy_c : cy_e;
+        g.cxp0 = pk(g.hasL ? cx_c : cx_e, cx_c);
+        g.cxp1 = pk(cx_c, g.hasR ? cx_c : cx_e);
+        g.cyy = pk(cyv, cyv);
+    } else {
+        // past the tile's end: read in-bounds stage words (the lane's natural position,
+        // which its left neighbour uses as the pixel after the tile) and store nothing
+        g.oc = min(p - lo_px, stage_floats - 4);
+        g.ou = g.od = g.oL = g.oR = g.oc;
+        g.hasL = g.hasR = true;
+        g.cxp0 = g.cxp1 = g.cyy = 0;
+    }
+}
+
+// The tile's 18 shading coefficients of this thread's four pixels, in registers, and the
+// RGB bytes of a flat neighbourhood.
+struct TileCoefs {
+    f2 cf[6][3][2];                   // term, channel, pixel pair
+    uint32_t bg0, bg1, bg2;           // RGB of a flat neighbourhood (n = (0, 0, -1))
+};
+
+__device__ __forceinline__ void take_coefficients(const float* coef, const TileGeom& g, int tid, TileCoefs& c) {
+    // coefficients in units of 1/256 with the rounding half folded into the bias:
+    // A0/256 + 1/512 and Ak/256 (exact power-of-two scaling)
+    const int q = g.px_valid ? 4 * tid : 0;
+    const f2 s256 = pk(0.00390625f, 0.00390625f), h512 = pk(0.001953125f, 0.001953125f);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(coef + (k * 3 + ch) * kShTile + q);
+            c.cf[k][ch][0] = k == 0 ? fma2(v.x, s256, h512) : mul2(v.x, s256);
+            c.cf[k][ch][1] = k == 0 ? fma2(v.y, s256, h512) : mul2(v.y, s256);
+        }
+    // a flat neighbourhood has m = (1, 0, 0, 0, 0, 0): the chain in shade_four then
+    // returns its bias term exactly, so the bytes are those of the bias alone
+    f2 qb[3][2];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            qb[ch][j] = floor256(__saturatef(lo(c.cf[0][ch][j])), __saturatef(hi(c.cf[0][ch][j])));
+    c.bg0 = pack_u8x4(__float_as_uint(lo(qb[0][0])), __float_as_uint(lo(qb[1][0])), __float_as_uint(lo(qb[2][0])),
+                      __float_as_uint(hi(qb[0][0])));
+    c.bg1 = pack_u8x4(__float_as_uint(hi(qb[1][0])), __float_as_uint(hi(qb[2][0])), __float_as_uint(lo(qb[0][1])),
+                      __float_as_uint(lo(qb[1][1])));
+    c.bg2 = pack_u8x4(__float_as_uint(lo(qb[2][1])), __float_as_uint(hi(qb[0][1])), __float_as_uint(hi(qb[1][1])),
+                      __float_as_uint(hi(qb[2][1])));
+}
+
+// RGB bytes of this thread's four pixels of the image in stage buffer sp, as three
+// words in memory order.  The warp arrives on the stage's empty barrier as soon as its
+// shared-memory reads are done.
+__device__ __forceinline__ void shade_four(const float* sp, const TileGeom& g, const TileCoefs& c, uint64_t* empty_bar,
+                                           int lane, uint32_t& w0, uint32_t& w1, uint32_t& w2) {
+    const f2 one2 = pk(1.f, 1.f);
+    const float4 cv = *reinterpret_cast<const float4*>(sp + g.oc);
+    const ulonglong2 up = *reinterpret_cast<const ulonglong2*>(sp + g.ou);
+    const ulonglong2 dn = *reinterpret_cast<const ulonglong2*>(sp + g.od);
+    float L = __shfl_up_sync(0xffffffffu, cv.w, 1);
+    float R = __shfl_down_sync(0xffffffffu, cv.x, 1);
+    if (lane == 0) L = sp[g.oL];
+    if (lane == 31) R = sp[g.oR];
+    L = g.hasL ? L : cv.x;
+    R = g.hasR ? R : cv.w;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(empty_bar));   // this warp is done with the stage
+
+    // depth differences of the pixel pairs (0,1) and (2,3)
+    const float ex0 = cv.y - L, ex1 = cv.z - cv.x, ex2 = cv.w - cv.y, ex3 = R - cv.z;
+    const f2 ey0 = sub2(dn.x, up.x), ey1 = sub2(dn.y, up.y);
+    // Exactness shortcut: where all four pixels see equal neighbours, D_x = D_y = 0,
+    // n = (0, 0, -1) and the shading is the bias term; the warp takes it when all of
+    // its lanes can (bitwise the bytes of the full evaluation).
+    const bool flat = ((__float_as_uint(ex0) | __float_as_uint(ex1) | __float_as_uint(ex2) | __float_as_uint(ex3) |
+                        static_cast<uint32_t>(ey0) | static_cast<uint32_t>(ey0 >> 32) | static_cast<uint32_t>(ey1) |
+                        static_cast<uint32_t>(ey1 >> 32)) &
+                       0x7fffffffu) == 0u;
+    w0 = c.bg0;
+    w1 = c.bg1;
+    w2 = c.bg2;
+    if (__all_sync(0xffffffffu, flat || !g.px_valid)) return;
+    const f2 gx0 = mul2(pk(ex0, ex1), g.cxp0);
+    const f2 gx1 = mul2(pk(ex2, ex3), g.cxp1);
+    const f2 gy0 = mul2(ey0, g.cyy);
+    const f2 gy1 = mul2(ey1, g.cyy);
+    f2 q[2][3];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const f2 gx = j ? gx1 : gx0, gy = j ? gy1 : gy0;
+        const f2 s2 = fma2(gx, gx, fma2(gy, gy, one2));
+        const f2 r = pk(rsqrt_ge1(lo(s2)), rsqrt_ge1(hi(s2)));
+        const f2 nx = mul2(gx, r), ny = mul2(gy, r);
+        const f2 m3 = mul2(nx, nx), m4 = mul2(ny, ny), m5 = mul2(nx, ny);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            // t = (I + 0.5)/256: four packed FMAs, the last term per lane with saturation
+            const f2 part = fma2(c.cf[4][ch][j], m4,
+                                 fma2(c.cf[3][ch][j], m3, fma2(c.cf[2][ch][j], ny, fma2(c.cf[1][ch][j], nx, c.cf[0][ch][j]))));
+            const float ta = __saturatef(fmaf(lo(c.cf[5][ch][j]), lo(m5), lo(part)));
+            const float tb = __saturatef(fmaf(hi(c.cf[5][ch][j]), hi(m5), hi(part)));
+            q[j][ch] = floor256(ta, tb);
+        }
+    }
+    // q[j][ch] holds pixels (2j, 2j+1); memory order is px0 rgb, px1 rgb, px2 rgb, px3 rgb
+    w0 = pack_u8x4(__float_as_uint(lo(q[0][0])), __float_as_uint(lo(q[0][1])), __float_as_uint(lo(q[0][2])),
+                   __float_as_uint(hi(q[0][0])));
+    w1 = pack_u8x4(__float_as_uint(hi(q[0][1])), __float_as_uint(hi(q[0][2])), __float_as_uint(lo(q[1][0])),
+                   __float_as_uint(lo(q[1][1])));
+    w2 = pack_u8x4(__float_as_uint(lo(q[1][2])), __float_as_uint(hi(q[1][0])), __float_as_uint(hi(q[1][1])),
+                   __float_as_uint(hi(q[1][2])));
+}
+
+// The warp's 128 pixels (384 bytes) starting at dst, 16-byte aligned: a transpose
+// through the warp's staging buffer, then one 16-byte store per lane.
+__device__ __forceinline__ void store_warp_vec(uint8_t* dst, uint8_t* staging, int lane, int warp_px, uint32_t w0,
+                                               uint32_t w1, uint32_t w2, uint64_t pol) {
+    uint32_t* sg = reinterpret_cast<uint32_t*>(staging);
+    sg[3 * lane] = w0;
+    sg[3 * lane + 1] = w1;
+    sg[3 * lane + 2] = w2;
+    __syncwarp();
+    if (lane * 16 < warp_px * 3) stg_v4_hint(dst + 16 * lane, reinterpret_cast<const uint4*>(sg)[lane], pol);
+}
+
+// Barrier set-up shared by both image kernels (thread 0, then a block barrier).
+__device__ __forceinline__ void shade_init_barriers(unsigned char* smem, int NS) {
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffFull);
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + kOffEmpty);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), kShConsumerWarps);
+        }
+        mbar_init(smem_u32(smem + kOffCoefFull), 1);
+        mbar_init(smem_u32(smem + kOffCoefEmpty), kShConsumerWarps);
+        mbar_fence_init();
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -284,17 +456,7 @@ __global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A)
     const float* stages = reinterpret_cast<const float*>(smem + kOffStage);
     const int NS = A.n_stages;
 
-    if (tid == 0) {
-        for (int s = 0; s < NS; ++s) {
-            mbar_init(smem_u32(&full[s]), 1);
-            mbar_init(smem_u32(&empty[s]), kShConsumerWarps);
-        }
-        mbar_init(smem_u32(cfull), 1);
-        mbar_init(smem_u32(cempty), kShConsumerWarps);
-        mbar_fence_init();
-    }
-    __syncthreads();
-
+    shade_init_barriers(smem, NS);
     if (warp == kShConsumerWarps) {
         shade_producer(A, smem);
         return;
@@ -303,15 +465,11 @@ __global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A)
     // ---- compute warps ----
     const uint64_t pol_stream = policy_evict_first();
     uint8_t* my_staging = smem + kOffStaging + warp * (kShStagingRing * kShWarpStaging);
-    f2 cf[6][3][2];                   // coefficients: term, channel, pixel pair
-    uint32_t bg0 = 0, bg1 = 0, bg2 = 0;   // RGB of a flat neighbourhood (n = (0, 0, -1))
-    int cur_item = -1, tile_start = 0, warp_px = 0;
-    int oc = 0, ou = 0, od = 0, oL = 0, oR = 0;
-    f2 cxp0 = 0, cxp1 = 0, cyy = 0;
-    bool px_valid = false, hasL = false, hasR = false;
+    TileGeom g;
+    TileCoefs c;
+    int cur_item = -1;
     int st = 0, wbuf = 0;
     uint32_t ph = 0, cph = 0;
-    const f2 one2 = pk(1.f, 1.f);
     for (;;) {
         if (!mbar_wait_bounded(smem_u32(&full[st]), ph)) {
             if (lane == 0) raise_dev_error(TACSL_DEVERR_TIMEOUT);
@@ -323,135 +481,25 @@ __global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A)
             // new item: geometry, then the tile's coefficients from shared memory
             cur_item = m.y;
             const Item it = decode_item(A, m.y);
-            tile_start = it.tile * kShTile;
-            const int tile_px = min(kShTile, A.HW - tile_start);
-            const int lo_px = max(tile_start - A.W, 0);
-            warp_px = min(max(tile_px - warp * kShWarpPx, 0), kShWarpPx);
-            px_valid = 4 * tid < tile_px;
-            const int p = tile_start + 4 * tid;
-            if (px_valid) {
-                const int y = p / A.W, x0 = p - y * A.W;
-                hasL = x0 > 0;
-                hasR = x0 + 4 < A.W;
-                oc = p - lo_px;
-                ou = ((y > 0) ? p - A.W : p) - lo_px;
-                od = ((y < A.H - 1) ? p + A.W : p) - lo_px;
-                oL = (hasL ? p - 1 : p) - lo_px;
-                oR = (hasR ? p + 4 : p + 3) - lo_px;
-                const float cyv = (y > 0 && y < A.H - 1) ? A.cy_c : A.cy_e;
-                cxp0 = pk(hasL ? A.cx_c : A.cx_e, A.cx_c);
-                cxp1 = pk(A.cx_c, hasR ? A.cx_c : A.cx_e);
-                cyy = pk(cyv, cyv);
-            } else {
-                // past the tile's end: read in-bounds stage words (the lane's natural position,
-                // which its left neighbour uses as the pixel after the tile) and store nothing
-                oc = min(p - lo_px, A.stage_floats - 4);
-                ou = od = oL = oR = oc;
-                hasL = hasR = true;
-            }
+            tile_geometry(A.H, A.W, A.HW, it.tile, A.cx_c, A.cx_e, A.cy_c, A.cy_e, A.stage_floats, tid, warp, g);
             if (!mbar_wait_bounded(smem_u32(cfull), cph)) {
                 if (lane == 0) raise_dev_error(TACSL_DEVERR_TIMEOUT);
                 break;
             }
             cph ^= 1u;
-            // coefficients in units of 1/256 with the rounding half folded into the bias:
-            // A0/256 + 1/512 and Ak/256 (exact power-of-two scaling)
-            const int q = px_valid ? 4 * tid : 0;
-            const f2 s256 = pk(0.00390625f, 0.00390625f), h512 = pk(0.001953125f, 0.001953125f);
-#pragma unroll
-            for (int k = 0; k < 6; ++k)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(coef + (k * 3 + c) * kShTile + q);
-                    cf[k][c][0] = k == 0 ? fma2(v.x, s256, h512) : mul2(v.x, s256);
-                    cf[k][c][1] = k == 0 ? fma2(v.y, s256, h512) : mul2(v.y, s256);
-                }
+            take_coefficients(coef, g, tid, c);
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(cempty));
-            // a flat neighbourhood has m = (1, 0, 0, 0, 0, 0): the chain below then returns
-            // its bias term exactly, so the bytes are those of the bias alone
-            f2 qb[3][2];
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch)
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-                    qb[ch][j] = floor256(__saturatef(lo(cf[0][ch][j])), __saturatef(hi(cf[0][ch][j])));
-            bg0 = pack_u8x4(__float_as_uint(lo(qb[0][0])), __float_as_uint(lo(qb[1][0])),
-                            __float_as_uint(lo(qb[2][0])), __float_as_uint(hi(qb[0][0])));
-            bg1 = pack_u8x4(__float_as_uint(hi(qb[1][0])), __float_as_uint(hi(qb[2][0])),
-                            __float_as_uint(lo(qb[0][1])), __float_as_uint(lo(qb[1][1])));
-            bg2 = pack_u8x4(__float_as_uint(lo(qb[2][1])), __float_as_uint(hi(qb[0][1])),
-                            __float_as_uint(hi(qb[1][1])), __float_as_uint(hi(qb[2][1])));
         }
-        const float* sp = stages + static_cast<int64_t>(st) * A.stage_floats;
-        const float4 c = *reinterpret_cast<const float4*>(sp + oc);
-        const ulonglong2 up = *reinterpret_cast<const ulonglong2*>(sp + ou);
-        const ulonglong2 dn = *reinterpret_cast<const ulonglong2*>(sp + od);
-        float L = __shfl_up_sync(0xffffffffu, c.w, 1);
-        float R = __shfl_down_sync(0xffffffffu, c.x, 1);
-        if (lane == 0) L = sp[oL];
-        if (lane == 31) R = sp[oR];
-        L = hasL ? L : c.x;
-        R = hasR ? R : c.w;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&empty[st]));   // this warp is done with the stage
-
-        // depth differences of the pixel pairs (0,1) and (2,3)
-        const float ex0 = c.y - L, ex1 = c.z - c.x, ex2 = c.w - c.y, ex3 = R - c.z;
-        const f2 ey0 = sub2(dn.x, up.x), ey1 = sub2(dn.y, up.y);
-        // Exactness shortcut: where all four pixels see equal neighbours, D_x = D_y = 0,
-        // n = (0, 0, -1) and the shading is the bias term; the warp takes it when all of
-        // its lanes can (bitwise the bytes of the full evaluation).
-        const bool flat = ((__float_as_uint(ex0) | __float_as_uint(ex1) | __float_as_uint(ex2) |
-                            __float_as_uint(ex3) | static_cast<uint32_t>(ey0) | static_cast<uint32_t>(ey0 >> 32) |
-                            static_cast<uint32_t>(ey1) | static_cast<uint32_t>(ey1 >> 32)) &
-                           0x7fffffffu) == 0u;
-        uint32_t w0 = bg0, w1 = bg1, w2 = bg2;
-        if (!__all_sync(0xffffffffu, flat || !px_valid)) {
-        const f2 gx0 = mul2(pk(ex0, ex1), cxp0);
-        const f2 gx1 = mul2(pk(ex2, ex3), cxp1);
-        const f2 gy0 = mul2(ey0, cyy);
-        const f2 gy1 = mul2(ey1, cyy);
-        f2 q[2][3];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const f2 gx = j ? gx1 : gx0, gy = j ? gy1 : gy0;
-            const f2 s2 = fma2(gx, gx, fma2(gy, gy, one2));
-            const f2 r = pk(rsqrt_ge1(lo(s2)), rsqrt_ge1(hi(s2)));
-            const f2 nx = mul2(gx, r), ny = mul2(gy, r);
-            const f2 m3 = mul2(nx, nx), m4 = mul2(ny, ny), m5 = mul2(nx, ny);
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                // t = (I + 0.5)/256: four packed FMAs, the last term per lane with saturation
-                const f2 part = fma2(cf[4][ch][j], m4, fma2(cf[3][ch][j], m3,
-                                                            fma2(cf[2][ch][j], ny, fma2(cf[1][ch][j], nx, cf[0][ch][j]))));
-                const float ta = __saturatef(fmaf(lo(cf[5][ch][j]), lo(m5), lo(part)));
-                const float tb = __saturatef(fmaf(hi(cf[5][ch][j]), hi(m5), hi(part)));
-                q[j][ch] = floor256(ta, tb);
-            }
-        }
-        // q[j][ch] holds pixels (2j, 2j+1); memory order is px0 rgb, px1 rgb, px2 rgb, px3 rgb
-        w0 = pack_u8x4(__float_as_uint(lo(q[0][0])), __float_as_uint(lo(q[0][1])), __float_as_uint(lo(q[0][2])),
-                       __float_as_uint(hi(q[0][0])));
-        w1 = pack_u8x4(__float_as_uint(hi(q[0][1])), __float_as_uint(hi(q[0][2])), __float_as_uint(lo(q[1][0])),
-                       __float_as_uint(lo(q[1][1])));
-        w2 = pack_u8x4(__float_as_uint(lo(q[1][2])), __float_as_uint(hi(q[1][0])), __float_as_uint(hi(q[1][1])),
-                       __float_as_uint(hi(q[1][2])));
-        }
+        uint32_t w0, w1, w2;
+        shade_four(stages + static_cast<int64_t>(st) * A.stage_floats, g, c, &empty[st], lane, w0, w1, w2);
         const int64_t img = m.x;
         if (A.store_mode == kStoreVec) {
-            // warp-local transpose through shared memory, then 16-byte stores
-            uint32_t* sg = reinterpret_cast<uint32_t*>(my_staging + wbuf * kShWarpStaging);
-            sg[3 * lane] = w0;
-            sg[3 * lane + 1] = w1;
-            sg[3 * lane + 2] = w2;
-            __syncwarp();
-            if (lane * 16 < warp_px * 3)
-                stg_v4_hint(A.rgb + (img * A.HW + tile_start + warp * kShWarpPx) * 3 + 16 * lane,
-                            reinterpret_cast<const uint4*>(sg)[lane], pol_stream);
+            store_warp_vec(A.rgb + (img * A.HW + g.tile_start + warp * kShWarpPx) * 3,
+                           my_staging + wbuf * kShWarpStaging, lane, g.warp_px, w0, w1, w2, pol_stream);
             wbuf ^= 1;
-        } else if (px_valid) {
-            uint8_t* dst = A.rgb + (img * A.HW + tile_start + 4 * tid) * 3;
+        } else if (g.px_valid) {
+            uint8_t* dst = A.rgb + (img * A.HW + g.tile_start + 4 * tid) * 3;
             if (A.store_mode == kStoreWord) {
                 uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
                 d32[0] = w0; d32[1] = w1; d32[2] = w2;
@@ -463,7 +511,6 @@ __global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A)
         }
         if (++st == NS) { st = 0; ph ^= 1u; }
     }
-
 }
 
 }  // namespace tacsl

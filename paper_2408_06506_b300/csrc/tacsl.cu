@@ -1,19 +1,26 @@
-// libtacsl.so -- host side of the C ABI declared in include/tacsl.h.
+// libtacsl.so -- host side of the C ABI declared in include/tacsl.h and
+// include/tacsl_batch.h.
 //
 // Every entry point validates its host-visible arguments, builds the kernel
 // parameter structs (the SDF table travels by value in the launch), picks the launch
 // shape for this device and enqueues its kernel(s) on the caller's stream.  Nothing
-// here allocates device memory or synchronises, except tacsl_check_errors.
+// here allocates device memory; tacsl_check_errors, tacsl_batch_autotune and the
+// graph set-up synchronise.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <numeric>
+#include <vector>
 
+#include "batch.cuh"
 #include "common.cuh"
 #include "render.cuh"
 #include "shade.cuh"
 #include "taxel.cuh"
+#include "tacsl_batch.h"
 
 namespace tacsl {
 namespace {
@@ -46,6 +53,8 @@ struct DevInfo {
     int sms = 0;
     int max_smem_optin = 0;
     bool shade_attr_set = false;
+    bool batch_shade_attr_set = false;
+    int batch_force_ctas[4] = {0, 0, 0, 0};   // resident CTAs per SM: [np == 4][dynamic]
 };
 constexpr int kMaxDevices = 64;
 DevInfo g_dev[kMaxDevices];
@@ -443,6 +452,548 @@ int tacsl_render_step(const tacsl_sdf_set* set, const tacsl_contact_params* para
     if (T == 0) return ok();
     return launch_penalty(tab, prm, B, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t, wrench, *dev,
                           stream);
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched step over uneven pads, objects and images (include/tacsl_batch.h)
+// ===========================================================================
+namespace tacsl {
+namespace {
+
+constexpr int64_t kBatchHeader = 256;        // workspace bytes before the pad schedule (the counters)
+constexpr int kSmemOptinSm103 = 232448;      // opt-in shared memory per block on sm_103
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+uint64_t batch_fingerprint(const tacsl_batch_desc* d, const tacsl_batch_plan& plan) {
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(h, &d->n_pad, sizeof(d->n_pad));
+    h = fnv1a(h, &d->n_layout, sizeof(d->n_layout));
+    h = fnv1a(h, &d->n_points, sizeof(d->n_points));
+    if (d->n_pad > 0) {
+        h = fnv1a(h, d->obj_id, sizeof(int32_t) * d->n_pad);
+        h = fnv1a(h, d->layout, sizeof(int32_t) * d->n_pad);
+        h = fnv1a(h, d->sensor, sizeof(int32_t) * d->n_pad);
+    }
+    if (d->n_layout > 0) {
+        h = fnv1a(h, d->layout_first, sizeof(int64_t) * d->n_layout);
+        h = fnv1a(h, d->layout_count, sizeof(int32_t) * d->n_layout);
+    }
+    h = fnv1a(h, plan.model_h, sizeof(int32_t) * plan.n_model);
+    h = fnv1a(h, plan.model_w, sizeof(int32_t) * plan.n_model);
+    return h;
+}
+
+int shade_stage_floats(int max_w) { return kShTile + 2 * max_w; }
+
+int batch_plan(const tacsl_batch_desc* d, const tacsl_sensor_set* sensors, tacsl_batch_plan* plan,
+               int64_t* taxel_offset, int64_t* pixel_offset) {
+    if (d == nullptr || plan == nullptr) return fail(TACSL_ERR_INVALID_ARG, "batch description or plan is NULL");
+    if (d->n_pad < 0) return fail(TACSL_ERR_INVALID_ARG, "n_pad = %d < 0", d->n_pad);
+    if (d->n_pad > 0 && (d->obj_id == nullptr || d->layout == nullptr || d->sensor == nullptr))
+        return fail(TACSL_ERR_INVALID_ARG, "obj_id, layout and sensor must be non-NULL");
+    if (d->n_pad > 0 && d->n_layout < 1) return fail(TACSL_ERR_INVALID_ARG, "n_layout = %d < 1", d->n_layout);
+    if (d->n_layout > 0 && (d->layout_first == nullptr || d->layout_count == nullptr))
+        return fail(TACSL_ERR_INVALID_ARG, "layout_first and layout_count must be non-NULL");
+    tacsl_batch_plan p;
+    memset(&p, 0, sizeof(p));
+    p.n_pad = d->n_pad;
+    p.force_np = 4;
+    p.force_dynamic = 1;
+    bool any_image = false;
+    for (int b = 0; b < d->n_pad; ++b) any_image |= d->sensor[b] >= 0;
+    if (any_image) {
+        if (sensors == nullptr || sensors->models == nullptr)
+            return fail(TACSL_ERR_INVALID_ARG, "a pad has an image but the sensor set is NULL");
+        if (sensors->n_model < 1 || sensors->n_model > TACSL_MAX_MODEL)
+            return fail(TACSL_ERR_INVALID_ARG, "n_model = %d outside [1, %d]", sensors->n_model, TACSL_MAX_MODEL);
+        p.n_model = sensors->n_model;
+        for (int m = 0; m < p.n_model; ++m) {
+            const tacsl_sensor_model& sm = sensors->models[m];
+            if (sm.H < 4 || sm.W < 4 || sm.H % 4 != 0 || sm.W % 4 != 0)
+                return fail(TACSL_ERR_INVALID_ARG, "sensor model %d: %d x %d, H and W must be positive multiples of 4",
+                            m, sm.H, sm.W);
+            if ((int64_t)sm.H * sm.W >= (int64_t(1) << 28))
+                return fail(TACSL_ERR_UNSUPPORTED, "sensor model %d: image too large", m);
+            p.model_h[m] = sm.H;
+            p.model_w[m] = sm.W;
+            p.max_w = std::max(p.max_w, sm.W);
+        }
+        if (shade_smem_bytes(2, shade_stage_floats(p.max_w)) > kSmemOptinSm103)
+            return fail(TACSL_ERR_UNSUPPORTED, "image width %d too large for the shared-memory pipeline", p.max_w);
+    }
+    for (int l = 0; l < d->n_layout; ++l) {
+        if (d->layout_count[l] < 1 || d->layout_count[l] > TACSL_MAX_TAXELS)
+            return fail(TACSL_ERR_INVALID_ARG, "layout %d: %d taxels outside [1, %d]", l, d->layout_count[l],
+                        TACSL_MAX_TAXELS);
+        if (d->layout_first[l] < 0 || d->layout_first[l] + d->layout_count[l] > d->n_points)
+            return fail(TACSL_ERR_INVALID_ARG, "layout %d: points [%lld, %lld) outside the pool of %lld", l,
+                        (long long)d->layout_first[l], (long long)(d->layout_first[l] + d->layout_count[l]),
+                        (long long)d->n_points);
+    }
+    std::vector<int64_t> per_model(p.n_model + 1, 0);
+    int64_t taxels = 0, pixels = 0;
+    for (int b = 0; b < d->n_pad; ++b) {
+        const int o = d->obj_id[b], l = d->layout[b], s = d->sensor[b];
+        if (o < 0 || o >= TACSL_MAX_SDF) return fail(TACSL_ERR_INVALID_ARG, "pad %d: obj_id %d out of range", b, o);
+        if (l < 0 || l >= d->n_layout) return fail(TACSL_ERR_INVALID_ARG, "pad %d: layout %d out of range", b, l);
+        if (s < -1 || s >= p.n_model) return fail(TACSL_ERR_INVALID_ARG, "pad %d: sensor %d out of range", b, s);
+        if (taxel_offset) taxel_offset[b] = taxels;
+        taxels += d->layout_count[l];
+        if (s >= 0) {
+            if (pixel_offset) pixel_offset[b] = pixels;
+            pixels += (int64_t)p.model_h[s] * p.model_w[s];
+            ++per_model[s];
+            ++p.n_image;
+        } else if (pixel_offset) {
+            pixel_offset[b] = -1;
+        }
+    }
+    p.n_taxel_out = taxels;
+    p.n_pixel_out = pixels;
+    for (int m = 0; m < p.n_model; ++m) p.model_img_begin[m + 1] = p.model_img_begin[m] + (int32_t)per_model[m];
+    p.off_sched = kBatchHeader;
+    p.off_images = (p.off_sched + (int64_t)sizeof(BatchPad) * p.n_pad + 255) / 256 * 256;
+    p.workspace_bytes = (p.off_images + (int64_t)sizeof(int64_t) * p.n_image + 255) / 256 * 256;
+    p.fingerprint = batch_fingerprint(d, p);
+    *plan = p;
+    return ok();
+}
+
+int batch_pack(const tacsl_batch_plan* plan, const tacsl_batch_desc* d, void* host) {
+    if (plan == nullptr || d == nullptr || host == nullptr)
+        return fail(TACSL_ERR_INVALID_ARG, "plan, description or buffer is NULL");
+    if (d->n_pad != plan->n_pad || batch_fingerprint(d, *plan) != plan->fingerprint)
+        return fail(TACSL_ERR_INVALID_ARG, "batch description differs from the one the plan was made for");
+    unsigned char* base = static_cast<unsigned char*>(host);
+    memset(base, 0, (size_t)plan->workspace_bytes);
+    // pad schedule: largest taxel count first (ties in pad order)
+    std::vector<int32_t> order(d->n_pad);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return d->layout_count[d->layout[a]] > d->layout_count[d->layout[b]];
+    });
+    std::vector<int64_t> out(d->n_pad), px(d->n_pad, -1);
+    int64_t t = 0, q = 0;
+    for (int b = 0; b < d->n_pad; ++b) {
+        out[b] = t;
+        t += d->layout_count[d->layout[b]];
+        if (d->sensor[b] >= 0) {
+            px[b] = q;
+            q += (int64_t)plan->model_h[d->sensor[b]] * plan->model_w[d->sensor[b]];
+        }
+    }
+    BatchPad* sched = reinterpret_cast<BatchPad*>(base + plan->off_sched);
+    for (int i = 0; i < d->n_pad; ++i) {
+        const int b = order[i];
+        const int l = d->layout[b];
+        sched[i] = BatchPad{b, d->layout_count[l], d->obj_id[b], 0, d->layout_first[l], out[b]};
+    }
+    // image list: grouped by model, pad order within a model
+    int64_t* img = reinterpret_cast<int64_t*>(base + plan->off_images);
+    std::vector<int32_t> fill(plan->model_img_begin, plan->model_img_begin + plan->n_model);
+    for (int b = 0; b < d->n_pad; ++b)
+        if (d->sensor[b] >= 0) img[fill[d->sensor[b]]++] = px[b];
+    return ok();
+}
+
+int check_batch_io_forces(const tacsl_batch_plan* plan, const void* ws, const tacsl_batch_io* io) {
+    if (plan == nullptr || io == nullptr) return fail(TACSL_ERR_INVALID_ARG, "plan or io is NULL");
+    if (ws == nullptr || !aligned(ws, 256)) return fail(TACSL_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+    if (plan->force_np != 0 && plan->force_np != 2 && plan->force_np != 4)
+        return fail(TACSL_ERR_INVALID_ARG, "force_np = %d must be 0, 2 or 4", plan->force_np);
+    if (plan->n_pad == 0) return TACSL_OK;
+    const void* ptrs[] = {io->taxels, io->pad_pose, io->pad_twist, io->depth, io->f_n, io->f_t};
+    const char* names[] = {"taxels", "pad_pose", "pad_twist", "depth", "f_n", "f_t"};
+    for (int i = 0; i < 6; ++i) {
+        if (ptrs[i] == nullptr) return fail(TACSL_ERR_INVALID_ARG, "io.%s is NULL", names[i]);
+        if (!aligned(ptrs[i], 4)) return fail(TACSL_ERR_INVALID_ARG, "io.%s is not 4-byte aligned", names[i]);
+    }
+    if (io->wrench != nullptr && !aligned(io->wrench, 4))
+        return fail(TACSL_ERR_INVALID_ARG, "io.wrench is not 4-byte aligned");
+    return TACSL_OK;
+}
+
+int check_batch_io_shade(const tacsl_batch_plan* plan, const void* ws, const tacsl_sensor_set* sensors,
+                         const tacsl_batch_io* io) {
+    if (plan == nullptr || io == nullptr) return fail(TACSL_ERR_INVALID_ARG, "plan or io is NULL");
+    if (ws == nullptr || !aligned(ws, 256)) return fail(TACSL_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+    if (plan->img_block != 0 && (plan->img_block < 1 || plan->img_block > 1024 ||
+                                 (plan->img_block & (plan->img_block - 1)) != 0))
+        return fail(TACSL_ERR_INVALID_ARG, "img_block = %d must be 0 or a power of two <= 1024", plan->img_block);
+    if (plan->n_stages != 0 && (plan->n_stages < 2 || plan->n_stages > 12))
+        return fail(TACSL_ERR_INVALID_ARG, "n_stages = %d must be 0 or in [2, 12]", plan->n_stages);
+    if (plan->n_image == 0) return TACSL_OK;
+    if (sensors == nullptr || sensors->models == nullptr) return fail(TACSL_ERR_INVALID_ARG, "sensor set is NULL");
+    if (sensors->n_model != plan->n_model)
+        return fail(TACSL_ERR_INVALID_ARG, "n_model = %d, the plan has %d", sensors->n_model, plan->n_model);
+    for (int m = 0; m < plan->n_model; ++m) {
+        const tacsl_sensor_model& sm = sensors->models[m];
+        if (sm.H != plan->model_h[m] || sm.W != plan->model_w[m])
+            return fail(TACSL_ERR_INVALID_ARG, "sensor model %d is %d x %d, the plan has %d x %d", m, sm.H, sm.W,
+                        plan->model_h[m], plan->model_w[m]);
+        if (!(sm.pitch_x > 0.f) || !(sm.pitch_y > 0.f) || !std::isfinite(sm.pitch_x) || !std::isfinite(sm.pitch_y))
+            return fail(TACSL_ERR_INVALID_ARG, "sensor model %d: pixel pitch must be positive and finite", m);
+        if (sm.coeffs == nullptr || !aligned(sm.coeffs, 16))
+            return fail(TACSL_ERR_INVALID_ARG, "sensor model %d: coeffs NULL or not 16-byte aligned", m);
+    }
+    if (io->depth_map == nullptr || !aligned(io->depth_map, 16))
+        return fail(TACSL_ERR_INVALID_ARG, "io.depth_map NULL or not 16-byte aligned");
+    if (io->rgb == nullptr || !aligned(io->rgb, 16)) return fail(TACSL_ERR_INVALID_ARG, "io.rgb NULL or not 16-byte aligned");
+    return TACSL_OK;
+}
+
+// Resident CTAs per SM of each force-kernel variant (queried once per device).
+int batch_force_ctas(DevInfo& dev, int np, bool dyn, int* out) {
+    const int slot = (np == 4 ? 2 : 0) + (dyn ? 1 : 0);
+    if (dev.batch_force_ctas[slot] == 0) {
+        int n = 0;
+        cudaError_t e;
+        if (np == 4)
+            e = dyn ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_force_kernel<4, true>, 256, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_force_kernel<4, false>, 256, 0);
+        else
+            e = dyn ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_force_kernel<2, true>, 256, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_force_kernel<2, false>, 256, 0);
+        if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(e));
+        dev.batch_force_ctas[slot] = n > 0 ? n : 1;
+    }
+    *out = dev.batch_force_ctas[slot];
+    return TACSL_OK;
+}
+
+int launch_batch_forces(const tacsl_batch_plan* plan, void* ws, const SdfTable& tab, const Params4& prm,
+                        const tacsl_batch_io* io, DevInfo& dev, int np, bool dyn, tacsl_stream_t stream) {
+    if (plan->n_pad == 0) return ok();
+    BatchForceArgs a;
+    a.tab = tab;
+    a.prm = prm;
+    a.sched = reinterpret_cast<const BatchPad*>(static_cast<const unsigned char*>(ws) + plan->off_sched);
+    a.n_pad = plan->n_pad;
+    a.taxels = io->taxels;
+    a.pose = io->pad_pose;
+    a.twist = io->pad_twist;
+    a.depth = io->depth;
+    a.f_n = io->f_n;
+    a.f_t = io->f_t;
+    a.wrench = io->wrench;
+    a.ticket = static_cast<unsigned int*>(ws);
+    int ctas = 0;
+    int rc = batch_force_ctas(dev, np, dyn, &ctas);
+    if (rc) return rc;
+    const int64_t need = (plan->n_pad + 7) / 8;
+    const int grid = static_cast<int>(std::min<int64_t>(need, (int64_t)dev.sms * ctas));
+    if (np == 4) {
+        if (dyn) batch_force_kernel<4, true><<<grid, 256, 0, stream>>>(a);
+        else batch_force_kernel<4, false><<<grid, 256, 0, stream>>>(a);
+    } else {
+        if (dyn) batch_force_kernel<2, true><<<grid, 256, 0, stream>>>(a);
+        else batch_force_kernel<2, false><<<grid, 256, 0, stream>>>(a);
+    }
+    return check_launch("batched force-field kernel");
+}
+
+// Work items of the image kernel with M images per item.
+int64_t batch_items(const tacsl_batch_plan* plan, int M) {
+    int64_t n = 0;
+    for (int m = 0; m < plan->n_model; ++m) {
+        const int64_t cnt = plan->model_img_begin[m + 1] - plan->model_img_begin[m];
+        const int64_t tiles = ((int64_t)plan->model_h[m] * plan->model_w[m] + kShTile - 1) / kShTile;
+        n += (cnt + M - 1) / M * tiles;
+    }
+    return n;
+}
+
+int batch_auto_block(const tacsl_batch_plan* plan, int sms) {
+    int M = 1024;
+    while (M > 32 && batch_items(plan, M) < 24LL * sms) M /= 2;
+    return M;
+}
+
+int batch_max_stages(const tacsl_batch_plan* plan, const DevInfo& dev) {
+    const int sf = shade_stage_floats(plan->max_w);
+    return std::min(12, (dev.max_smem_optin - shade_smem_bytes(0, sf)) / (sf * 4));
+}
+
+int launch_batch_shade(const tacsl_batch_plan* plan, const void* ws, const tacsl_sensor_set* sensors,
+                       const tacsl_batch_io* io, DevInfo& dev, int M, int ns, tacsl_stream_t stream) {
+    if (plan->n_image == 0) return ok();
+    BatchShadeArgs a;
+    memset(&a, 0, sizeof(a));
+    a.stage_floats = shade_stage_floats(plan->max_w);
+    const int ns_max = batch_max_stages(plan, dev);
+    if (ns_max < 2) return fail(TACSL_ERR_UNSUPPORTED, "image width %d too large for this device", plan->max_w);
+    if (M == 0) M = batch_auto_block(plan, dev.sms);
+    if (ns == 0 || ns > ns_max) ns = ns_max;
+    int64_t items = 0;
+    for (int m = 0; m < plan->n_model; ++m) {
+        const tacsl_sensor_model& sm = sensors->models[m];
+        BatchModel& md = a.mdl[m];
+        md.coeffs = sm.coeffs;
+        md.H = sm.H;
+        md.W = sm.W;
+        md.HW = sm.H * sm.W;
+        md.n_tiles = (md.HW + kShTile - 1) / kShTile;
+        md.cx_c = 1.f / (2.f * sm.pitch_x);
+        md.cx_e = 1.f / sm.pitch_x;
+        md.cy_c = 1.f / (2.f * sm.pitch_y);
+        md.cy_e = 1.f / sm.pitch_y;
+        md.img_begin = plan->model_img_begin[m];
+        md.img_end = plan->model_img_begin[m + 1];
+        md.item_begin = static_cast<int>(std::min<int64_t>(items, INT32_MAX));
+        items += (int64_t)(md.img_end - md.img_begin + M - 1) / M * md.n_tiles;
+    }
+    if (items >= (int64_t(1) << 31)) return fail(TACSL_ERR_UNSUPPORTED, "too many work items");
+    a.img_px = reinterpret_cast<const int64_t*>(static_cast<const unsigned char*>(ws) + plan->off_images);
+    a.depth = io->depth_map;
+    a.rgb = io->rgb;
+    a.n_model = plan->n_model;
+    a.M = M;
+    a.n_items = static_cast<int>(items);
+    a.n_stages = ns;
+    if (!dev.batch_shade_attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(batch_shade_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   dev.max_smem_optin);
+        if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        dev.batch_shade_attr_set = true;
+    }
+    const int grid = static_cast<int>(std::min<int64_t>(items, dev.sms));
+    batch_shade_kernel<<<grid, kShThreads, shade_smem_bytes(ns, a.stage_floats), stream>>>(a);
+    return check_launch("batched image kernel");
+}
+
+// Everything of a batch step that needs no launch: checks, tables, device facts.
+struct BatchCall {
+    SdfTable tab;
+    Params4 prm;
+    DevInfo* dev = nullptr;
+};
+
+int batch_prepare(const tacsl_batch_plan* plan, const void* ws, const tacsl_sdf_set* set,
+                  const tacsl_contact_params* params, const tacsl_sensor_set* sensors, const tacsl_batch_io* io,
+                  bool forces, bool images, BatchCall& c) {
+    int rc;
+    if (forces) {
+        if ((rc = build_table(set, c.tab))) return rc;
+        if ((rc = check_batch_io_forces(plan, ws, io))) return rc;
+        if ((rc = build_params(params, plan->n_pad, c.prm))) return rc;
+    }
+    if (images && (rc = check_batch_io_shade(plan, ws, sensors, io))) return rc;
+    if ((rc = device_info(&c.dev))) return rc;
+    if (forces) {
+        int ctas;
+        const int np = plan->force_np == 2 ? 2 : 4;
+        if ((rc = batch_force_ctas(*c.dev, np, plan->force_dynamic != 0, &ctas))) return rc;
+    }
+    return TACSL_OK;
+}
+
+int run_batch_forces(const tacsl_batch_plan* plan, void* ws, const BatchCall& c, const tacsl_batch_io* io,
+                     tacsl_stream_t stream) {
+    return launch_batch_forces(plan, ws, c.tab, c.prm, io, *c.dev, plan->force_np == 2 ? 2 : 4,
+                               plan->force_dynamic != 0, stream);
+}
+
+int run_batch_shade(const tacsl_batch_plan* plan, const void* ws, const tacsl_sensor_set* sensors,
+                    const BatchCall& c, const tacsl_batch_io* io, tacsl_stream_t stream) {
+    return launch_batch_shade(plan, ws, sensors, io, *c.dev, plan->img_block, plan->n_stages, stream);
+}
+
+// Mean time of `reps` launches after one warm-up (ms), via events on the stream.
+template <class F>
+int time_launches(F&& launch, int reps, tacsl_stream_t stream, float* ms) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaEventCreate failed");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(TACSL_ERR_CUDA, "cudaEventCreate failed");
+    }
+    int rc = launch();
+    if (!rc) {
+        cudaEventRecord(e0, stream);
+        for (int r = 0; r < reps && !rc; ++r) rc = launch();
+        cudaEventRecord(e1, stream);
+        const cudaError_t e = cudaEventSynchronize(e1);
+        if (!rc && e != cudaSuccess) rc = fail(TACSL_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+        if (!rc) {
+            cudaEventElapsedTime(ms, e0, e1);
+            *ms /= reps;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+}  // namespace
+}  // namespace tacsl
+
+extern "C" {
+
+int tacsl_batch_plan_create(const tacsl_batch_desc* desc, const tacsl_sensor_set* sensors, tacsl_batch_plan* plan,
+                            int64_t* taxel_offset, int64_t* pixel_offset) {
+    return batch_plan(desc, sensors, plan, taxel_offset, pixel_offset);
+}
+
+int tacsl_batch_pack(const tacsl_batch_plan* plan, const tacsl_batch_desc* desc, void* host_workspace) {
+    return batch_pack(plan, desc, host_workspace);
+}
+
+int tacsl_batch_upload(const tacsl_batch_plan* plan, const tacsl_batch_desc* desc, void* workspace,
+                       tacsl_stream_t stream) {
+    if (workspace == nullptr || !aligned(workspace, 256))
+        return fail(TACSL_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+    if (plan == nullptr) return fail(TACSL_ERR_INVALID_ARG, "plan is NULL");
+    std::vector<unsigned char> host((size_t)plan->workspace_bytes);
+    int rc = batch_pack(plan, desc, host.data());
+    if (rc) return rc;
+    // from pageable memory: the copy is staged before the call returns, so the
+    // temporary buffer may go
+    const cudaError_t e = cudaMemcpyAsync(workspace, host.data(), host.size(), cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "workspace upload: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+int tacsl_batch_forces(const tacsl_batch_plan* plan, void* workspace, const tacsl_sdf_set* set,
+                       const tacsl_contact_params* params, const tacsl_batch_io* io, tacsl_stream_t stream) {
+    BatchCall c;
+    int rc = batch_prepare(plan, workspace, set, params, nullptr, io, true, false, c);
+    if (rc) return rc;
+    return run_batch_forces(plan, workspace, c, io, stream);
+}
+
+int tacsl_batch_shade(const tacsl_batch_plan* plan, const void* workspace, const tacsl_sensor_set* sensors,
+                      const tacsl_batch_io* io, tacsl_stream_t stream) {
+    BatchCall c;
+    int rc = batch_prepare(plan, workspace, nullptr, nullptr, sensors, io, false, true, c);
+    if (rc) return rc;
+    return run_batch_shade(plan, workspace, sensors, c, io, stream);
+}
+
+int tacsl_batch_step(const tacsl_batch_plan* plan, void* workspace, const tacsl_sdf_set* set,
+                     const tacsl_contact_params* params, const tacsl_sensor_set* sensors, const tacsl_batch_io* io,
+                     tacsl_stream_t stream) {
+    BatchCall c;
+    int rc = batch_prepare(plan, workspace, set, params, sensors, io, true, true, c);
+    if (rc) return rc;
+    if ((rc = run_batch_shade(plan, workspace, sensors, c, io, stream))) return rc;
+    return run_batch_forces(plan, workspace, c, io, stream);
+}
+
+int tacsl_batch_autotune(tacsl_batch_plan* plan, void* workspace, const tacsl_sdf_set* set,
+                         const tacsl_contact_params* params, const tacsl_sensor_set* sensors, const tacsl_batch_io* io,
+                         int32_t reps, double* best_ms, tacsl_stream_t stream) {
+    if (reps < 1 || reps > 1000) return fail(TACSL_ERR_INVALID_ARG, "reps = %d outside [1, 1000]", reps);
+    BatchCall c;
+    int rc = batch_prepare(plan, workspace, set, params, sensors, io, true, true, c);
+    if (rc) return rc;
+    DevInfo& dev = *c.dev;
+    double total = 0.0;
+    // force kernel: taxels in flight per lane x pad dealing
+    if (plan->n_pad > 0) {
+        float best = 0.f;
+        int best_np = 4, best_dyn = 1;
+        for (int np : {4, 2})
+            for (int dyn : {1, 0}) {
+                float ms = 0.f;
+                rc = time_launches([&] { return launch_batch_forces(plan, workspace, c.tab, c.prm, io, dev, np, dyn != 0,
+                                                                    stream); },
+                                   reps, stream, &ms);
+                if (rc) return rc;
+                if (best == 0.f || ms < best) { best = ms; best_np = np; best_dyn = dyn; }
+            }
+        plan->force_np = best_np;
+        plan->force_dynamic = best_dyn;
+        total += best;
+    }
+    // image kernel: images per item x stages in flight
+    if (plan->n_image > 0) {
+        const int ns_max = batch_max_stages(plan, dev);
+        if (ns_max < 2) return fail(TACSL_ERR_UNSUPPORTED, "image width %d too large for this device", plan->max_w);
+        std::vector<int> stage_set = {ns_max};
+        for (int s : {4, 8})
+            if (s < ns_max) stage_set.push_back(s);
+        float best = 0.f;
+        int best_m = 0, best_ns = 0;
+        for (int M = 1024; M >= 16; M /= 2) {
+            if (batch_items(plan, M) < dev.sms && M != 16) continue;   // fewer items than SMs: idle SMs
+            for (int ns : stage_set) {
+                float ms = 0.f;
+                rc = time_launches([&] { return launch_batch_shade(plan, workspace, sensors, io, dev, M, ns, stream); },
+                                   reps, stream, &ms);
+                if (rc) return rc;
+                if (best == 0.f || ms < best) { best = ms; best_m = M; best_ns = ns; }
+            }
+        }
+        plan->img_block = best_m;
+        plan->n_stages = best_ns;
+        total += best;
+    }
+    if (best_ms) *best_ms = total;
+    return ok();
+}
+
+int tacsl_batch_graph_create(const tacsl_batch_plan* plan, void* workspace, const tacsl_sdf_set* set,
+                             const tacsl_contact_params* params, const tacsl_sensor_set* sensors,
+                             const tacsl_batch_io* io, tacsl_graph_t* graph) {
+    if (graph == nullptr) return fail(TACSL_ERR_INVALID_ARG, "graph is NULL");
+    *graph = nullptr;
+    BatchCall c;
+    int rc = batch_prepare(plan, workspace, set, params, sensors, io, true, true, c);
+    if (rc) return rc;
+    // one-time device set-up (kernel attributes) happens outside the capture
+    if (plan->n_image > 0 && !c.dev->batch_shade_attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(batch_shade_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   c.dev->max_smem_optin);
+        if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        c.dev->batch_shade_attr_set = true;
+    }
+    cudaStream_t s;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return fail(TACSL_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    }
+    rc = run_batch_shade(plan, workspace, sensors, c, io, s);
+    if (!rc) rc = run_batch_forces(plan, workspace, c, io, s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    cudaStreamDestroy(s);
+    if (!rc && e != cudaSuccess) rc = fail(TACSL_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    if (!rc) {
+        e = cudaGraphInstantiate(&exec, g, 0);
+        if (e != cudaSuccess) rc = fail(TACSL_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+    if (g) cudaGraphDestroy(g);
+    if (rc) return rc;
+    *graph = reinterpret_cast<tacsl_graph_t>(exec);
+    return ok();
+}
+
+int tacsl_graph_launch(tacsl_graph_t graph, tacsl_stream_t stream) {
+    if (graph == nullptr) return fail(TACSL_ERR_INVALID_ARG, "graph is NULL");
+    const cudaError_t e = cudaGraphLaunch(reinterpret_cast<cudaGraphExec_t>(graph), stream);
+    if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+int tacsl_graph_destroy(tacsl_graph_t graph) {
+    if (graph == nullptr) return ok();
+    const cudaError_t e = cudaGraphExecDestroy(reinterpret_cast<cudaGraphExec_t>(graph));
+    if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaGraphExecDestroy: %s", cudaGetErrorString(e));
+    return ok();
 }
 
 }  // extern "C"

@@ -193,32 +193,31 @@ __device__ __forceinline__ void contact_force(const float* r, float phi, const f
     }
 }
 
-// All taxels of pad b by ONE warp (see the file comment); NP taxels per lane in flight.
+// All T taxels of one pad by ONE warp (see the file comment); NP taxels per lane in
+// flight.  The pad's pose / twist / outputs are addressed directly: depth[t],
+// f_n[3t..3t+2], f_t[3t..3t+2], wrench[0..5] (wrench may be NULL); parameters come from
+// entry pi of prm; id selects the object's SDF (out of range: NaN outputs and an error flag).
 template <int NP>
-__device__ __forceinline__ void pad_by_warp(const SdfTable& tab, const Params4& prm, int P, int T,
-                                            const float* __restrict__ taxels, const int32_t* __restrict__ obj_id,
-                                            const float* __restrict__ pad_pose, const float* __restrict__ pad_twist,
-                                            float* __restrict__ depth, float* __restrict__ f_n,
-                                            float* __restrict__ f_t, float* __restrict__ wrench, int64_t b) {
+__device__ __forceinline__ void pad_taxels_by_warp(const SdfTable& tab, const Params4& prm, int pi, int id, int T,
+                                                   const float* __restrict__ taxels, const float* __restrict__ pose7,
+                                                   const float* __restrict__ twist6, float* __restrict__ depth,
+                                                   float* __restrict__ f_n, float* __restrict__ f_t,
+                                                   float* __restrict__ wrench) {
     const int lane = threadIdx.x & 31;
-    const int64_t e = b / P;
-    const int id = __ldg(obj_id + e);
-    const int64_t o = b * T;
     if (id < 0 || id >= tab.count) {
         const float qnan = __int_as_float(0x7fc00000);
         for (int t = lane; t < T; t += 32) {
-            depth[o + t] = qnan;
+            depth[t] = qnan;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) { f_n[(o + t) * 3 + a] = qnan; f_t[(o + t) * 3 + a] = qnan; }
+            for (int a = 0; a < 3; ++a) { f_n[t * 3 + a] = qnan; f_t[t * 3 + a] = qnan; }
         }
-        if (wrench != nullptr && lane < 6) wrench[b * 6 + lane] = qnan;
+        if (wrench != nullptr && lane < 6) wrench[lane] = qnan;
         if (lane == 0) raise_dev_error(TACSL_DEVERR_BAD_OBJ_ID);
         return;
     }
     const DevSdf& S = tab.s[id];
     Pose Pz;
-    load_pose(pad_pose + b * 7, pad_twist + b * 6, Pz);
-    const int pi = prm.count == 1 ? 0 : static_cast<int>(e);
+    load_pose(pose7, twist6, Pz);
     const float kn = __ldg(prm.k_n + pi), kd = __ldg(prm.k_d + pi), kt = __ldg(prm.k_t + pi),
                 mu = __ldg(prm.mu + pi);
     const uint64_t pol = policy_evict_last();
@@ -271,9 +270,9 @@ __device__ __forceinline__ void pad_by_warp(const SdfTable& tab, const Params4& 
             }
             float dep, fn[3], ft[3];
             contact_force(r, phi, g, vel[u][0], vel[u][1], vel[u][2], kn, kd, kt, mu, dep, fn, ft);
-            depth[o + t] = dep;
+            depth[t] = dep;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) { f_n[(o + t) * 3 + a] = fn[a]; f_t[(o + t) * 3 + a] = ft[a]; }
+            for (int a = 0; a < 3; ++a) { f_n[t * 3 + a] = fn[a]; f_t[t * 3 + a] = ft[a]; }
             const float fx = fn[0] + ft[0], fy = fn[1] + ft[1], fz = fn[2] + ft[2];
             acc[0] += fx; acc[1] += fy; acc[2] += fz;
             acc[3] += p[u][1] * fz - p[u][2] * fy;
@@ -291,9 +290,23 @@ __device__ __forceinline__ void pad_by_warp(const SdfTable& tab, const Params4& 
             float w = acc[0];
 #pragma unroll
             for (int k = 1; k < 6; ++k) w = (lane == k) ? acc[k] : w;
-            wrench[b * 6 + lane] = w;
+            wrench[lane] = w;
         }
     }
+}
+
+// Pad b = (env b / P, slot b % P) of a uniform batch: T taxels per pad, outputs at b*T.
+template <int NP>
+__device__ __forceinline__ void pad_by_warp(const SdfTable& tab, const Params4& prm, int P, int T,
+                                            const float* __restrict__ taxels, const int32_t* __restrict__ obj_id,
+                                            const float* __restrict__ pad_pose, const float* __restrict__ pad_twist,
+                                            float* __restrict__ depth, float* __restrict__ f_n,
+                                            float* __restrict__ f_t, float* __restrict__ wrench, int64_t b) {
+    const int64_t e = b / P;
+    const int64_t o = b * T;
+    pad_taxels_by_warp<NP>(tab, prm, prm.count == 1 ? 0 : static_cast<int>(e), __ldg(obj_id + e), T, taxels,
+                           pad_pose + b * 7, pad_twist + b * 6, depth + o, f_n + o * 3, f_t + o * 3,
+                           wrench != nullptr ? wrench + b * 6 : nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -157,6 +157,34 @@ def bake(shape: Shape, n: int | tuple, voxel: float, origin=None) -> Grid:
     return Grid(np.ascontiguousarray(data), origin, voxel, shape)
 
 
+def bake_extrusion(shape: Shape, n: int, voxel: float) -> Grid:
+    """``bake`` for the shapes that are extrusions along z of a 2-D section (box,
+    cylinder, hexagonal prism), at a fraction of the cost: the exact SDF of an
+    extrusion is sqrt(max(d2, 0)^2 + max(dz, 0)^2) + min(max(d2, dz), 0) with d2 the
+    section's 2-D distance and dz = |z| - hz, so d2 is evaluated on the n x n plane and
+    dz on the n nodes of the z axis only (the same values as ``bake`` up to float64
+    rounding)."""
+    voxel = float(np.float32(voxel))
+    origin = np.asarray([-(n - 1) * voxel / 2.0] * 3, dtype=np.float32)
+    ax = [origin[a].astype(np.float64) + np.arange(n, dtype=np.float64) * voxel for a in range(3)]
+    yy, xx = np.meshgrid(ax[1], ax[0], indexing="ij")
+    k, d = shape.kind, shape.dims
+    if k == "box":
+        qx, qy = np.abs(xx) - d[0], np.abs(yy) - d[1]
+        d2 = np.hypot(np.maximum(qx, 0.0), np.maximum(qy, 0.0)) + np.minimum(np.maximum(qx, qy), 0.0)
+        hz = d[2]
+    elif k == "cylinder":
+        d2, hz = np.hypot(xx, yy) - d[0], d[1]
+    elif k == "hexprism":
+        d2, hz = _hexagon_sdf(xx, yy, d[0]), d[1]
+    else:
+        raise ValueError(f"{k} is not an extrusion along z")
+    dz = (np.abs(ax[2]) - hz)[:, None, None]
+    d2 = d2[None, :, :]
+    out = np.hypot(np.maximum(d2, 0.0), np.maximum(dz, 0.0)) + np.minimum(np.maximum(d2, dz), 0.0)
+    return Grid(np.ascontiguousarray(out.astype(np.float32)), origin, voxel, shape)
+
+
 def bake_field(values_fn, n: tuple, voxel: float, origin) -> Grid:
     """Bake an arbitrary callable f(x, y, z) (float64 arrays) into a grid."""
     voxel = float(np.float32(voxel))
@@ -207,10 +235,11 @@ def quat_from_axis_angle(axis, angle) -> np.ndarray:
 # Pads
 # ---------------------------------------------------------------------------
 
-def taxel_grid(ny: int, nx: int, pitch: float) -> np.ndarray:
-    """Taxel template [ny*nx][3] (row-major, x fastest), centred, z = 0."""
+def taxel_grid(ny: int, nx: int, pitch: float, pitch_y: float | None = None) -> np.ndarray:
+    """Taxel template [ny*nx][3] (row-major, x fastest), centred, z = 0; rows are
+    ``pitch_y`` apart (default ``pitch``)."""
     xs = (np.arange(nx) - (nx - 1) / 2.0) * pitch
-    ys = (np.arange(ny) - (ny - 1) / 2.0) * pitch
+    ys = (np.arange(ny) - (ny - 1) / 2.0) * (pitch if pitch_y is None else pitch_y)
     yy, xx = np.meshgrid(ys, xs, indexing="ij")
     return np.ascontiguousarray(np.stack([xx, yy, np.zeros_like(xx)], -1).reshape(-1, 3).astype(np.float32))
 
@@ -435,4 +464,158 @@ def scene_objects(seed: int = 2, E: int = 4096, P: int = 2, ny: int = 20, nx: in
             flat[b] = flat[b % nd]
         sc.depth_map = dm
         sc.meta["distinct_depth_maps"] = nd
+    return sc
+
+
+# ---------------------------------------------------------------------------
+# Uneven batches: every pad with its own resolution, object and sensor model
+# ---------------------------------------------------------------------------
+
+def log_uniform_int(g: np.random.Generator, lo: int, hi: int, size=None) -> np.ndarray:
+    """Integers log-uniform on [lo, hi] (rounded from a log-uniform real)."""
+    return np.rint(np.exp(g.uniform(np.log(lo), np.log(hi), size=size))).astype(np.int64)
+
+
+def grid_pool(seed: int, n_grid: int = 32, n_lo: int = 32, n_hi: int = 256, dims_mm=(5.0, 20.0),
+              sides=None) -> list:
+    """``n_grid`` objects (cylinders, boxes, hex prisms in turn, dimensions U(dims_mm))
+    baked at cubic grids of side log-uniform in [n_lo, n_hi] (or the given ``sides``);
+    grid extent = largest dimension + 6 mm."""
+    g = rng(seed)
+    kinds = ["cylinder", "box", "hexprism"]
+    lo, hi = dims_mm[0] * 1e-3, dims_mm[1] * 1e-3
+    if sides is None:
+        sides = log_uniform_int(g, n_lo, n_hi, size=n_grid)
+    grids = []
+    for i, n in enumerate(sides):
+        kind = kinds[i % 3]
+        if kind == "box":
+            shape = Shape(kind, tuple(g.uniform(lo, hi, size=3) / 2))
+        else:
+            shape = Shape(kind, (g.uniform(lo, hi) / 2, g.uniform(lo, hi) / 2))
+        side = shape.extent() + 6e-3
+        grids.append(bake_extrusion(shape, int(n), side / (int(n) - 1)))
+    return grids
+
+
+@dataclass
+class BatchScene:
+    """An uneven batch (host numpy arrays).  Pad b of env e = b // P uses object
+    obj_id[b], taxel layout layout[b] (points layout_first[l] .. + layout_count[l] of
+    ``taxels``) and sensor model sensor[b] (-1: no image); its depth map is the
+    ``depth_maps[b]`` array of the model's size (None without image)."""
+    grids: list
+    taxels: np.ndarray                # [n_points][3] taxel pool
+    layout_first: np.ndarray          # [n_layout] i64
+    layout_count: np.ndarray          # [n_layout] i32
+    layout_shape: list                # [(ny, nx)]
+    obj_id: np.ndarray                # [n_pad] i32
+    layout: np.ndarray                # [n_pad] i32
+    sensor: np.ndarray                # [n_pad] i32
+    pad_pose: np.ndarray              # [n_pad][7] f32
+    pad_twist: np.ndarray             # [n_pad][6] f32
+    k_n: np.ndarray                   # [n_pad] f32
+    k_d: np.ndarray
+    k_t: np.ndarray
+    mu: np.ndarray
+    models: list                      # [(coeffs [6][3][H][W] f32, pitch_x, pitch_y)]
+    depth_maps: list                  # [n_pad] of [H][W] f32 or None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_pad(self):
+        return self.obj_id.shape[0]
+
+
+PAD_EXTENT = (24e-3, 19e-3)   # taxel-grid extent (x, y) of every pad, metres
+
+
+def scene_batch(seed: int = 3, E: int = 16384, P: int = 2, grids: list | None = None, n_grid: int = 32,
+                grid_sides=(32, 256), res_y=(10, 40), res_x=(12, 50), width=(160, 640), n_size_class: int = 16,
+                vel_sigma: float = 0.05, depth_maps: str = "exact", n_distinct_maps: int = 8,
+                no_image_frac: float = 0.0) -> BatchScene:
+    """E envs x P pads, every env drawing its own pad resolution (ny log-uniform in
+    res_y, nx in res_x; the taxels span PAD_EXTENT at pitch extent/(n-1)), its object
+    from a pool of ``n_grid`` SDF grids (sides log-uniform in grid_sides) and an image
+    size class (W log-uniform in ``width``, stratified over the classes, rounded to a
+    multiple of 4; H = 3/4 W rounded to a multiple of 4); pad slot p of size class c uses sensor model
+    P*c + p, each with its own seeded coefficients.  Poses, twists and contact
+    parameters follow ``scene_objects``; parameters are drawn per env and repeated per
+    pad.  A fraction ``no_image_frac`` of the pads has no image.
+
+    ``depth_maps``: "exact" renders each pad's heightfield; "cycled" renders
+    ``n_distinct_maps`` per sensor model and hands them out in turn."""
+    g = rng(seed)
+    if grids is None:
+        grids = grid_pool(seed + 1, n_grid, *grid_sides)
+    # image size classes
+    # class c's width is log-uniform within the c-th of n_size_class equal slices of
+    # [log width[0], log width[1]] (stratified, so the classes span the whole range)
+    u = (np.arange(n_size_class) + g.random(n_size_class)) / n_size_class
+    ws = np.exp(np.log(width[0]) + u * (np.log(width[1]) - np.log(width[0])))
+    ws = np.maximum(4, 4 * np.rint(ws / 4.0).astype(np.int64))
+    hs = np.maximum(4, 4 * np.rint(0.75 * ws / 4.0).astype(np.int64))
+    models = []
+    for c in range(n_size_class):
+        H, W = int(hs[c]), int(ws[c])
+        for p in range(P):
+            co = shading_coeffs(1, H, W, seed * 1000 + P * c + p)[0]
+            models.append((co, PAD_EXTENT[0] / W, PAD_EXTENT[1] / H))
+    # per env draws
+    ny = log_uniform_int(g, res_y[0], res_y[1], size=E)
+    nx = log_uniform_int(g, res_x[0], res_x[1], size=E)
+    obj_env = g.integers(0, len(grids), size=E)
+    cls_env = g.integers(0, n_size_class, size=E)
+    layouts, pool, first, count, shapes = {}, [], [], [], []
+    n_points = 0
+    lay_env = np.empty(E, np.int32)
+    for e in range(E):
+        key = (int(ny[e]), int(nx[e]))
+        if key not in layouts:
+            t = taxel_grid(key[0], key[1], PAD_EXTENT[0] / max(key[1] - 1, 1), PAD_EXTENT[1] / max(key[0] - 1, 1))
+            layouts[key] = len(first)
+            first.append(n_points)
+            count.append(t.shape[0])
+            shapes.append(key)
+            pool.append(t)
+            n_points += t.shape[0]
+        lay_env[e] = layouts[key]
+    n_pad = E * P
+    obj = np.repeat(obj_env, P).astype(np.int32)
+    layout = np.repeat(lay_env, P).astype(np.int32)
+    sensor = (P * np.repeat(cls_env, P) + np.tile(np.arange(P), E)).astype(np.int32)
+    if no_image_frac > 0:
+        sensor[g.random(n_pad) < no_image_frac] = -1
+    pose = np.zeros((n_pad, 7), np.float32)
+    twist = np.zeros((n_pad, 6), np.float32)
+    for b in range(n_pad):
+        q = random_quaternion(g)
+        delta = g.uniform(-2e-3, 2e-3)
+        off = g.uniform(-2e-3, 2e-3, size=2)
+        pose[b] = place_pad(grids[obj[b]].shape, q, delta, off)
+        twist[b, :3] = g.normal(0.0, vel_sigma, size=3)
+    k_n = np.repeat(g.uniform(0.5e4, 1.5e4, size=E), P).astype(np.float32)
+    k_d = np.zeros(n_pad, np.float32)
+    k_t = np.repeat(g.uniform(50.0, 150.0, size=E), P).astype(np.float32)
+    mu = np.repeat(g.uniform(0.3, 0.7, size=E), P).astype(np.float32)
+    maps = [None] * n_pad
+    made = {}
+    for b in range(n_pad):
+        m = int(sensor[b])
+        if m < 0:
+            continue
+        H, W = models[m][0].shape[2], models[m][0].shape[3]
+        if depth_maps == "exact":
+            maps[b] = depth_map(grids[obj[b]].shape, pose[b], H, W, *PAD_EXTENT)
+        else:
+            lst = made.setdefault(m, [])
+            if len(lst) < n_distinct_maps:
+                lst.append(depth_map(grids[obj[b]].shape, pose[b], H, W, *PAD_EXTENT))
+                maps[b] = lst[-1]
+            else:
+                maps[b] = lst[(b // P) % n_distinct_maps]
+    sc = BatchScene(grids, np.ascontiguousarray(np.concatenate(pool).astype(np.float32)),
+                    np.asarray(first, np.int64), np.asarray(count, np.int32), shapes, obj, layout, sensor, pose,
+                    twist, k_n, k_d, k_t, mu, models, maps)
+    sc.meta.update(E=E, P=P, n_layout=len(first), n_model=len(models), depth_maps=depth_maps)
     return sc
