@@ -142,6 +142,27 @@ int tacsl_batch_forces(const tacsl_batch_plan* plan, void* workspace, const tacs
                        const tacsl_contact_params* params, const tacsl_batch_io* io,
                        tacsl_stream_t stream);
 
+/* tacsl_batch_forces for callers that cannot give the library device memory: a
+ * real-time loop in which cudaMalloc / cudaFree would synchronise the device, or a
+ * plug-in whose host application owns every device allocation.  The paper has no
+ * counterpart; this is an interface convenience.  The call takes the batch description
+ * itself (no plan, no workspace) and allocates nothing.  The pad schedule and the pad
+ * counters live in one fixed 2 MiB array inside the library, present on every GPU that
+ * loads it until the process exits; each call copies its schedule there (from host
+ * memory, on stream) with the counters cleared to zero, then launches the force kernel.
+ * Outputs are laid out as for a plan of the same description (taxel_offset = prefix sum
+ * of T in pad order; wrench [n_pad][6]); desc->sensor is ignored.
+ *   - At most 65528 pads per call; more returns TACSL_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's address there (set-up, once per
+ *     device, with that device current); make that first call before any stream
+ *     capture.
+ *   - Every call shares the one array and it keeps the last call's contents: calls whose
+ *     work overlaps on the GPU (different streams, or different host threads without
+ *     ordering) race on it.  Calls on one stream are ordered and safe. */
+int tacsl_batch_forces_static(const tacsl_batch_desc* desc, const tacsl_sdf_set* set,
+                              const tacsl_contact_params* params, const tacsl_batch_io* io,
+                              tacsl_stream_t stream);
+
 /* The RGB image of every pad that has one (Sec. III-B; per image exactly
  * tacsl_shade_image with that model).  sensors must have the model sizes of the plan. */
 int tacsl_batch_shade(const tacsl_batch_plan* plan, const void* workspace, const tacsl_sensor_set* sensors,

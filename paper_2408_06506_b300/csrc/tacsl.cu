@@ -997,3 +997,123 @@ int tacsl_graph_destroy(tacsl_graph_t graph) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Batched force field without a caller-provided workspace
+// ===========================================================================
+//
+// Some callers cannot hand the library device memory for a workspace: a real-time
+// control loop where cudaMalloc / cudaFree would synchronise the device and stall the
+// step, or a plug-in running inside a host application that owns every device
+// allocation and allows none from its callbacks.  tacsl_batch_forces_static serves
+// them: the pad schedule and the two pad counters that tacsl_batch_forces keeps in the
+// caller's workspace live instead in the fixed array below, which exists on every GPU
+// that loads the library until the process exits.
+
+namespace {
+constexpr int64_t kStaticScratchBytes = int64_t(2) << 20;   // 2 MiB per GPU
+constexpr int kStaticMaxPads = static_cast<int>((kStaticScratchBytes - tacsl::kBatchHeader) / sizeof(tacsl::BatchPad));
+}  // namespace
+
+// Counters (first 256 bytes) and pad schedule of tacsl_batch_forces_static.  In host
+// code this name only stands for the array; its device address comes from
+// cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char tacsl_static_scratch[kStaticScratchBytes];
+
+namespace tacsl {
+namespace {
+
+unsigned char g_static_host[kStaticScratchBytes];   // host image of one call's scratch
+std::mutex g_static_mu;
+void* g_static_dev[kMaxDevices] = {};               // device address of the array, per device
+
+// The array's address on the current device, looked up on the first call there.
+int static_scratch_address(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(TACSL_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (g_static_dev[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, tacsl_static_scratch);
+        if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_static_dev[dev] = p;
+    }
+    *out = g_static_dev[dev];
+    return TACSL_OK;
+}
+
+}  // namespace
+}  // namespace tacsl
+
+extern "C" int tacsl_batch_forces_static(const tacsl_batch_desc* desc, const tacsl_sdf_set* set,
+                                         const tacsl_contact_params* params, const tacsl_batch_io* io,
+                                         tacsl_stream_t stream) {
+    // host-visible checks first: nothing below them touches the GPU on failure
+    if (desc == nullptr || io == nullptr) return fail(TACSL_ERR_INVALID_ARG, "batch description or io is NULL");
+    const int n = desc->n_pad;
+    if (n < 0) return fail(TACSL_ERR_INVALID_ARG, "n_pad = %d < 0", n);
+    if (n > kStaticMaxPads)
+        return fail(TACSL_ERR_UNSUPPORTED, "n_pad = %d exceeds the %d pads the static scratch (%lld bytes) holds", n,
+                    kStaticMaxPads, (long long)kStaticScratchBytes);
+    if (n > 0 && (desc->obj_id == nullptr || desc->layout == nullptr))
+        return fail(TACSL_ERR_INVALID_ARG, "obj_id and layout must be non-NULL");
+    if (n > 0 && (desc->n_layout < 1 || desc->layout_first == nullptr || desc->layout_count == nullptr))
+        return fail(TACSL_ERR_INVALID_ARG, "the batch needs at least one taxel layout");
+    for (int l = 0; l < desc->n_layout && n > 0; ++l) {
+        if (desc->layout_count[l] < 1 || desc->layout_count[l] > TACSL_MAX_TAXELS)
+            return fail(TACSL_ERR_INVALID_ARG, "layout %d: %d taxels outside [1, %d]", l, desc->layout_count[l],
+                        TACSL_MAX_TAXELS);
+        if (desc->layout_first[l] < 0 || desc->layout_first[l] + desc->layout_count[l] > desc->n_points)
+            return fail(TACSL_ERR_INVALID_ARG, "layout %d lies outside the taxel pool", l);
+    }
+    for (int b = 0; b < n; ++b) {
+        if (desc->obj_id[b] < 0 || desc->obj_id[b] >= TACSL_MAX_SDF)
+            return fail(TACSL_ERR_INVALID_ARG, "pad %d: obj_id %d out of range", b, desc->obj_id[b]);
+        if (desc->layout[b] < 0 || desc->layout[b] >= desc->n_layout)
+            return fail(TACSL_ERR_INVALID_ARG, "pad %d: layout %d out of range", b, desc->layout[b]);
+    }
+    SdfTable tab;
+    Params4 prm;
+    int rc = build_table(set, tab);
+    if (rc) return rc;
+    if ((rc = build_params(params, n, prm))) return rc;
+    if (n == 0) return ok();
+    const void* ptrs[] = {io->taxels, io->pad_pose, io->pad_twist, io->depth, io->f_n, io->f_t};
+    const char* names[] = {"taxels", "pad_pose", "pad_twist", "depth", "f_n", "f_t"};
+    for (int i = 0; i < 6; ++i) {
+        if (ptrs[i] == nullptr) return fail(TACSL_ERR_INVALID_ARG, "io.%s is NULL", names[i]);
+        if (!aligned(ptrs[i], 4)) return fail(TACSL_ERR_INVALID_ARG, "io.%s is not 4-byte aligned", names[i]);
+    }
+    if (io->wrench != nullptr && !aligned(io->wrench, 4))
+        return fail(TACSL_ERR_INVALID_ARG, "io.wrench is not 4-byte aligned");
+
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    void* scratch = nullptr;
+    if ((rc = static_scratch_address(&scratch))) return rc;
+
+    // the schedule as tacsl_batch_pack lays it out (largest layout first, outputs packed
+    // in pad order), behind 256 zero bytes: the pad counters start every call at zero
+    tacsl_batch_plan p;
+    memset(&p, 0, sizeof(p));
+    p.n_pad = n;
+    p.off_sched = kBatchHeader;
+    const size_t bytes = (size_t)kBatchHeader + sizeof(BatchPad) * (size_t)n;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    memset(g_static_host, 0, (size_t)kBatchHeader);
+    BatchPad* sched = reinterpret_cast<BatchPad*>(g_static_host + kBatchHeader);
+    int64_t out = 0;
+    for (int b = 0; b < n; ++b) {   // pad order first: output offsets
+        const int l = desc->layout[b];
+        sched[b] = BatchPad{b, desc->layout_count[l], desc->obj_id[b], 0, desc->layout_first[l], out};
+        out += desc->layout_count[l];
+    }
+    std::stable_sort(sched, sched + n, [](const BatchPad& a, const BatchPad& c) { return a.T > c.T; });
+    // from pageable memory the copy is staged before the call returns, so the host image
+    // may be rewritten by the next call as soon as the lock is released
+    const cudaError_t e = cudaMemcpyAsync(scratch, g_static_host, bytes, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "scratch upload: %s", cudaGetErrorString(e));
+    return launch_batch_forces(&p, scratch, tab, prm, io, *dev, 4, true, stream);
+}

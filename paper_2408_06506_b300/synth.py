@@ -544,7 +544,8 @@ def scene_batch(seed: int = 3, E: int = 16384, P: int = 2, grids: list | None = 
     pad.  A fraction ``no_image_frac`` of the pads has no image.
 
     ``depth_maps``: "exact" renders each pad's heightfield; "cycled" renders
-    ``n_distinct_maps`` per sensor model and hands them out in turn."""
+    ``n_distinct_maps`` per sensor model and hands them out in turn; "none" makes no
+    depth maps (the pads keep their sensor models)."""
     g = rng(seed)
     if grids is None:
         grids = grid_pool(seed + 1, n_grid, *grid_sides)
@@ -602,7 +603,7 @@ def scene_batch(seed: int = 3, E: int = 16384, P: int = 2, grids: list | None = 
     made = {}
     for b in range(n_pad):
         m = int(sensor[b])
-        if m < 0:
+        if m < 0 or depth_maps == "none":
             continue
         H, W = models[m][0].shape[2], models[m][0].shape[3]
         if depth_maps == "exact":
