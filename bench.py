@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--batch-envs", type=int, default=16384)
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-config", default=None,
+                    help="img_block,n_stages,force_np,force_dynamic for the batch step instead of autotuning")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="run only the uneven-batch section and print it as the JSON line (profiling aid)")
     return ap.parse_args()
 
 
@@ -73,7 +77,6 @@ def make_scene(envs, seed):
 
 def touched_sdf_bytes(sc):
     """Unique 32-byte sectors of the SDF grids the step's stencils touch (bench accounting)."""
-    total = 0
     from paper_2408_06506_b300.synth import quat_to_matrix
     pts_by_obj = {}
     for e in range(sc.E):
@@ -81,8 +84,16 @@ def touched_sdf_bytes(sc):
             pose = sc.pad_pose[e, p].astype(np.float64)
             xo = sc.taxels.astype(np.float64) @ quat_to_matrix(pose[3:]).T + pose[:3]
             pts_by_obj.setdefault(int(sc.obj_id[e]), []).append(xo)
+    return _touched_sectors(sc.grids, pts_by_obj)
+
+
+def _touched_sectors(grids, pts_by_obj):
+    """32-byte sectors of each grid covered by the 27-node windows of its in-domain points
+    (an upper bound on what the force kernel reads: only penetrating taxels read the
+    27-node window, the rest the 8-node cell inside it), in bytes."""
+    total = 0
     for i, g in pts_by_obj.items():
-        grid = sc.grids[i]
+        grid = grids[i]
         n = np.array(grid.data.shape[::-1])
         x = np.concatenate(g)
         u = (x - grid.origin.astype(np.float64)) / grid.voxel
@@ -96,6 +107,31 @@ def touched_sdf_bytes(sc):
                 mark[(lin + 2) // 8] = True
         total += int(mark.sum()) * 32
     return total
+
+
+def touched_sdf_bytes_batch(sc):
+    """touched_sdf_bytes for an uneven batch (synth.BatchScene)."""
+    from paper_2408_06506_b300.synth import quat_to_matrix
+    pts_by_obj = {}
+    for b in range(sc.n_pad):
+        l = sc.layout[b]
+        tax = sc.taxels[sc.layout_first[l]:sc.layout_first[l] + sc.layout_count[l]].astype(np.float64)
+        pose = sc.pad_pose[b].astype(np.float64)
+        pts_by_obj.setdefault(int(sc.obj_id[b]), []).append(tax @ quat_to_matrix(pose[3:]).T + pose[:3])
+    return _touched_sectors(sc.grids, pts_by_obj)
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch from profiles/<name>_traffic.txt, if taken on the current
+    sources of the files it lists (else None: the counters are stale)."""
+    tfile = os.path.join(ROOT, "profiles", f"{name}_traffic.txt")
+    if not os.path.exists(tfile):
+        return None
+    kv = dict(ln.strip().split("=", 1) for ln in open(tfile) if "=" in ln and not ln.startswith("#"))
+    files = kv.get("source_files", "").split(",")
+    if not files[0] or kv.get("source_hash") != _source_hash(files):
+        return None
+    return int(kv["dram_bytes_per_launch"])
 
 
 def algorithmic_bytes(sc, sdf_bytes):
@@ -416,12 +452,7 @@ def run_ours(args, rank, world, local_rank, dist):
     # dominant kernel: the image kernel; its compulsory bytes over its own event-timed launches
     img_bytes = parts["depth_map_read"] + parts["rgb_write"] + parts["shading_coeffs"]
     achieved = img_bytes / (breakdown["shade_image_ms"] * 1e-3) / 1e9
-    traffic = None   # ncu DRAM bytes per launch of the image kernel, if taken on these sources
-    tfile = os.path.join(ROOT, "profiles", "shade_kernel_traffic.txt")
-    if os.path.exists(tfile):
-        kv = dict(ln.strip().split("=", 1) for ln in open(tfile) if "=" in ln and not ln.startswith("#"))
-        if kv.get("source_hash") == _source_hash():
-            traffic = int(kv["dram_bytes_per_launch"])
+    traffic = profiled_traffic("shade_kernel")   # ncu DRAM bytes per launch, if taken on these sources
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -511,7 +542,12 @@ def run_batch(args, rank, world, local_rank, dist):
 
     default_ms = timed(lambda: plan.step(sdfs, params, taxels, pose, twist, depth_map, out=out), 10)
     t_tune = time.perf_counter()
-    tuned_ms = plan.autotune(sdfs, params, taxels, pose, twist, depth_map, out=out, reps=3)
+    if args.batch_config:
+        blk, ns, np_, dyn = (int(v) for v in args.batch_config.split(","))
+        plan.set_config(img_block=blk, n_stages=ns, force_np=np_, force_dynamic=dyn)
+        tuned_ms = None
+    else:
+        tuned_ms = plan.autotune(sdfs, params, taxels, pose, twist, depth_map, out=out, reps=3)
     t_tune = time.perf_counter() - t_tune
     graph = plan.graph(sdfs, params, taxels, pose, twist, depth_map, out)
     for _ in range(max(3, args.warmup)):
@@ -588,7 +624,10 @@ def run_batch(args, rank, world, local_rank, dist):
     coef_bytes = sum(72 * co.shape[2] * co.shape[3] for co, _, _ in sc.models)
     img_bytes = 7 * npx + coef_bytes
     nt = plan.n_taxel_out
-    force_bytes = 28 * nt + 12 * nt + 52 * sc.n_pad + 24 * sc.n_pad + 16 * sc.n_pad   # outputs, taxel reads, pads
+    sdf_bytes = touched_sdf_bytes_batch(sc)
+    # outputs 28 B/taxel; the taxel pool once; per pad: pose + twist 52 B, wrench 24 B,
+    # contact parameters 16 B, schedule entry 32 B; the SDF sectors the stencils touch
+    force_bytes = (28 * nt + 12 * int(sc.layout_count.sum()) + (52 + 24 + 16 + 32) * sc.n_pad + sdf_bytes)
     taxel_pts = world * nt
     images = world * plan.plan.n_image
     return {
@@ -600,11 +639,16 @@ def run_batch(args, rank, world, local_rank, dist):
         "value": taxel_pts / (ms_step * 1e-3), "unit": "taxel-points/s",
         "images_per_s": images / (ms_step * 1e-3), "pixels_per_s": world * npx / (ms_step * 1e-3),
         "default_config_ms": default_ms, "tuned_config": plan.config(), "autotune_estimate_ms": tuned_ms,
+        "config_source": "given (--batch-config)" if args.batch_config else "tacsl_batch_autotune",
         "autotune_s": t_tune, "generation_s": t_gen,
         "kernel_ms": {"batch_shade_kernel": shade_ms, "batch_force_kernel": forces_ms},
         "roofline": {"bound": "hbm", "kernel": "tacsl::batch_shade_kernel", "algorithmic_bytes": img_bytes,
                      "achieved": img_bytes / (shade_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": img_bytes / (shade_ms * 1e-3) / 1e9 / peak},
+                     "frac": img_bytes / (shade_ms * 1e-3) / 1e9 / peak,
+                     "traffic": profiled_traffic("batch_shade_kernel")},
+        "roofline_force": {"bound": "hbm", "kernel": "tacsl::batch_force_kernel", "algorithmic_bytes": force_bytes,
+                           "sdf_sectors_touched": sdf_bytes, "achieved": force_bytes / (forces_ms * 1e-3) / 1e9,
+                           "frac": force_bytes / (forces_ms * 1e-3) / 1e9 / peak},
         "roofline_step": {"algorithmic_bytes": img_bytes + force_bytes,
                           "frac": (img_bytes + force_bytes) / (ms_step * 1e-3) / 1e9 / peak},
         "plain_grouped": {"launches_per_step": len(sc.models) + len(sc.layout_count), "ms_per_step": grouped_ms,
@@ -626,12 +670,13 @@ def _smi_id(ordinal):
         return str(ordinal)
 
 
-def _source_hash():
+def _source_hash(files):
+    """Hash of the named files under paper_2408_06506_b300/csrc (the kernel's sources)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2408_06506_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in sorted(files):
+        h.update(open(os.path.join(csrc, f.strip()), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -651,6 +696,18 @@ def main():
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
         dist = tdist
     try:
+        if args.only_batch:
+            import torch
+            torch.cuda.set_device(local_rank)
+            from paper_2408_06506_b300 import build
+            if rank == 0:
+                build.build()
+            if dist is not None:
+                dist.barrier()
+            out = run_batch(args, rank, world, local_rank, dist)
+            if rank == 0:
+                print(json.dumps({"impl": "ours", "section": "batch", "n_gpus": world, **out}), flush=True)
+            return
         run_ours(args, rank, world, local_rank, dist)
     finally:
         if dist is not None:

@@ -86,7 +86,7 @@ typedef struct {
     int32_t img_block;        /* images per work item of the image kernel: a power of two <= 1024, 0 = auto */
     int32_t n_stages;         /* depth-map stages in flight per CTA: 2..12, 0 = as many as fit */
     int32_t force_np;         /* taxels in flight per lane in the force kernel: 2 or 4 (0 = 4) */
-    int32_t force_dynamic;    /* 1: pads dealt from a counter (largest first); 0: round-robin */
+    int32_t force_dynamic;    /* 1: pads dealt from a counter in schedule order (by object, largest first); 0: round-robin */
     /* library-owned */
     int32_t n_model;
     int32_t max_w;

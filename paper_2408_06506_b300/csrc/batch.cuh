@@ -3,17 +3,17 @@
 // pad free to carry its own taxel layout, object and camera model).
 //
 // Force field: one warp per pad, as in the uniform kernel, but the pads come from a
-// schedule in the workspace (largest first) with their own taxel count, layout, object
-// and output offset.  Pads are dealt either round-robin or from a counter that each warp
+// schedule in the workspace (grouped by object, largest first within an object) with their
+// own taxel count, layout, object and output offset.  Pads are dealt either round-robin or from a counter that each warp
 // bumps when it takes a pad (the next ticket is fetched while the current pad runs); the
 // last warp out returns the counter to zero, so consecutive launches - and graph replays
 // - need no reset in between.
 //
 // Image: the uniform kernel's producer / compute-warp pipeline with work items over
-// (sensor model, block of M images of that model, tile).  Each model brings its own
-// size, pixel pitch and coefficients; its images are listed contiguously in the
-// workspace with their first pixel in the packed depth_map / rgb arrays, so an item's
-// images need no filtering on the GPU.
+// (sensor model, block of M images of that model, tile), dealt from a counter.  Each
+// model brings its own size, pixel pitch and coefficients; its images are listed
+// contiguously in the workspace with their first pixel in the packed depth_map / rgb
+// arrays, so an item's images need no filtering on the GPU.
 #pragma once
 
 #include "common.cuh"
@@ -107,6 +107,7 @@ struct BatchShadeArgs {
     const int64_t* img_px;   // image list: first pixel of each image in depth / rgb
     const float* depth;      // packed depth maps, 16-byte aligned
     uint8_t* rgb;            // packed RGB, 16-byte aligned
+    unsigned int* ticket;    // [0]: next work item, [1]: CTAs finished; both 0 between launches
     int n_model, M, n_items, n_stages, stage_floats;
 };
 
@@ -138,9 +139,15 @@ __device__ __forceinline__ void batch_load_coefficients(const BatchShadeArgs& A,
         bulk_g2s(smem_u32(coef + r * kShTile), src + static_cast<int64_t>(r) * HW, row_bytes, smem_u32(cfull), pol);
 }
 
-// Producer warp: as in the uniform kernel (coefficients one item ahead, each image's
-// tile plus halo rows into the stage ring); the item's images are a contiguous range
-// of the image list, whose pixel offsets the warp reads 32 at a time.
+// Producer warp: as in the uniform kernel (each image's tile plus halo rows into the
+// stage ring; the next item's coefficients staged while the current item's images are
+// still being issued), but items are dealt from a counter: a CTA draws its next item when
+// its current one has about a ring's worth of images left to issue.  So consecutive items
+// - neighbouring tiles of the same images - start within microseconds of each other on
+// whichever CTAs are free, and the rows one tile reads as its halo are still in L2 when
+// its neighbour reads them as its own (with a fixed round-robin, items of different
+// models take different times and the CTAs drift apart).  The last producer out resets
+// the counters.
 __device__ __forceinline__ void batch_shade_producer(const BatchShadeArgs& A, unsigned char* smem) {
     const int lane = threadIdx.x & 31;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffFull);
@@ -155,19 +162,22 @@ __device__ __forceinline__ void batch_shade_producer(const BatchShadeArgs& A, un
     int st = 0;
     uint32_t ph = 0, cph = 0;
     bool ok = true;
-    int k = blockIdx.x;
-    if (k < A.n_items && lane == 0) batch_load_coefficients(A, k, coef, cfull, pol_keep);
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(A.ticket, 1u);
+    int k = static_cast<int>(__shfl_sync(0xffffffffu, t, 0));
+    if (k < A.n_items && lane == 0) batch_load_coefficients(A, k, coef, cfull, pol_keep);   // buffer starts free
     while (k < A.n_items && ok) {
-        const int kn = k + gridDim.x;
-        bool next_loaded = kn >= A.n_items;
         const BatchItem it = batch_item(A, k);
         const int W = A.mdl[it.m].W, HW = A.mdl[it.m].HW;
         const int i0 = A.mdl[it.m].img_begin + it.blk * A.M;
         const int i1 = min(i0 + A.M, A.mdl[it.m].img_end);
+        const int draw_at = max(i1 - NS, i0 + 1);   // draw the next item after issuing this image
         const int tile_start = it.tile * kShTile;
         const int tile_px = min(kShTile, HW - tile_start);
         const int lo_px = max(tile_start - W, 0);
         const uint32_t bytes = static_cast<uint32_t>(min(tile_start + tile_px + W, HW) - lo_px) * 4u;
+        int kn = A.n_items;
+        bool drawn = false, next_loaded = false;
         for (int base = i0; base < i1 && ok; base += 32) {
             const int64_t px = base + lane < i1 ? __ldg(A.img_px + base + lane) : 0;
             const int cnt = min(32, i1 - base);
@@ -183,33 +193,46 @@ __device__ __forceinline__ void batch_shade_producer(const BatchShadeArgs& A, un
                         raise_dev_error(TACSL_DEVERR_TIMEOUT);
                         ok = false;
                     }
-                    if (ok && !next_loaded && mbar_test(smem_u32(cempty), cph)) {
+                    if (ok && !drawn && base + j + 1 >= draw_at) {
+                        kn = static_cast<int>(atomicAdd(A.ticket, 1u));
+                        drawn = true;
+                        next_loaded = kn >= A.n_items;
+                    }
+                    // stage the next item's coefficients once item k's have been taken
+                    if (ok && drawn && !next_loaded && mbar_test(smem_u32(cempty), cph)) {
                         batch_load_coefficients(A, kn, coef, cfull, pol_keep);
                         next_loaded = true;
                     }
                 }
                 ok = __shfl_sync(0xffffffffu, ok, 0);
-                next_loaded = __shfl_sync(0xffffffffu, next_loaded, 0);
                 if (++st == NS) { st = 0; ph ^= 1u; }
             }
         }
-        if (ok && !next_loaded) {
-            if (lane == 0) {
-                if (mbar_wait_bounded(smem_u32(cempty), cph))
-                    batch_load_coefficients(A, kn, coef, cfull, pol_keep);
-                else {
-                    raise_dev_error(TACSL_DEVERR_TIMEOUT);
-                    ok = false;
-                }
+        if (lane == 0 && ok && !next_loaded) {
+            // item k ended before its coefficients were taken: wait for that, then stage kn
+            if (mbar_wait_bounded(smem_u32(cempty), cph))
+                batch_load_coefficients(A, kn, coef, cfull, pol_keep);
+            else {
+                raise_dev_error(TACSL_DEVERR_TIMEOUT);
+                ok = false;
             }
-            ok = __shfl_sync(0xffffffffu, ok, 0);
         }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        kn = __shfl_sync(0xffffffffu, kn, 0);
         cph ^= 1u;
         k = kn;
     }
-    if (lane == 0 && mbar_wait_bounded(smem_u32(&empty[st]), ph ^ 1u)) {
-        meta[st] = make_int2(-1, -1);
-        mbar_arrive(smem_u32(&full[st]));
+    if (lane == 0) {
+        if (mbar_wait_bounded(smem_u32(&empty[st]), ph ^ 1u)) {
+            meta[st] = make_int2(-1, -1);
+            mbar_arrive(smem_u32(&full[st]));
+        }
+        // every ticket of this CTA has been drawn; the last producer out resets the counters
+        __threadfence();
+        if (atomicAdd(A.ticket + 1, 1u) == gridDim.x - 1) {
+            atomicExch(A.ticket, 0u);
+            atomicExch(A.ticket + 1, 0u);
+        }
     }
 }
 

@@ -576,10 +576,12 @@ int batch_pack(const tacsl_batch_plan* plan, const tacsl_batch_desc* d, void* ho
         return fail(TACSL_ERR_INVALID_ARG, "batch description differs from the one the plan was made for");
     unsigned char* base = static_cast<unsigned char*>(host);
     memset(base, 0, (size_t)plan->workspace_bytes);
-    // pad schedule: largest taxel count first (ties in pad order)
+    // pad schedule: grouped by object (the pads in flight then share one grid's touched
+    // sectors in L2), largest taxel count first within an object, ties in pad order
     std::vector<int32_t> order(d->n_pad);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        if (d->obj_id[a] != d->obj_id[b]) return d->obj_id[a] < d->obj_id[b];
         return d->layout_count[d->layout[a]] > d->layout_count[d->layout[b]];
     });
     std::vector<int64_t> out(d->n_pad), px(d->n_pad, -1);
@@ -754,6 +756,8 @@ int launch_batch_shade(const tacsl_batch_plan* plan, const void* ws, const tacsl
     }
     if (items >= (int64_t(1) << 31)) return fail(TACSL_ERR_UNSUPPORTED, "too many work items");
     a.img_px = reinterpret_cast<const int64_t*>(static_cast<const unsigned char*>(ws) + plan->off_images);
+    // the image kernel's item counter: words 2-3 of the workspace header (0-1: force kernel)
+    a.ticket = static_cast<unsigned int*>(const_cast<void*>(ws)) + 2;
     a.depth = io->depth_map;
     a.rgb = io->rgb;
     a.n_model = plan->n_model;
@@ -1094,8 +1098,9 @@ extern "C" int tacsl_batch_forces_static(const tacsl_batch_desc* desc, const tac
     void* scratch = nullptr;
     if ((rc = static_scratch_address(&scratch))) return rc;
 
-    // the schedule as tacsl_batch_pack lays it out (largest layout first, outputs packed
-    // in pad order), behind 256 zero bytes: the pad counters start every call at zero
+    // the schedule as tacsl_batch_pack lays it out (by object, largest layout first,
+    // outputs packed in pad order), behind 256 zero bytes: the pad counters start every
+    // call at zero
     tacsl_batch_plan p;
     memset(&p, 0, sizeof(p));
     p.n_pad = n;
@@ -1110,7 +1115,9 @@ extern "C" int tacsl_batch_forces_static(const tacsl_batch_desc* desc, const tac
         sched[b] = BatchPad{b, desc->layout_count[l], desc->obj_id[b], 0, desc->layout_first[l], out};
         out += desc->layout_count[l];
     }
-    std::stable_sort(sched, sched + n, [](const BatchPad& a, const BatchPad& c) { return a.T > c.T; });
+    std::stable_sort(sched, sched + n, [](const BatchPad& a, const BatchPad& c) {
+        return a.obj != c.obj ? a.obj < c.obj : a.T > c.T;
+    });
     // from pageable memory the copy is staged before the call returns, so the host image
     // may be rewritten by the next call as soon as the lock is released
     const cudaError_t e = cudaMemcpyAsync(scratch, g_static_host, bytes, cudaMemcpyHostToDevice, stream);

@@ -82,8 +82,8 @@ def test_pack_schedule_and_image_list(lib):
                           dtype=[("pad", "<i4"), ("T", "<i4"), ("obj", "<i4"), ("unused", "<i4"),
                                  ("first", "<i8"), ("out", "<i8")])
     T = counts[layout]
-    # largest first, ties in pad order (a stable sort of the pads by -T)
-    assert np.array_equal(sched["pad"], np.argsort(-T, kind="stable"))
+    # grouped by object, largest first within an object, ties in pad order
+    assert np.array_equal(sched["pad"], np.lexsort((np.arange(n), -T, obj)))
     b = sched["pad"]
     assert np.array_equal(sched["T"], T[b])
     assert np.array_equal(sched["obj"], obj[b])
