@@ -1,0 +1,334 @@
+"""Pins of the FP64 gradient oracle (oracle/grad.py), CPU only.
+
+The gradient oracle restates the force law and the shading in float64 torch ops and
+lets autograd differentiate them.  It is pinned to things other than itself:
+  * its forward equals the C oracle's (which the other pin files fix);
+  * its gradients equal float64 central differences of the C oracle, h = 1e-6 (Sec. III-C
+    force law; the differentiated step of the calibration workload), on pads whose
+    taxels all lie away from kinks;
+  * closed forms: d f_n/d k_n = depth n; in stick d f_t/d k_t = f_t/k_t and in slip
+    d f_t/d mu = f_t/mu; a half-space whose SDF is exactly linear; d I/d A_k = m_k; on an
+    undeformed gel d I(q)/d D(q +- 1) = +-A_1(q)/(2 pitch_x), d I(q)/d D(q +- W) =
+    +-A_2(q)/(2 pitch_y);
+  * planted mistakes in a copy of the module fail at least one of the checks above.
+"""
+import importlib.util
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import grad as G0
+from paper_2408_06506_b300 import synth
+
+H_FD = 1e-6
+
+
+# ---------------------------------------------------------------------------
+# scenes and kink margins
+# ---------------------------------------------------------------------------
+
+def _scene(seed=3):
+    grids = synth.object_set(seed, n_obj=3, n=40)
+    sc = synth.scene_objects(seed=seed, E=12, P=2, ny=6, nx=7, pitch=1.5e-3, grids=grids, depth_maps="none",
+                             vel_sigma=0.05)
+    sc.k_d = np.full(sc.E, 3.0, np.float32)     # exercise the damping term
+    return sc
+
+
+def _margins_ok(G, grid, taxels, pose, twist, kn, kd, kt, mu):
+    """True when every taxel of the pad is away from every kink by more than an FD step
+    moves it: contact on/off, the domain boundary, interpolation cell faces (centre and
+    the +-h/2 points), the unilateral clamp, stick/slip, v_t = 0."""
+    with torch.no_grad():
+        gt = G.grid_tensors(grid)
+        R = G.rotation(torch.tensor(pose[3:7], dtype=torch.float64))
+        tax = torch.tensor(taxels, dtype=torch.float64)
+        x = tax @ R.T + torch.tensor(pose[:3], dtype=torch.float64)
+        data, origin, h = gt
+        u = ((x - origin) / h).numpy()
+        n = np.array([data.shape[2], data.shape[1], data.shape[0]])
+        inside = np.all((u >= 0.5) & (u <= n - 1.5), axis=1)
+        edge = np.minimum(np.abs(u - 0.5), np.abs(u - (n - 1.5))).min(axis=1)
+        if np.any(edge < 0.05):
+            return False
+        phi, g, _ = G.sdf_eval(gt, x)
+        phi = phi.numpy()
+        if np.any(inside & (np.abs(phi) < 2e-5)):
+            return False
+        con = inside & (phi < 0)
+        for off in (0.0, 0.5, -0.5):
+            fr = u[con] + off
+            if np.any(np.abs(fr - np.rint(fr)) < 0.03):
+                return False
+        if con.any():
+            xd = torch.tensor(twist[:3], dtype=torch.float64) + torch.cross(
+                torch.tensor(twist[3:], dtype=torch.float64).expand_as(x), x, dim=1)
+            gg = g.numpy()[con]
+            nn = gg / np.linalg.norm(gg, axis=1, keepdims=True)
+            xdc = xd.numpy()[con]
+            ddot = (nn * xdc).sum(1)
+            mag = (-kn + kd * ddot) * phi[con]
+            if np.any(mag < 1e-3 * kn * np.abs(phi[con])):
+                return False
+            vt = xdc - ddot[:, None] * nn
+            s = np.linalg.norm(vt, axis=1)
+            if np.any(s < 1e-4):
+                return False
+            cap, lim = kt * s, mu * mag
+            if np.any(np.abs(cap - lim) < 1e-3 * np.maximum(cap, lim)):
+                return False
+    return True
+
+
+def _clean_pads(G, sc, want=4):
+    out = []
+    for e in range(sc.E):
+        for p in range(sc.P):
+            args = (sc.grids[sc.obj_id[e]], sc.taxels, sc.pad_pose[e, p], sc.pad_twist[e, p], float(sc.k_n[e]),
+                    float(sc.k_d[e]), float(sc.k_t[e]), float(sc.mu[e]))
+            if _margins_ok(G, *args):
+                # keep pads in contact (otherwise every gradient is zero)
+                with torch.no_grad():
+                    d = G.pad_forces(G.grid_tensors(args[0]), torch.tensor(sc.taxels, dtype=torch.float64),
+                                     torch.tensor(args[2], dtype=torch.float64),
+                                     torch.tensor(args[3], dtype=torch.float64), *[torch.tensor(v) for v in args[4:]])[0]
+                if (d > 0).sum() >= 3:
+                    out.append((e, p))
+        if len(out) >= want:
+            break
+    return out
+
+
+def _weights(rng, T):
+    return rng.normal(size=T), rng.normal(size=(T, 3)), rng.normal(size=(T, 3)), rng.normal(size=6)
+
+
+def _c_loss(sc, e, p, pose, twist, prm, w):
+    r = oracle.penalty_forces(sc.grids, sc.taxels, sc.obj_id[e:e + 1], pose[None, None], twist[None, None], *prm)
+    return (np.sum(w[0] * r["depth"][0, 0]) + np.sum(w[1] * r["f_n"][0, 0]) + np.sum(w[2] * r["f_t"][0, 0]) +
+            np.sum(w[3] * r["wrench"][0, 0]))
+
+
+def _fd(f, x, j, h=H_FD):
+    """Central difference of f at float32 vector x along component j; the step is the
+    exact difference of the two float32 arguments."""
+    xp, xm = x.copy(), x.copy()
+    xp[j] = np.float32(x[j] + h)
+    xm[j] = np.float32(x[j] - h)
+    return (f(xp) - f(xm)) / (float(xp[j]) - float(xm[j]))
+
+
+# ---------------------------------------------------------------------------
+# checks (take the module under test, so planted mistakes can be run through them)
+# ---------------------------------------------------------------------------
+
+def check_forward_matches_c_oracle(G):
+    sc = _scene()
+    rng = np.random.default_rng(0)
+    T = sc.T
+    z = np.zeros((sc.E, sc.P, T, 3))
+    out = G.force_gradients(sc.grids, sc.taxels, sc.obj_id, sc.pad_pose, sc.pad_twist, sc.k_n, sc.k_d, sc.k_t,
+                            sc.mu, rng.normal(size=(sc.E, sc.P, T)), z, z)
+    ref = oracle.penalty_forces(sc.grids, sc.taxels, sc.obj_id, sc.pad_pose, sc.pad_twist, sc.k_n, sc.k_d, sc.k_t,
+                                sc.mu)
+    assert (ref["depth"] > 0).sum() > 20
+    for k in ("depth", "f_n", "f_t", "wrench"):
+        scale = np.abs(ref[k]).max() + 1e-30
+        assert np.abs(out[k] - ref[k]).max() <= 1e-12 * scale, k
+
+
+def check_intensity_matches_c_oracle(G):
+    rng = np.random.default_rng(1)
+    H, W, S, B = 9, 12, 2, 3
+    co = synth.shading_coeffs(S, H, W, 5)
+    dm = (synth.D0 + 2e-4 * rng.normal(size=(B, H, W))).astype(np.float32)
+    sid = np.array([0, 1, 1], np.int32)
+    out = G.shade_gradients(co, 1e-4, 1.5e-4, sid, dm, np.zeros((B, H, W, 3)))
+    _, inten, bad = oracle.shade(co, 1e-4, 1.5e-4, sid, dm, with_intensity=True)
+    assert bad == 0
+    assert np.abs(out["intensity"] - np.clip(inten, 0, 255)).max() <= 1e-9
+
+
+def check_force_gradients_match_central_differences(G):
+    sc = _scene()
+    pads = _clean_pads(G, sc, want=3)
+    assert len(pads) >= 2
+    rng = np.random.default_rng(2)
+    T = sc.T
+    for e, p in pads:
+        w = _weights(rng, T)
+        gd = np.zeros((1, 1, T)); gd[0, 0] = w[0]
+        gfn = np.zeros((1, 1, T, 3)); gfn[0, 0] = w[1]
+        gft = np.zeros((1, 1, T, 3)); gft[0, 0] = w[2]
+        gw = w[3][None, None]
+        prm = [np.array([v[e]], np.float32) for v in (sc.k_n, sc.k_d, sc.k_t, sc.mu)]
+        got = G.force_gradients(sc.grids, sc.taxels, sc.obj_id[e:e + 1], sc.pad_pose[e:e + 1, p:p + 1],
+                                sc.pad_twist[e:e + 1, p:p + 1], *prm, gd, gfn, gft, gw)
+        pose, tw = sc.pad_pose[e, p].copy(), sc.pad_twist[e, p].copy()
+        fd_pose = np.array([_fd(lambda x: _c_loss(sc, e, p, x, tw, prm, w), pose, j) for j in range(7)])
+        fd_tw = np.array([_fd(lambda x: _c_loss(sc, e, p, pose, x, prm, w), tw, j) for j in range(6)])
+        fd_prm = []
+        for i in range(4):
+            def f(x, i=i):
+                pr = list(prm)
+                pr[i] = x
+                return _c_loss(sc, e, p, pose, tw, pr, w)
+            fd_prm.append(_fd(f, prm[i].copy(), 0, h=H_FD * max(1.0, abs(float(prm[i][0])))))
+        for name, a, b in (("pose", got["pose"][0, 0], fd_pose), ("twist", got["twist"][0, 0], fd_tw),
+                           ("params", np.array([got[k][0] for k in ("k_n", "k_d", "k_t", "mu")]), np.array(fd_prm))):
+            assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max() + 1e-9, (name, a, b)
+
+
+def check_closed_forms_kn_kt_mu(G):
+    sc = _scene()
+    rng = np.random.default_rng(3)
+    T = sc.T
+    seen_stick = seen_slip = False
+    for e in range(sc.E):
+        for p in range(sc.P):
+            prm = [np.array([v[e]], np.float32) for v in (sc.k_n, sc.k_d, sc.k_t, sc.mu)]
+            wfn = rng.normal(size=(1, 1, T, 3))
+            z1, z3 = np.zeros((1, 1, T)), np.zeros((1, 1, T, 3))
+            a = G.force_gradients(sc.grids, sc.taxels, sc.obj_id[e:e + 1], sc.pad_pose[e:e + 1, p:p + 1],
+                                  sc.pad_twist[e:e + 1, p:p + 1], *prm, z1, wfn, z3)
+            fn = a["f_n"][0, 0]
+            mag = np.linalg.norm(fn, axis=1)
+            on = mag > 0
+            if not on.any():
+                continue
+            # d f_n / d k_n = depth * n  (d mag / d k_n = -phi = depth)
+            want = np.sum(wfn[0, 0][on] * (a["depth"][0, 0][on, None] * fn[on] / mag[on, None]))
+            assert abs(a["k_n"][0] - want) <= 1e-9 * (abs(want) + 1e-12)
+            # shear: stick -> f_t = -u k_t |v_t| (d/dk_t = f_t/k_t), slip -> f_t = -u mu |f_n| (d/dmu = f_t/mu)
+            wft = rng.normal(size=(1, 1, T, 3))
+            b = G.force_gradients(sc.grids, sc.taxels, sc.obj_id[e:e + 1], sc.pad_pose[e:e + 1, p:p + 1],
+                                  sc.pad_twist[e:e + 1, p:p + 1], *prm, z1, z3, wft)
+            ft = b["f_t"][0, 0]
+            ftn = np.linalg.norm(ft, axis=1)
+            slip = on & (np.abs(ftn - float(prm[3][0]) * mag) <= 1e-9 * (mag + 1e-30))
+            stick = on & (ftn > 0) & ~slip
+            seen_slip |= slip.any()
+            seen_stick |= stick.any()
+            want_kt = np.sum(wft[0, 0][stick] * ft[stick]) / float(prm[2][0])
+            want_mu = np.sum(wft[0, 0][slip] * ft[slip]) / float(prm[3][0])
+            assert abs(b["k_t"][0] - want_kt) <= 1e-9 * (abs(want_kt) + 1e-12)
+            assert abs(b["mu"][0] - want_mu) <= 1e-9 * (abs(want_mu) + 1e-12)
+    assert seen_stick and seen_slip
+
+
+def check_half_space(G):
+    """phi = z baked on a grid (trilinear and its differences are exact for a linear
+    field); an unrotated pad at depth delta with normal velocity v_z:
+    F_z = T (k_n - k_d v_z) delta, so dF_z/dt_z = -T (k_n - k_d v_z), dF_z/dv_z = -T k_d delta,
+    dF_z/dk_n = T delta, dF_z/dt_x = dF_z/dt_y = 0, and a rotation about z does not change F_z."""
+    n, h = 24, 5e-4
+    grid = synth.bake_field(lambda x, y, z: z, (n, n, n), h, [-(n - 1) * h / 2] * 3)
+    tax = synth.taxel_grid(3, 4, 1e-3)
+    T = tax.shape[0]
+    delta, vz, kn, kd = 7.25e-4, 0.03, 1.0e4, 5.0
+    pose = np.array([[[0.0, 0.0, -delta, 1.0, 0.0, 0.0, 0.0]]], np.float32)
+    twist = np.array([[[0.0, 0.0, vz, 0.0, 0.0, 0.0]]], np.float32)
+    gw = np.array([[[0.0, 0.0, 1.0, 0.0, 0.0, 0.0]]])       # L = F_z
+    z1, z3 = np.zeros((1, 1, T)), np.zeros((1, 1, T, 3))
+    r = G.force_gradients([grid], tax, [0], pose, twist, kn, kd, 100.0, 0.5, z1, z3, z3, gw)
+    d, v = float(np.float32(delta)), float(np.float32(vz))
+    assert abs(r["wrench"][0, 0, 2] - T * (kn - kd * v) * d) <= 1e-9 * kn * d * T
+    g = r["pose"][0, 0]
+    assert abs(g[2] - (-T * (kn - kd * v))) <= 1e-9 * kn * T
+    assert abs(g[0]) <= 1e-9 * kn and abs(g[1]) <= 1e-9 * kn
+    assert abs(g[6]) <= 1e-9 * kn          # q_z at the identity: rotation about the normal
+    assert abs(r["twist"][0, 0, 2] - (-T * kd * d)) <= 1e-9 * kd * d * T
+    assert abs(r["k_n"][0] - T * d) <= 1e-12 * T
+
+
+def check_shading_closed_forms(G):
+    rng = np.random.default_rng(4)
+    H, W = 7, 9
+    px, py = 1e-4, 2e-4
+    co = synth.shading_coeffs(1, H, W, 9)
+    # d L / d A_k[c, q] = sum_b g[b, q, c] m_k(b, q) with the C oracle's normals
+    dm = (synth.D0 + 1e-4 * rng.normal(size=(2, H, W))).astype(np.float32)
+    gI = rng.normal(size=(2, H, W, 3))
+    out = G.shade_gradients(co, px, py, [0, 0], dm, gI)
+    _, inten, _ = oracle.shade(co, px, py, [0, 0], dm, with_intensity=True)
+    want = np.zeros((6, 3, H, W))
+    for b in range(2):
+        nrm = oracle.depth_normals(dm[b], px, py)
+        m = np.stack([np.ones((H, W)), nrm[..., 0], nrm[..., 1], nrm[..., 0] ** 2, nrm[..., 1] ** 2,
+                      nrm[..., 0] * nrm[..., 1]])
+        live = (inten[b] > 0) & (inten[b] < 255)                  # [H, W, 3]
+        for c in range(3):
+            want[:, c] += m * np.where(live[..., c], gI[b, ..., c], 0.0)
+    assert np.abs(out["coeffs"][0] - want).max() <= 1e-9 * np.abs(want).max()
+    # undeformed gel, one-hot upstream gradient at an interior pixel q, channel c
+    flat = np.full((1, H, W), synth.D0, np.float32)
+    qy, qx, c = 3, 4, 1
+    g1 = np.zeros((1, H, W, 3))
+    g1[0, qy, qx, c] = 1.0
+    gd = G.shade_gradients(co, px, py, [0], flat, g1)["depth"][0]
+    A1, A2 = float(co[0, 1, c, qy, qx]), float(co[0, 2, c, qy, qx])
+    px, py = float(np.float32(px)), float(np.float32(py))       # the pitches the images carry
+    want = np.zeros((H, W))
+    want[qy, qx + 1], want[qy, qx - 1] = A1 / (2 * px), -A1 / (2 * px)
+    want[qy + 1, qx], want[qy - 1, qx] = A2 / (2 * py), -A2 / (2 * py)
+    assert np.abs(gd - want).max() <= 1e-9 * np.abs(want).max()
+
+
+CHECKS = [check_forward_matches_c_oracle, check_intensity_matches_c_oracle,
+          check_force_gradients_match_central_differences, check_closed_forms_kn_kt_mu, check_half_space,
+          check_shading_closed_forms]
+
+
+@pytest.mark.parametrize("check", CHECKS, ids=[c.__name__ for c in CHECKS])
+def test_gradient_oracle(orc, check):
+    check(G0)
+
+
+# ---------------------------------------------------------------------------
+# planted mistakes
+# ---------------------------------------------------------------------------
+
+MUTATIONS = {
+    "omega_cross_order": ("torch.cross(w.expand_as(x), x, dim=1)", "torch.cross(x, w.expand_as(x), dim=1)"),
+    "pose_transposed": ("x = taxels @ R.T + pose[0:3]", "x = taxels @ R + pose[0:3]"),
+    "output_not_rotated_back": ("fn_pad = fn_all @ R  ", "fn_pad = fn_all @ R.T  "),
+    "fd_step": ("e[a] = 0.5", "e[a] = 1.0"),
+    "normal_edge_central": ("first = (sl(1, 2) - sl(0, 1)) / pitch", "first = (sl(1, 2) - sl(0, 1)) / (2 * pitch)"),
+    "damping_sign": ("mraw = (-kn + kd * ddot) * ph", "mraw = (-kn - kd * ddot) * ph"),
+    "friction_cap_max": ("torch.where(cap.detach() < lim.detach(), cap, lim)",
+                         "torch.where(cap.detach() > lim.detach(), cap, lim)"),
+    "intensity_unclamped": ("return torch.clamp(I, 0.0, 255.0).permute(1, 2, 0)", "return I.permute(1, 2, 0)"),
+    "monomial_swap": ("m = torch.stack([torch.ones_like(nx), nx, ny, nx * nx, ny * ny, nx * ny])",
+                      "m = torch.stack([torch.ones_like(nx), ny, nx, nx * nx, ny * ny, nx * ny])"),
+}
+
+
+def _load_variant(src, tmp_path, name):
+    f = tmp_path / f"grad_{name}.py"
+    f.write_text(src)
+    spec = importlib.util.spec_from_file_location(f"grad_{name}", str(f))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_every_mutation_site_exists():
+    src = open(G0.__file__).read()
+    for name, (old, _) in MUTATIONS.items():
+        assert src.count(old) == 1, name
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(orc, name, tmp_path):
+    old, new = MUTATIONS[name]
+    mod = _load_variant(open(G0.__file__).read().replace(old, new), tmp_path, name)
+    caught = False
+    for check in CHECKS:
+        try:
+            check(mod)
+        except AssertionError:
+            caught = True
+            break
+    assert caught, f"mutation {name} survived the gradient-oracle pins"
