@@ -51,11 +51,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--grad-envs", type=int, default=1024)
+    ap.add_argument("--grad-steps", type=int, default=20)
+    ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--batch-envs", type=int, default=16384)
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-config", default=None,
                     help="img_block,n_stages,force_np,force_dynamic for the batch step instead of autotuning")
+    ap.add_argument("--only-grad", action="store_true",
+                    help="run only the calibration (gradient) section and print it as the JSON line")
     ap.add_argument("--only-batch", action="store_true",
                     help="run only the uneven-batch section and print it as the JSON line (profiling aid)")
     return ap.parse_args()
@@ -435,6 +440,7 @@ def run_ours(args, rank, world, local_rank, dist):
                "path": "pinned host -> cudaMemcpyAsync -> tacsl_tactile_step -> pinned host, one stream"}
 
     batch = None if args.no_batch else run_batch(args, rank, world, local_rank, dist)
+    grad = None if args.no_grad else run_grad(args, rank, world, local_rank, dist)
 
     if rank != 0:
         return
@@ -481,6 +487,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "breakdown": breakdown,
         "render_step": render,
         "batch": batch,
+        "grad": grad,
         "gpu_launches": 2 * args.steps,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -660,6 +667,126 @@ def run_batch(args, rank, world, local_rank, dist):
     }
 
 
+GRAD_WORKLOAD = ("1024 envs x 2 pads x 20x25 taxels, 8 SDFs 128^3 f32, 2048 depth maps 320x240 (2 sensors); "
+                 "loss = MSE of f_n, f_t and the clamped intensity against seeded targets; gradients w.r.t. pad pose, "
+                 "twist, per-env k_n, k_d, k_t, mu and the shading coefficients")
+
+
+def run_grad(args, rank, world, local_rank, dist):
+    """The calibration workload: one loss evaluation and its gradient per step, through
+    the torch.autograd bindings of the adjoint kernels."""
+    import torch
+
+    import paper_2408_06506_b300 as tacsl
+    from paper_2408_06506_b300 import autograd as ta
+    from paper_2408_06506_b300.dist import max_over_ranks
+
+    sc = make_scene(args.grad_envs, args.seed + 200 + rank)
+
+    def dev(a):
+        return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+    sdfs = tacsl.SdfSet.from_grids(sc.grids)
+    taxels, obj, sid = dev(sc.taxels), dev(sc.obj_id), dev(sc.sensor_id)
+    depth_map = dev(sc.depth_map)
+    E, P, T, HW = sc.E, sc.P, sc.T, sc.H * sc.W
+    g = np.random.default_rng(args.seed + 300 + rank)
+    # seeded targets: the field of 10 % stiffer / softer parameters and the image of
+    # coefficients with 2 % noise
+    with torch.no_grad():
+        tk = [dev((v * g.uniform(0.9, 1.1, size=v.shape)).astype(np.float32)) for v in (sc.k_n, sc.k_t, sc.mu)]
+        tgt = ta.force_field(sdfs, taxels, obj, dev(sc.pad_pose), dev(sc.pad_twist), tk[0], dev(sc.k_d), tk[1],
+                             tk[2])
+        tco = dev((sc.coeffs * (1 + 0.02 * g.standard_normal(sc.coeffs.shape))).astype(np.float32))
+        tI = ta.shade_intensity(tco, depth_map, sid, sc.pitch_x, sc.pitch_y)
+    pose = dev(sc.pad_pose).requires_grad_(True)
+    twist = dev(sc.pad_twist).requires_grad_(True)
+    ks = [dev(v).requires_grad_(True) for v in (sc.k_n, sc.k_d, sc.k_t, sc.mu)]
+    coeffs = dev(sc.coeffs).requires_grad_(True)
+    leaves = [pose, twist, *ks, coeffs]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for t in leaves:
+            t.grad = None
+        _, fn, ft, _ = ta.force_field(sdfs, taxels, obj, pose, twist, *ks)
+        I = ta.shade_intensity(coeffs, depth_map, sid, sc.pitch_x, sc.pitch_y)
+        loss = ((fn - tgt[1]) ** 2).mean() + ((ft - tgt[2]) ** 2).mean() + 1e-4 * ((I - tI) ** 2).mean()
+        loss.backward()
+
+    def timed(fn, n, warm=3):
+        for _ in range(warm):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    assert tacsl.check_errors() == 0
+    K = args.grad_steps
+    if dist is not None:
+        dist.barrier()
+    ms = max_over_ranks(timed(step, K, warm=0), dist, device="cuda")
+    # the kernels alone: forward force field and intensity, and their adjoints for fixed
+    # upstream gradients
+    params = tacsl.ContactParams(*[k.detach() for k in ks])
+    shading = tacsl.Shading(coeffs.detach(), sc.pitch_x, sc.pitch_y)
+    lib = ta._lib()
+    import ctypes as C
+    gfn = torch.randn(E, P, T, 3, device="cuda")
+    gft = torch.randn(E, P, T, 3, device="cuda")
+    gI = torch.randn(E * P, sc.H, sc.W, 3, device="cuda")
+    gp = torch.empty(E, P, 7, device="cuda")
+    gt = torch.empty(E, P, 6, device="cuda")
+    gk = torch.empty(E, 4, device="cuda")
+    gc = torch.empty_like(coeffs)
+    inten = torch.empty(E * P, sc.H, sc.W, 3, device="cuda")
+    pz, tw = pose.detach(), twist.detach()
+    k_ms = {
+        "penalty_kernel (forward)": timed(lambda: tacsl.penalty_forces(sdfs, params, taxels, obj, pz, tw), 20),
+        "shade_intensity_kernel": timed(lambda: lib.tacsl_shade_intensity(
+            C.byref(shading.c), E * P, tacsl._ptr(sid), tacsl._ptr(depth_map), tacsl._ptr(inten), None), 20),
+        "force_adjoint_kernel": timed(lambda: lib.tacsl_penalty_forces_adjoint(
+            C.byref(sdfs.c), C.byref(params.c), E, P, T, tacsl._ptr(taxels), tacsl._ptr(obj), tacsl._ptr(pz),
+            tacsl._ptr(tw), None, tacsl._ptr(gfn), tacsl._ptr(gft), None, tacsl._ptr(gp), tacsl._ptr(gt),
+            tacsl._ptr(gk), None), 20),
+        "shade_coeff_grad_kernel": timed(lambda: lib.tacsl_shade_adjoint(
+            C.byref(shading.c), E * P, tacsl._ptr(sid), tacsl._ptr(depth_map), tacsl._ptr(gI), tacsl._ptr(gc), None,
+            None), 5),
+    }
+    assert tacsl.check_errors() == 0
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = float(json.load(open(peaks_path))["hbm_gbs"]) if os.path.exists(peaks_path) else 6400.0
+    npx = E * P * HW
+    coef_bytes = int(sc.coeffs.nbytes)
+    # compulsory bytes: intensity forward reads depth 4 B/px and the coefficients once,
+    # writes 12 B/px; the coefficient adjoint reads depth 4 + upstream 12 B/px and writes
+    # the coefficient gradient once
+    inten_bytes = 16 * npx + coef_bytes
+    cgrad_bytes = 16 * npx + 2 * coef_bytes
+    return {
+        "workload": GRAD_WORKLOAD, "envs_per_gpu": E, "steps": K,
+        "ms_per_step": ms, "unit": "taxel-points/s", "value": world * E * P * T / (ms * 1e-3),
+        "images_per_s": world * E * P / (ms * 1e-3),
+        "path": "force_field + shade_intensity (torch.autograd.Function over the C ABI), MSE in torch, backward",
+        "kernel_ms": k_ms,
+        "roofline": {
+            "shade_intensity_kernel": {"algorithmic_bytes": inten_bytes,
+                                       "frac": inten_bytes / (k_ms["shade_intensity_kernel"] * 1e-3) / 1e9 / peak},
+            "shade_coeff_grad_kernel": {"algorithmic_bytes": cgrad_bytes,
+                                        "frac": cgrad_bytes / (k_ms["shade_coeff_grad_kernel"] * 1e-3) / 1e9 / peak},
+            "peak_gbs": peak},
+        "gpu_launches_per_step": 4,
+    }
+
+
 def _smi_id(ordinal):
     """nvidia-smi id of a CUDA ordinal (its UUID; ordinals differ under CUDA_VISIBLE_DEVICES)."""
     import torch
@@ -696,6 +823,18 @@ def main():
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
         dist = tdist
     try:
+        if args.only_grad:
+            import torch
+            torch.cuda.set_device(local_rank)
+            from paper_2408_06506_b300 import build
+            if rank == 0:
+                build.build()
+            if dist is not None:
+                dist.barrier()
+            out = run_grad(args, rank, world, local_rank, dist)
+            if rank == 0:
+                print(json.dumps({"impl": "ours", "section": "grad", "n_gpus": world, **out}), flush=True)
+            return
         if args.only_batch:
             import torch
             torch.cuda.set_device(local_rank)

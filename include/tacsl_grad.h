@@ -1,0 +1,60 @@
+/*
+ * tacsl_grad.h -- gradients of the tactile step (libtacsl.so; conventions, frames and
+ * status codes as in tacsl.h).
+ *
+ * Calibrating a tactile sensor model means fitting the contact parameters (the paper
+ * measures the contact stiffness of its pads, Sec. VI-A) and the image model (the
+ * calibrated depth-to-RGB mapping of Sec. III-B) to observations.  These entry points
+ * give the gradients such a fit needs, computed by hand-written adjoint kernels:
+ *   - of the force field and wrenches (Sec. III-C) w.r.t. each pad's pose and twist and
+ *     the contact parameters k_n, k_d, k_t, mu;
+ *   - of the image w.r.t. the per-pixel shading coefficients and the depth maps.
+ * The differentiable image is the clamped intensity clamp(sum_k A_k m_k, 0, 255), the
+ * continuous quantity the uint8 image rounds.  Gradients are those of the smooth piece
+ * a point lies in: contact on/off, the unilateral clamp, stick/slip, the interpolation
+ * cell and the intensity clamp carry no derivative.
+ */
+#ifndef TACSL_GRAD_H
+#define TACSL_GRAD_H
+
+#include "tacsl.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Adjoint of tacsl_penalty_forces (same set, params, E, P, T, taxels, obj_id, pad_pose,
+ * pad_twist).  Upstream gradients (device, may be NULL = zero): g_depth [E*P][T],
+ * g_f_n and g_f_t [E*P][T][3] (pad frame), g_wrench [E*P][6].  Outputs (device, may be
+ * NULL = not wanted): grad_pose [E*P][7] (t and the raw quaternion q; the rotation uses
+ * q/|q|, so the q part is tangent to the sphere through q, divided by |q|),
+ * grad_twist [E*P][6], grad_params [params->count][4] = (k_n, k_d, k_t, mu).  With
+ * count E each env's entry is its sum in a fixed order; with count 1 the call first
+ * zeroes grad_params and every env adds into it with atomics (the summation order, and so
+ * the last bits, vary between runs).  A bad obj_id gives NaN gradients for its env and sets
+ * TACSL_DEVERR_BAD_OBJ_ID. */
+int tacsl_penalty_forces_adjoint(const tacsl_sdf_set* set, const tacsl_contact_params* params, int32_t E,
+                                 int32_t P, int32_t T, const float* taxels, const int32_t* obj_id,
+                                 const float* pad_pose, const float* pad_twist, const float* g_depth,
+                                 const float* g_f_n, const float* g_f_t, const float* g_wrench,
+                                 float* grad_pose, float* grad_twist, float* grad_params,
+                                 tacsl_stream_t stream);
+
+/* Clamped intensities [B][H][W][3] (float, HWC) of the images tacsl_shade_image would
+ * quantise: the forward of the differentiable image.  An image with a bad sensor_id is
+ * left untouched and sets TACSL_DEVERR_BAD_SENSOR_ID. */
+int tacsl_shade_intensity(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id,
+                          const float* depth_map, float* intensity, tacsl_stream_t stream);
+
+/* Adjoint of tacsl_shade_intensity for upstream g_intensity [B][H][W][3] (device).
+ * grad_coeffs [S][6][3][H][W] (may be NULL): for each sensor, the sum over its images,
+ * in image order.  grad_depth [B][H][W] (may be NULL): zero for an image with a bad
+ * sensor_id. */
+int tacsl_shade_adjoint(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id,
+                        const float* depth_map, const float* g_intensity, float* grad_coeffs,
+                        float* grad_depth, tacsl_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TACSL_GRAD_H */

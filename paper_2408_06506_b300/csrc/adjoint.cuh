@@ -1,0 +1,646 @@
+// Hand-written adjoints of the tactile step, for calibrating the sensor and contact
+// models from observed force fields and images (the use the paper makes of measured
+// contact stiffness, Sec. VI-A, and of a calibrated image model, Sec. III-B).
+//
+// Force field (Sec. III-C).  For an upstream gradient of the depth, normal and shear
+// force fields and of the per-pad wrench, the kernel returns the gradient w.r.t. each
+// pad's pose (t, q), twist (v, w) and the contact parameters (k_n, k_d, k_t, mu).  It
+// recomputes the forward values in the same float32 operations as the force kernel
+// (so contact, clamp and stick/slip decisions match it) and runs the chain rule back:
+//   f_pad = R^T f            -> dR, df
+//   f_t = -(v_t/|v_t|) min(k_t |v_t|, mu |f_n|),  f_n = max((-k_n + k_d d') phi, 0) n,
+//   v_t = x' - d' n,  d' = n . x',  n = g/|g|      -> dx', dphi, dg, parameters
+//   phi(x), g(x): trilinear interpolant and its h/2 central difference; their
+//     derivatives come from the same 27-node window folded with the derivative weights
+//     of each axis (a sample's weights are (1-f, f) on its cell, so d/du is (-1, 1))
+//   x' = v + w x x,  x = R p + t                   -> dt, dR, dv, dw
+//   R = R(q/|q|)                                     -> dq (tangent to the unit sphere, / |q|)
+// A taxel contributes only where it penetrates (phi < 0); elsewhere its outputs are
+// constant zero.  One warp per env walks its P pads; lanes take taxels; pose / twist
+// gradients are reduced per pad with shuffles, parameter gradients per env.
+//
+// Image (Sec. III-B).  The differentiable image is the clamped intensity
+// clamp(sum_k A_k m_k(n), 0, 255) (the quantity the uint8 image rounds).  Its forward
+// kernel writes float intensities; the adjoint returns the gradient w.r.t. the per-pixel
+// coefficients (summed over the images of each sensor) and w.r.t. the depth maps (the
+// transpose of the central / one-sided difference stencil of the normals).
+#pragma once
+
+#include "common.cuh"
+#include "taxel.cuh"
+
+namespace tacsl {
+
+// Derivative weights of one axis: for the centre sample (dc) and for the difference
+// d = w(u + 1/2) - w(u - 1/2) (dd); a sample on the window's first cell has weights
+// (1-f, f, 0), on the second (0, 1-f, f), so d/du of them is (-1, 1, 0) or (0, -1, 1).
+__device__ __forceinline__ void axis_dweights(float u, int n, int b, float dc[3], float dd[3]) {
+    auto dsample = [&](float s, float* w) {
+        const int cell = min(static_cast<int>(floorf(s)), n - 2);
+        const bool r0 = (cell == b);
+        w[0] = r0 ? -1.f : 0.f;
+        w[1] = r0 ? 1.f : -1.f;
+        w[2] = r0 ? 0.f : 1.f;
+    };
+    float wm[3], wp[3];
+    dsample(u - 0.5f, wm);
+    dsample(u, dc);
+    dsample(u + 0.5f, wp);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dd[k] = wp[k] - wm[k];
+}
+
+__device__ __forceinline__ float dot3w(const float* w, float a, float b, float c) {
+    return fmaf(w[2], c, fmaf(w[1], b, w[0] * a));
+}
+
+// SDF sample of a penetrating taxel with derivatives, in continuous-index units:
+// phi, g (per metre, as the force kernel), dphi[b] = d phi / d u_b and
+// J[a][b] = d g_a / d u_b.
+struct SdfJet {
+    float phi, g[3], dphi[3], J[3][3];
+};
+
+__device__ __forceinline__ void sdf_jet(const DevSdf& S, const GridPos& gp, uint64_t pol, SdfJet& o) {
+    Stencil q;
+    q.inside = true;
+    int bx, by, bz;
+    axis_weights(gp.ux, S.n0, bx, q.cx, q.dx);
+    axis_weights(gp.uy, S.n1, by, q.cy, q.dy);
+    axis_weights(gp.uz, S.n2, bz, q.cz, q.dz);
+    const int n0 = S.n0, n01 = S.n0 * S.n1;
+    q.base = S.data + (static_cast<int64_t>(bz) * n01 + static_cast<int64_t>(by) * n0 + bx);
+    float v[3][3][3];
+    stencil_load(q, n0, n01, pol, v);
+    stencil_fold(q, v, S.inv_h, o.phi, o.g);     // bitwise the force kernel's phi and g
+    float ecx[3], edx[3], ecy[3], edy[3], ecz[3], edz[3];
+    axis_dweights(gp.ux, S.n0, bx, ecx, edx);
+    axis_dweights(gp.uy, S.n1, by, ecy, edy);
+    axis_dweights(gp.uz, S.n2, bz, ecz, edz);
+    // x stage: rows of the window folded along x with c, c', d, d'
+    float rc[3][3], rdc[3][3], rd[3][3], rdd[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            rc[k][j] = dot3w(q.cx, v[k][j][0], v[k][j][1], v[k][j][2]);
+            rdc[k][j] = dot3w(ecx, v[k][j][0], v[k][j][1], v[k][j][2]);
+            rd[k][j] = dot3w(q.dx, v[k][j][0], v[k][j][1], v[k][j][2]);
+            rdd[k][j] = dot3w(edx, v[k][j][0], v[k][j][1], v[k][j][2]);
+        }
+    // y stage: the (x, y) weight pairs the sixteen (x, y, z) triples need
+    float cc[3], cdc[3], cd[3], cdd[3], dcc[3], dcd[3], dc_[3], ddc[3], ddd[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        cc[k] = dot3w(q.cy, rc[k][0], rc[k][1], rc[k][2]);      // (c, c)
+        cdc[k] = dot3w(ecy, rc[k][0], rc[k][1], rc[k][2]);      // (c, c')
+        cd[k] = dot3w(q.dy, rc[k][0], rc[k][1], rc[k][2]);      // (c, d)
+        cdd[k] = dot3w(edy, rc[k][0], rc[k][1], rc[k][2]);      // (c, d')
+        dcc[k] = dot3w(q.cy, rdc[k][0], rdc[k][1], rdc[k][2]);  // (c', c)
+        dcd[k] = dot3w(q.dy, rdc[k][0], rdc[k][1], rdc[k][2]);  // (c', d)
+        dc_[k] = dot3w(q.cy, rd[k][0], rd[k][1], rd[k][2]);     // (d, c)
+        ddc[k] = dot3w(ecy, rd[k][0], rd[k][1], rd[k][2]);      // (d, c')
+        ddd[k] = dot3w(q.cy, rdd[k][0], rdd[k][1], rdd[k][2]);  // (d', c)
+    }
+    // z stage
+    o.dphi[0] = dot3w(q.cz, dcc[0], dcc[1], dcc[2]);
+    o.dphi[1] = dot3w(q.cz, cdc[0], cdc[1], cdc[2]);
+    o.dphi[2] = dot3w(ecz, cc[0], cc[1], cc[2]);
+    const float ih = S.inv_h;
+    o.J[0][0] = dot3w(q.cz, ddd[0], ddd[1], ddd[2]) * ih;
+    o.J[0][1] = dot3w(q.cz, ddc[0], ddc[1], ddc[2]) * ih;
+    o.J[0][2] = dot3w(ecz, dc_[0], dc_[1], dc_[2]) * ih;
+    o.J[1][0] = dot3w(q.cz, dcd[0], dcd[1], dcd[2]) * ih;
+    o.J[1][1] = dot3w(q.cz, cdd[0], cdd[1], cdd[2]) * ih;
+    o.J[1][2] = dot3w(ecz, cd[0], cd[1], cd[2]) * ih;
+    o.J[2][0] = dot3w(q.dz, dcc[0], dcc[1], dcc[2]) * ih;
+    o.J[2][1] = dot3w(q.dz, cdc[0], cdc[1], cdc[2]) * ih;
+    o.J[2][2] = dot3w(edz, cc[0], cc[1], cc[2]) * ih;
+}
+
+struct ForceAdjointArgs {
+    SdfTable tab;
+    Params4 prm;
+    int64_t E;
+    int P, T;
+    const float* taxels;
+    const int32_t* obj_id;
+    const float* pose;
+    const float* twist;
+    const float* g_depth;   // [B][T] or NULL
+    const float* g_fn;      // [B][T][3] or NULL
+    const float* g_ft;      // [B][T][3] or NULL
+    const float* g_wrench;  // [B][6] or NULL
+    float* grad_pose;       // [B][7] or NULL
+    float* grad_twist;      // [B][6] or NULL
+    float* grad_params;     // [count][4] or NULL
+};
+
+__device__ __forceinline__ float ld_or0(const float* p, int64_t i) { return p != nullptr ? __ldg(p + i) : 0.f; }
+
+// Gradient of R(q/|q|) (row-major r) w.r.t. q, given dL/dR in gR.
+__device__ __forceinline__ void quat_backward(const float* q4, const float* gR, float gq[4]) {
+    const float s = rsqrtf(q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3]);
+    const float w = q4[0] * s, x = q4[1] * s, y = q4[2] * s, z = q4[3] * s;
+    // dL/dq_hat from the partial derivatives of each entry of R
+    float gw = 2.f * (-z * gR[1] + y * gR[2] + z * gR[3] - x * gR[5] - y * gR[6] + x * gR[7]);
+    float gx = 2.f * (y * gR[1] + z * gR[2] + y * gR[3] - 2.f * x * gR[4] - w * gR[5] + z * gR[6] + w * gR[7] -
+                      2.f * x * gR[8]);
+    float gy = 2.f * (-2.f * y * gR[0] + x * gR[1] + w * gR[2] + x * gR[3] + z * gR[5] - w * gR[6] + z * gR[7] -
+                      2.f * y * gR[8]);
+    float gz = 2.f * (-2.f * z * gR[0] - w * gR[1] + x * gR[2] + w * gR[3] - 2.f * z * gR[4] + y * gR[5] +
+                      x * gR[6] + y * gR[7]);
+    // through the normalisation: (I - q_hat q_hat^T) / |q|
+    const float proj = w * gw + x * gx + y * gy + z * gz;
+    gq[0] = (gw - w * proj) * s;
+    gq[1] = (gx - x * proj) * s;
+    gq[2] = (gy - y * proj) * s;
+    gq[3] = (gz - z * proj) * s;
+}
+
+// acc layout: 0-2 t, 3-11 R (row-major), 12-14 v, 15-17 w, 18-21 k_n, k_d, k_t, mu
+constexpr int kAdjAcc = 22;
+
+__device__ __forceinline__ void taxel_adjoint(const DevSdf& S, const Pose& Pz, float kn, float kd, float kt, float mu,
+                                              const float p[3], const float gfp[3], const float gtp[3], float gdep,
+                                              uint64_t pol, float (&acc)[kAdjAcc]) {
+    const float* r = Pz.r;
+    const float x0 = fmaf(r[0], p[0], fmaf(r[1], p[1], fmaf(r[2], p[2], Pz.t[0])));
+    const float x1 = fmaf(r[3], p[0], fmaf(r[4], p[1], fmaf(r[5], p[2], Pz.t[1])));
+    const float x2 = fmaf(r[6], p[0], fmaf(r[7], p[1], fmaf(r[8], p[2], Pz.t[2])));
+    const float xd[3] = {Pz.v[0] + (Pz.w[1] * x2 - Pz.w[2] * x1), Pz.v[1] + (Pz.w[2] * x0 - Pz.w[0] * x2),
+                         Pz.v[2] + (Pz.w[0] * x1 - Pz.w[1] * x0)};
+    const GridPos gp = grid_pos(S, x0, x1, x2);
+    if (!gp.inside) return;
+    if (!(phi_cell8(S, gp, pol) < 0.f)) return;         // no contact: constant zero outputs
+    SdfJet jt;
+    sdf_jet(S, gp, pol, jt);
+    const float phi = jt.phi;
+    float g_phi = -gdep;                                 // depth = -phi
+    float g_g[3] = {0.f, 0.f, 0.f}, g_xd[3] = {0.f, 0.f, 0.f};
+    const float gn2 = fmaf(jt.g[0], jt.g[0], fmaf(jt.g[1], jt.g[1], jt.g[2] * jt.g[2]));
+    if (gn2 >= 1e-24f) {
+        // forward, as contact_force
+        const float inv = rsqrtf(gn2);
+        const float n[3] = {jt.g[0] * inv, jt.g[1] * inv, jt.g[2] * inv};
+        const float ddot = fmaf(n[0], xd[0], fmaf(n[1], xd[1], n[2] * xd[2]));
+        const float craw = fmaf(kd, ddot, -kn);
+        const float mraw = craw * phi;
+        const float mag = fmaxf(mraw, 0.f);
+        const float tv[3] = {fmaf(-ddot, n[0], xd[0]), fmaf(-ddot, n[1], xd[1]), fmaf(-ddot, n[2], xd[2])};
+        const float vt2 = fmaf(tv[0], tv[0], fmaf(tv[1], tv[1], tv[2] * tv[2]));
+        float fn[3], ft[3] = {0.f, 0.f, 0.f};
+        fn[0] = mag * n[0]; fn[1] = mag * n[1]; fn[2] = mag * n[2];
+        float s = 0.f, cap = 0.f, lim = 0.f, ftm = 0.f, sc = 0.f;
+        if (vt2 > 0.f) {
+            s = sqrtf(vt2);
+            cap = kt * s;
+            lim = mu * mag;
+            ftm = fminf(cap, lim);
+            sc = -ftm / s;
+            ft[0] = sc * tv[0]; ft[1] = sc * tv[1]; ft[2] = sc * tv[2];
+        }
+        // upstream in the object frame (f_pad = R^T f  =>  df = R df_pad) and dR from it
+        float gfn[3], gft[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gfn[a] = fmaf(r[3 * a], gfp[0], fmaf(r[3 * a + 1], gfp[1], r[3 * a + 2] * gfp[2]));
+            gft[a] = fmaf(r[3 * a], gtp[0], fmaf(r[3 * a + 1], gtp[1], r[3 * a + 2] * gtp[2]));
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[3 + 3 * j + a] += fmaf(fn[j], gfp[a], ft[j] * gtp[a]);
+        float g_n[3] = {0.f, 0.f, 0.f}, g_tv[3] = {0.f, 0.f, 0.f}, g_mag = 0.f, g_ddot = 0.f;
+        if (vt2 > 0.f) {
+            // f_t = sc tv, sc = -ftm / s, ftm = min(k_t s, mu mag)
+            const float g_sc = fmaf(tv[0], gft[0], fmaf(tv[1], gft[1], tv[2] * gft[2]));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) g_tv[a] = sc * gft[a];
+            const float g_ftm = -g_sc / s;
+            float g_s = ftm * g_sc / (s * s);
+            if (cap <= lim) {                  // stick (fminf takes cap)
+                acc[20] += s * g_ftm;
+                g_s += kt * g_ftm;
+            } else {                           // slip
+                acc[21] += mag * g_ftm;
+                g_mag += mu * g_ftm;
+            }
+            const float k = g_s / s;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) g_tv[a] = fmaf(k, tv[a], g_tv[a]);
+            // tv = x' - ddot n
+#pragma unroll
+            for (int a = 0; a < 3; ++a) g_xd[a] += g_tv[a];
+            g_ddot -= fmaf(n[0], g_tv[0], fmaf(n[1], g_tv[1], n[2] * g_tv[2]));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) g_n[a] -= ddot * g_tv[a];
+        }
+        // f_n = mag n
+        g_mag += fmaf(n[0], gfn[0], fmaf(n[1], gfn[1], n[2] * gfn[2]));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) g_n[a] = fmaf(mag, gfn[a], g_n[a]);
+        // mag = max(craw phi, 0), craw = k_d ddot - k_n
+        if (mraw > 0.f) {
+            const float g_c = phi * g_mag;
+            g_phi = fmaf(craw, g_mag, g_phi);
+            acc[18] -= g_c;
+            acc[19] += ddot * g_c;
+            g_ddot = fmaf(kd, g_c, g_ddot);
+        }
+        // ddot = n . x'
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            g_n[a] = fmaf(xd[a], g_ddot, g_n[a]);
+            g_xd[a] = fmaf(n[a], g_ddot, g_xd[a]);
+        }
+        // n = g / |g|
+        const float pn = fmaf(n[0], g_n[0], fmaf(n[1], g_n[1], n[2] * g_n[2]));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) g_g[a] = (g_n[a] - n[a] * pn) * inv;
+    }
+    // phi(x), g(x): d/dx = (1/h) d/du
+    float g_x[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+        g_x[b] = fmaf(jt.dphi[b], g_phi, fmaf(jt.J[0][b], g_g[0], fmaf(jt.J[1][b], g_g[1], jt.J[2][b] * g_g[2]))) *
+                 S.inv_h;
+    // x' = v + w x x
+    const float xs[3] = {x0, x1, x2};
+    acc[12] += g_xd[0]; acc[13] += g_xd[1]; acc[14] += g_xd[2];
+    acc[15] += xs[1] * g_xd[2] - xs[2] * g_xd[1];
+    acc[16] += xs[2] * g_xd[0] - xs[0] * g_xd[2];
+    acc[17] += xs[0] * g_xd[1] - xs[1] * g_xd[0];
+    g_x[0] += g_xd[1] * Pz.w[2] - g_xd[2] * Pz.w[1];
+    g_x[1] += g_xd[2] * Pz.w[0] - g_xd[0] * Pz.w[2];
+    g_x[2] += g_xd[0] * Pz.w[1] - g_xd[1] * Pz.w[0];
+    // x = R p + t
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc[a] += g_x[a];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) acc[3 + 3 * a + j] = fmaf(g_x[a], p[j], acc[3 + 3 * a + j]);
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// One warp per env; 8 envs per 256-thread CTA; grid-stride over envs.
+__global__ void __launch_bounds__(256) force_adjoint_kernel(const ForceAdjointArgs A) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * 8;
+    const uint64_t pol = policy_evict_last();
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * 8 + (threadIdx.x >> 5); e < A.E; e += nwarps) {
+        const int id = __ldg(A.obj_id + e);
+        const int pi = A.prm.count == 1 ? 0 : static_cast<int>(e);
+        if (id < 0 || id >= A.tab.count) {
+            const float qnan = __int_as_float(0x7fc00000);
+            for (int p = 0; p < A.P; ++p) {
+                const int64_t b = e * A.P + p;
+                if (A.grad_pose != nullptr && lane < 7) A.grad_pose[b * 7 + lane] = qnan;
+                if (A.grad_twist != nullptr && lane < 6) A.grad_twist[b * 6 + lane] = qnan;
+            }
+            if (A.grad_params != nullptr && lane < 4) {
+                if (A.prm.count == 1) atomicAdd(A.grad_params + lane, qnan);
+                else A.grad_params[static_cast<int64_t>(pi) * 4 + lane] = qnan;
+            }
+            if (lane == 0) raise_dev_error(TACSL_DEVERR_BAD_OBJ_ID);
+            continue;
+        }
+        const DevSdf& S = A.tab.s[id];
+        const float kn = __ldg(A.prm.k_n + pi), kd = __ldg(A.prm.k_d + pi), kt = __ldg(A.prm.k_t + pi),
+                    mu = __ldg(A.prm.mu + pi);
+        float kacc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int p = 0; p < A.P; ++p) {
+            const int64_t b = e * A.P + p;
+            Pose Pz;
+            load_pose(A.pose + b * 7, A.twist + b * 6, Pz);
+            float gW[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) gW[k] = ld_or0(A.g_wrench, b * 6 + k);
+            float acc[kAdjAcc];
+#pragma unroll
+            for (int k = 0; k < kAdjAcc; ++k) acc[k] = 0.f;
+            const int64_t o = b * A.T;
+            for (int t = lane; t < A.T; t += 32) {
+                const float pt[3] = {__ldg(A.taxels + 3 * t), __ldg(A.taxels + 3 * t + 1), __ldg(A.taxels + 3 * t + 2)};
+                // wrench = (sum f, sum p x f): dL/df_i += g_F + g_tau x p_i, for f_n and f_t alike
+                const float gwx = gW[0] + (gW[4] * pt[2] - gW[5] * pt[1]);
+                const float gwy = gW[1] + (gW[5] * pt[0] - gW[3] * pt[2]);
+                const float gwz = gW[2] + (gW[3] * pt[1] - gW[4] * pt[0]);
+                const float gfp[3] = {ld_or0(A.g_fn, (o + t) * 3) + gwx, ld_or0(A.g_fn, (o + t) * 3 + 1) + gwy,
+                                      ld_or0(A.g_fn, (o + t) * 3 + 2) + gwz};
+                const float gtp[3] = {ld_or0(A.g_ft, (o + t) * 3) + gwx, ld_or0(A.g_ft, (o + t) * 3 + 1) + gwy,
+                                      ld_or0(A.g_ft, (o + t) * 3 + 2) + gwz};
+                taxel_adjoint(S, Pz, kn, kd, kt, mu, pt, gfp, gtp, ld_or0(A.g_depth, o + t), pol, acc);
+            }
+#pragma unroll
+            for (int k = 0; k < kAdjAcc; ++k) acc[k] = warp_sum(acc[k]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) kacc[k] += acc[18 + k];
+            if (lane == 0) {
+                if (A.grad_pose != nullptr) {
+                    const float q4[4] = {__ldg(A.pose + b * 7 + 3), __ldg(A.pose + b * 7 + 4), __ldg(A.pose + b * 7 + 5),
+                                         __ldg(A.pose + b * 7 + 6)};
+                    float gq[4];
+                    quat_backward(q4, acc + 3, gq);
+                    float* gp = A.grad_pose + b * 7;
+                    gp[0] = acc[0]; gp[1] = acc[1]; gp[2] = acc[2];
+                    gp[3] = gq[0]; gp[4] = gq[1]; gp[5] = gq[2]; gp[6] = gq[3];
+                }
+                if (A.grad_twist != nullptr) {
+                    float* gt = A.grad_twist + b * 6;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) gt[k] = acc[12 + k];
+                }
+            }
+        }
+        if (A.grad_params != nullptr && lane == 0) {
+            if (A.prm.count == 1) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomicAdd(A.grad_params + k, kacc[k]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) A.grad_params[static_cast<int64_t>(pi) * 4 + k] = kacc[k];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Image: clamped intensity and its adjoint
+// ---------------------------------------------------------------------------
+
+struct ShadeGeom {
+    int H, W, S;
+    int64_t HW;
+    float px, py;   // pixel pitch
+};
+
+// Depth derivative of image D along x at (x, y) and its stencil: D_x = cx_lo D[.. lo] +
+// cx_hi D[.. hi] (central inside, one-sided on the border, zero on a 1-wide axis).
+__device__ __forceinline__ void axis_stencil(int i, int len, float pitch, int& lo, int& hi, float& c) {
+    if (len < 2) { lo = hi = i; c = 0.f; return; }
+    if (i == 0) { lo = 0; hi = 1; c = 1.f / pitch; return; }
+    if (i == len - 1) { lo = len - 2; hi = len - 1; c = 1.f / pitch; return; }
+    lo = i - 1; hi = i + 1; c = 1.f / (2.f * pitch);
+}
+
+struct PixelState {
+    float dx, dy, r, nx, ny;
+};
+
+__device__ __forceinline__ PixelState pixel_state(const float* D, const ShadeGeom& G, int x, int y) {
+    int lo, hi;
+    float cx, cy;
+    axis_stencil(x, G.W, G.px, lo, hi, cx);
+    PixelState s;
+    s.dx = (__ldg(D + static_cast<int64_t>(y) * G.W + hi) - __ldg(D + static_cast<int64_t>(y) * G.W + lo)) * cx;
+    axis_stencil(y, G.H, G.py, lo, hi, cy);
+    s.dy = (__ldg(D + static_cast<int64_t>(hi) * G.W + x) - __ldg(D + static_cast<int64_t>(lo) * G.W + x)) * cy;
+    s.r = rsqrtf(fmaf(s.dx, s.dx, fmaf(s.dy, s.dy, 1.f)));
+    s.nx = s.dx * s.r;
+    s.ny = s.dy * s.r;
+    return s;
+}
+
+// Images of one sensor within [c0, c1), found 32 ids at a time and handed over in
+// order, two at a time: f(b0, b1) with b1 = -1 when only one is left.  The pairs let a
+// warp issue the loads of two images before it computes either.
+template <class F>
+__device__ __forceinline__ void for_image_pairs(const int32_t* __restrict__ sensor_id, int64_t c0, int64_t c1, int s,
+                                                F&& f) {
+    const int lane = threadIdx.x & 31;
+    int64_t pending = -1;
+    for (int64_t base = c0; base < c1; base += 32) {
+        const int sid = base + lane < c1 ? __ldg(sensor_id + base + lane) : -1;
+        unsigned mask = __ballot_sync(0xffffffffu, sid == s);
+        while (mask != 0u) {
+            const int j = __ffs(mask) - 1;
+            mask &= mask - 1u;
+            if (pending < 0) {
+                pending = base + j;
+            } else {
+                f(pending, base + j);
+                pending = -1;
+            }
+        }
+    }
+    if (pending >= 0) f(pending, int64_t(-1));
+}
+
+// Work split of the per-pixel image kernels: a CTA of 8 warps owns 32 consecutive pixels
+// of one sensor's image plane (one per lane, so the per-pixel coefficients stay in
+// registers) and a range of images; its warps take equal slices of that range.
+constexpr int kPxTile = 32;
+constexpr int kImgWarps = 8;
+
+// Clamped intensity: grid (pixel tiles, sensors, image chunks).
+__global__ void __launch_bounds__(256) shade_intensity_kernel(ShadeGeom G, int64_t B, int64_t chunk,
+                                                               const float* __restrict__ coeffs,
+                                                               const int32_t* __restrict__ sensor_id,
+                                                               const float* __restrict__ depth,
+                                                               float* __restrict__ inten) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = blockIdx.y;
+    const int64_t px = static_cast<int64_t>(blockIdx.x) * kPxTile + lane;
+    const bool valid = px < G.HW;
+    const int y = valid ? static_cast<int>(px / G.W) : 0, x = valid ? static_cast<int>(px - static_cast<int64_t>(y) * G.W) : 0;
+    float a[6][3];
+#pragma unroll
+    for (int kk = 0; kk < 6; ++kk)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            a[kk][c] = valid ? __ldg(coeffs + (static_cast<int64_t>(s) * 18 + kk * 3 + c) * G.HW + px) : 0.f;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.z) * chunk, c1 = min(c0 + chunk, B);
+    const int64_t per = (c1 - c0 + kImgWarps - 1) / kImgWarps;
+    const int64_t w0 = min(c0 + warp * per, c1), w1 = min(w0 + per, c1);
+    for_image_pairs(sensor_id, w0, w1, s, [&](int64_t b0, int64_t b1) {
+        if (!valid) return;
+        const PixelState st0 = pixel_state(depth + b0 * G.HW, G, x, y);
+        const PixelState st1 = pixel_state(depth + (b1 >= 0 ? b1 : b0) * G.HW, G, x, y);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            if (i == 1 && b1 < 0) break;
+            const PixelState& st = i ? st1 : st0;
+            const float m[6] = {1.f, st.nx, st.ny, st.nx * st.nx, st.ny * st.ny, st.nx * st.ny};
+            float* out = inten + ((i ? b1 : b0) * G.HW + px) * 3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float I = 0.f;
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk) I = fmaf(a[kk][c], m[kk], I);
+                out[c] = fminf(fmaxf(I, 0.f), 255.f);
+            }
+        }
+    });
+}
+
+// Bad sensor ids of the intensity forward: flagged once per image.
+__global__ void __launch_bounds__(256) flag_bad_sensors_kernel(int64_t B, int S, const int32_t* __restrict__ sensor_id) {
+    for (int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; b < B;
+         b += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int s = __ldg(sensor_id + b);
+        if (s < 0 || s >= S) raise_dev_error(TACSL_DEVERR_BAD_SENSOR_ID);
+    }
+}
+
+// dL/dm_k at one pixel for upstream g[3], and (dL/dD_x, dL/dD_y) through the normal.
+__device__ __forceinline__ void pixel_backward(const float* A, int64_t HW, const PixelState& st, const float g[3],
+                                               float gm[6], float& gDx, float& gDy) {
+    const float m[6] = {1.f, st.nx, st.ny, st.nx * st.nx, st.ny * st.ny, st.nx * st.ny};
+#pragma unroll
+    for (int kk = 0; kk < 6; ++kk) gm[kk] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float a[6], I = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 6; ++kk) {
+            a[kk] = __ldg(A + (kk * 3 + c) * HW);
+            I = fmaf(a[kk], m[kk], I);
+        }
+        if (I > 0.f && I < 255.f) {            // the clamp passes the gradient only inside
+#pragma unroll
+            for (int kk = 0; kk < 6; ++kk) gm[kk] = fmaf(g[c], a[kk], gm[kk]);
+        }
+    }
+    const float gnx = fmaf(2.f * st.nx, gm[3], fmaf(st.ny, gm[5], gm[1]));
+    const float gny = fmaf(2.f * st.ny, gm[4], fmaf(st.nx, gm[5], gm[2]));
+    // n_x = D_x r, n_y = D_y r, r = (1 + D_x^2 + D_y^2)^(-1/2)
+    const float r3 = st.r * st.r * st.r;
+    gDx = gnx * (st.r - st.dx * st.dx * r3) - gny * st.dx * st.dy * r3;
+    gDy = gny * (st.r - st.dy * st.dy * r3) - gnx * st.dx * st.dy * r3;
+}
+
+// dL/dA[s][k][c][px] = sum over images b of sensor s of g[b][px][c] m_k(b, px) (where the
+// clamp passes).  Grid (pixel tiles, sensors); each warp sums its slice of the images in
+// order and the eight partial sums are added in warp order (deterministic).
+__global__ void __launch_bounds__(256) shade_coeff_grad_kernel(ShadeGeom G, int64_t B, const float* __restrict__ coeffs,
+                                                                const int32_t* __restrict__ sensor_id,
+                                                                const float* __restrict__ depth,
+                                                                const float* __restrict__ g_inten,
+                                                                float* __restrict__ grad_coeffs) {
+    __shared__ float part[kImgWarps][18][kPxTile];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = blockIdx.y;
+    const int64_t px = static_cast<int64_t>(blockIdx.x) * kPxTile + lane;
+    const bool valid = px < G.HW;
+    const int y = valid ? static_cast<int>(px / G.W) : 0, x = valid ? static_cast<int>(px - static_cast<int64_t>(y) * G.W) : 0;
+    float a[6][3], acc[6][3];
+#pragma unroll
+    for (int kk = 0; kk < 6; ++kk)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a[kk][c] = valid ? __ldg(coeffs + (static_cast<int64_t>(s) * 18 + kk * 3 + c) * G.HW + px) : 0.f;
+            acc[kk][c] = 0.f;
+        }
+    const int64_t per = (B + kImgWarps - 1) / kImgWarps;
+    const int64_t w0 = min(warp * per, B), w1 = min(w0 + per, B);
+    for_image_pairs(sensor_id, w0, w1, s, [&](int64_t b0, int64_t b1) {
+        if (!valid) return;
+        const int64_t bb1 = b1 >= 0 ? b1 : b0;
+        const PixelState st0 = pixel_state(depth + b0 * G.HW, G, x, y);
+        const PixelState st1 = pixel_state(depth + bb1 * G.HW, G, x, y);
+        float g0[3], g1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            g0[c] = __ldg(g_inten + (b0 * G.HW + px) * 3 + c);
+            g1[c] = b1 >= 0 ? __ldg(g_inten + (bb1 * G.HW + px) * 3 + c) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {          // image b0, then b1: the summation order is the image order
+            if (i == 1 && b1 < 0) break;
+            const PixelState& st = i ? st1 : st0;
+            const float m[6] = {1.f, st.nx, st.ny, st.nx * st.nx, st.ny * st.ny, st.nx * st.ny};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float I = 0.f;
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk) I = fmaf(a[kk][c], m[kk], I);
+                if (I > 0.f && I < 255.f) {
+                    const float gc = i ? g1[c] : g0[c];
+#pragma unroll
+                    for (int kk = 0; kk < 6; ++kk) acc[kk][c] = fmaf(gc, m[kk], acc[kk][c]);
+                }
+            }
+        }
+    });
+#pragma unroll
+    for (int kk = 0; kk < 6; ++kk)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) part[warp][kk * 3 + c][lane] = acc[kk][c];
+    __syncthreads();
+    // 18 x 32 sums over the 8 warps, in warp order; 256 threads take them in turn
+    for (int i = threadIdx.x; i < 18 * kPxTile; i += blockDim.x) {
+        const int term = i / kPxTile, l = i - term * kPxTile;
+        const int64_t p = static_cast<int64_t>(blockIdx.x) * kPxTile + l;
+        if (p >= G.HW) continue;
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < kImgWarps; ++w) sum += part[w][term][l];
+        grad_coeffs[(static_cast<int64_t>(s) * 18 + term) * G.HW + p] = sum;
+    }
+}
+
+// dL/dD[b][p]: the transpose of the difference stencils, gathered from the pixels q whose
+// D_x (q in p's row, |q - p| <= 1) or D_y (q in p's column) reads D[p].
+__global__ void __launch_bounds__(128) shade_depth_grad_kernel(ShadeGeom G, int64_t B, const float* __restrict__ coeffs,
+                                                                const int32_t* __restrict__ sensor_id,
+                                                                const float* __restrict__ depth,
+                                                                const float* __restrict__ g_inten,
+                                                                float* __restrict__ grad_depth) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= G.W) return;
+    const int64_t px = static_cast<int64_t>(y) * G.W + x;
+    for (int64_t b = blockIdx.z; b < B; b += gridDim.z) {
+        const int64_t k = b * G.HW + px;
+        const int s = __ldg(sensor_id + b);
+        if (s < 0 || s >= G.S) {
+            grad_depth[k] = 0.f;
+            continue;
+        }
+        const float* D = depth + b * G.HW;
+        const float* Ab = coeffs + static_cast<int64_t>(s) * 18 * G.HW;
+        const float* gI = g_inten + b * G.HW * 3;
+        float acc = 0.f;
+        // row neighbours: D_x(q) for q = (x + dq, y)
+        for (int dq = -1; dq <= 1; ++dq) {
+            const int qx = x + dq;
+            if (qx < 0 || qx >= G.W) continue;
+            int lo, hi;
+            float c;
+            axis_stencil(qx, G.W, G.px, lo, hi, c);
+            const float w = (hi == x ? c : 0.f) - (lo == x ? c : 0.f);
+            if (w == 0.f) continue;
+            const int64_t q = static_cast<int64_t>(y) * G.W + qx;
+            const PixelState st = pixel_state(D, G, qx, y);
+            const float g[3] = {__ldg(gI + q * 3), __ldg(gI + q * 3 + 1), __ldg(gI + q * 3 + 2)};
+            float gm[6], gDx, gDy;
+            pixel_backward(Ab + q, G.HW, st, g, gm, gDx, gDy);
+            acc = fmaf(w, gDx, acc);
+        }
+        // column neighbours: D_y(q) for q = (x, y + dq)
+        for (int dq = -1; dq <= 1; ++dq) {
+            const int qy = y + dq;
+            if (qy < 0 || qy >= G.H) continue;
+            int lo, hi;
+            float c;
+            axis_stencil(qy, G.H, G.py, lo, hi, c);
+            const float w = (hi == y ? c : 0.f) - (lo == y ? c : 0.f);
+            if (w == 0.f) continue;
+            const int64_t q = static_cast<int64_t>(qy) * G.W + x;
+            const PixelState st = pixel_state(D, G, x, qy);
+            const float g[3] = {__ldg(gI + q * 3), __ldg(gI + q * 3 + 1), __ldg(gI + q * 3 + 2)};
+            float gm[6], gDx, gDy;
+            pixel_backward(Ab + q, G.HW, st, g, gm, gDx, gDy);
+            acc = fmaf(w, gDy, acc);
+        }
+        grad_depth[k] = acc;
+    }
+}
+
+}  // namespace tacsl

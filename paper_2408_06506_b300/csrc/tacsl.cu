@@ -15,12 +15,14 @@
 #include <numeric>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "batch.cuh"
 #include "common.cuh"
 #include "render.cuh"
 #include "shade.cuh"
 #include "taxel.cuh"
 #include "tacsl_batch.h"
+#include "tacsl_grad.h"
 
 namespace tacsl {
 namespace {
@@ -1124,3 +1126,125 @@ extern "C" int tacsl_batch_forces_static(const tacsl_batch_desc* desc, const tac
     if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "scratch upload: %s", cudaGetErrorString(e));
     return launch_batch_forces(&p, scratch, tab, prm, io, *dev, 4, true, stream);
 }
+
+// ===========================================================================
+// Gradients (include/tacsl_grad.h)
+// ===========================================================================
+namespace tacsl {
+namespace {
+
+int shade_geom(const tacsl_shading* sh, ShadeGeom& G) {
+    G.H = sh->H;
+    G.W = sh->W;
+    G.S = sh->n_sensor;
+    G.HW = (int64_t)sh->H * sh->W;
+    G.px = sh->pitch_x;
+    G.py = sh->pitch_y;
+    return TACSL_OK;
+}
+
+// (row segments of 128 pixels, rows, images); images beyond 65535 are looped over
+dim3 pixel_grid(const ShadeGeom& G, int64_t B) {
+    return dim3(static_cast<unsigned>((G.W + 127) / 128), static_cast<unsigned>(G.H),
+                static_cast<unsigned>(std::min<int64_t>(std::max<int64_t>(B, 1), 65535)));
+}
+
+int grid_for(int64_t n, int per_sm, const DevInfo& dev) {
+    const int64_t blocks = (n + 255) / 256;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)dev.sms * per_sm)));
+}
+
+}  // namespace
+}  // namespace tacsl
+
+extern "C" {
+
+int tacsl_penalty_forces_adjoint(const tacsl_sdf_set* set, const tacsl_contact_params* params, int32_t E, int32_t P,
+                                 int32_t T, const float* taxels, const int32_t* obj_id, const float* pad_pose,
+                                 const float* pad_twist, const float* g_depth, const float* g_f_n, const float* g_f_t,
+                                 const float* g_wrench, float* grad_pose, float* grad_twist, float* grad_params,
+                                 tacsl_stream_t stream) {
+    SdfTable tab;
+    Params4 prm;
+    int rc = build_table(set, tab);
+    if (rc) return rc;
+    if ((rc = build_params(params, E, prm))) return rc;
+    if (E < 0 || P < 0 || T < 0) return fail(TACSL_ERR_INVALID_ARG, "negative size (E=%d P=%d T=%d)", E, P, T);
+    if (T > TACSL_MAX_TAXELS) return fail(TACSL_ERR_UNSUPPORTED, "T = %d > %d taxels per pad", T, TACSL_MAX_TAXELS);
+    if ((int64_t)E * P >= (int64_t(1) << 31)) return fail(TACSL_ERR_UNSUPPORTED, "E*P >= 2^31 pads");
+    const void* req[] = {taxels, obj_id, pad_pose, pad_twist};
+    const char* rn[] = {"taxels", "obj_id", "pad_pose", "pad_twist"};
+    for (int i = 0; i < 4; ++i) {
+        if (req[i] == nullptr && !(i == 0 && T == 0)) return fail(TACSL_ERR_INVALID_ARG, "%s is NULL", rn[i]);
+        if (!aligned(req[i], 4)) return fail(TACSL_ERR_INVALID_ARG, "%s is not 4-byte aligned", rn[i]);
+    }
+    const void* opt[] = {g_depth, g_f_n, g_f_t, g_wrench, grad_pose, grad_twist, grad_params};
+    for (const void* q : opt)
+        if (!aligned(q, 4)) return fail(TACSL_ERR_INVALID_ARG, "a gradient array is not 4-byte aligned");
+    if (E == 0) return ok();
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    if (grad_params != nullptr && prm.count == 1) {
+        const cudaError_t e = cudaMemsetAsync(grad_params, 0, 4 * sizeof(float), stream);
+        if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+    ForceAdjointArgs a{tab, prm, E, P, T, taxels, obj_id, pad_pose, pad_twist, g_depth, g_f_n, g_f_t, g_wrench,
+                       grad_pose, grad_twist, grad_params};
+    const int64_t blocks = ((int64_t)E + 7) / 8;
+    const int grid = static_cast<int>(std::min<int64_t>(blocks, (int64_t)dev->sms * 16));
+    force_adjoint_kernel<<<grid, 256, 0, stream>>>(a);
+    return check_launch("tacsl_penalty_forces_adjoint");
+}
+
+int tacsl_shade_intensity(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id, const float* depth_map,
+                          float* intensity, tacsl_stream_t stream) {
+    if (shading != nullptr && B == 0) return ok();
+    int rc = check_shade_args(shading, B, sensor_id, depth_map, reinterpret_cast<const uint8_t*>(intensity));
+    if (rc) return rc;
+    if (!aligned(intensity, 4)) return fail(TACSL_ERR_INVALID_ARG, "intensity is not 4-byte aligned");
+    if (shading->H > 65535) return fail(TACSL_ERR_UNSUPPORTED, "image height %d > 65535", shading->H);
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    ShadeGeom G;
+    shade_geom(shading, G);
+    // images per CTA: enough chunks to give every SM several CTAs
+    const int64_t tiles = (G.HW + kPxTile - 1) / kPxTile;
+    int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(65535, (int64_t)dev->sms * 8 / std::max<int64_t>(1, tiles * G.S) + 1));
+    chunks = std::min<int64_t>(chunks, B);
+    const int64_t chunk = (B + chunks - 1) / chunks;
+    flag_bad_sensors_kernel<<<grid_for(B, 4, *dev), 256, 0, stream>>>(B, G.S, sensor_id);
+    shade_intensity_kernel<<<dim3(static_cast<unsigned>(tiles), static_cast<unsigned>(G.S),
+                                  static_cast<unsigned>((B + chunk - 1) / chunk)), 256, 0, stream>>>(
+        G, B, chunk, shading->coeffs, sensor_id, depth_map, intensity);
+    return check_launch("tacsl_shade_intensity");
+}
+
+int tacsl_shade_adjoint(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id, const float* depth_map,
+                        const float* g_intensity, float* grad_coeffs, float* grad_depth, tacsl_stream_t stream) {
+    if (shading != nullptr && B == 0 && grad_coeffs == nullptr) return ok();
+    // the image checks of tacsl_shade_image, with g_intensity in the place of the output
+    int rc = check_shade_args(shading, B, sensor_id, depth_map, reinterpret_cast<const uint8_t*>(g_intensity));
+    if (rc) return rc;
+    if (!aligned(g_intensity, 4) || !aligned(grad_coeffs, 4) || !aligned(grad_depth, 4))
+        return fail(TACSL_ERR_INVALID_ARG, "gradient arrays must be 4-byte aligned");
+    if (shading->H > 65535) return fail(TACSL_ERR_UNSUPPORTED, "image height %d > 65535", shading->H);
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    ShadeGeom G;
+    shade_geom(shading, G);
+    if (grad_coeffs != nullptr) {
+        const int64_t tiles = (G.HW + kPxTile - 1) / kPxTile;
+        if (tiles > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "image too large");
+        shade_coeff_grad_kernel<<<dim3(static_cast<unsigned>(tiles), static_cast<unsigned>(G.S)), 256, 0, stream>>>(
+            G, B, shading->coeffs, sensor_id, depth_map, g_intensity, grad_coeffs);
+        if ((rc = check_launch("tacsl_shade_adjoint (coefficients)"))) return rc;
+    }
+    if (grad_depth != nullptr && B > 0) {
+        shade_depth_grad_kernel<<<pixel_grid(G, B), 128, 0, stream>>>(G, B, shading->coeffs, sensor_id, depth_map,
+                                                                       g_intensity, grad_depth);
+        if ((rc = check_launch("tacsl_shade_adjoint (depth)"))) return rc;
+    }
+    return ok();
+}
+
+}  // extern "C"
