@@ -1248,3 +1248,8 @@ int tacsl_shade_adjoint(const tacsl_shading* shading, int64_t B, const int32_t* 
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Serving (include/tacsl_serve.h)
+// ===========================================================================
+#include "serve.cuh"
