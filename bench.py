@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-templates", type=int, default=16)
+    ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--only-serve", action="store_true",
+                    help="run only the serving section and print it as the JSON line")
     ap.add_argument("--grad-envs", type=int, default=1024)
     ap.add_argument("--grad-steps", type=int, default=20)
     ap.add_argument("--no-grad", action="store_true")
@@ -441,6 +447,7 @@ def run_ours(args, rank, world, local_rank, dist):
 
     batch = None if args.no_batch else run_batch(args, rank, world, local_rank, dist)
     grad = None if args.no_grad else run_grad(args, rank, world, local_rank, dist)
+    serve = None if args.no_serve else run_serve(args, rank, world, local_rank, dist)
 
     if rank != 0:
         return
@@ -488,6 +495,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "render_step": render,
         "batch": batch,
         "grad": grad,
+        "serve": serve,
         "gpu_launches": 2 * args.steps,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -787,6 +795,148 @@ def run_grad(args, rank, world, local_rank, dist):
     }
 
 
+SERVE_WORKLOAD = ("Poisson stream of tactile-step requests of 1-2048 envs (log-uniform) x 2 pads, pad resolutions "
+                  "10x12..40x50 and images 160x120..640x480 per env, over 32 resident SDFs 64^3..256^3; 16 request "
+                  "templates; server admission by a 120 GB HBM budget")
+
+
+def run_serve(args, rank, world, local_rank, dist):
+    """Served requests against the same requests served one at a time through the batch
+    entry points (plain), at Poisson arrival rates of 50 % and 80 % of the plain path's
+    saturation rate; p50 / p99 latency from submission to outputs in host memory."""
+    import threading
+
+    import torch
+
+    import paper_2408_06506_b300 as tacsl
+    from paper_2408_06506_b300 import batch as tb
+    from paper_2408_06506_b300 import serve as sv
+    from paper_2408_06506_b300 import synth
+
+    t_gen = time.perf_counter()
+    w = synth.serve_workload(seed=args.seed + 400 + rank, n_templates=args.serve_templates)
+    t_gen = time.perf_counter() - t_gen
+    torch.cuda.empty_cache()
+
+    def dev(a):
+        return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+    sdfs = tacsl.SdfSet.from_grids(w.grids)
+    sensors = tb.SensorSet([(dev(co), px, py) for co, px, py in w.models])
+    taxels = dev(w.taxels)
+    keys = ("obj_id", "layout", "sensor", "pad_pose", "pad_twist", "k_n", "k_d", "k_t", "mu", "depth_map")
+    tpl = [{k: torch.from_numpy(np.ascontiguousarray(t[k])).pin_memory() for k in keys} for t in w.templates]
+    n_taxel = [int(w.layout_count[t["layout"]].sum()) for t in w.templates]
+    n_pads = [len(t["obj_id"]) for t in w.templates]
+    max_pads = max(n_pads)
+
+    # ---- plain: one request at a time, synchronous, through the batch entry points ----
+    plain_out = {}
+
+    def plain_serve(i):
+        t = tpl[i]
+        plan = tb.BatchPlan(t["obj_id"].numpy(), t["layout"].numpy(), t["sensor"].numpy(), w.layout_first,
+                            w.layout_count, sensors, n_points=w.taxels.shape[0])
+        d = {k: t[k].cuda(non_blocking=True) for k in ("pad_pose", "pad_twist", "k_n", "k_d", "k_t", "mu", "depth_map")}
+        params = tacsl.ContactParams(d["k_n"], d["k_d"], d["k_t"], d["mu"])
+        o = plan.step(sdfs, params, taxels, d["pad_pose"], d["pad_twist"], d["depth_map"])
+        if i not in plain_out:
+            plain_out[i] = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in o.items() if v is not None}
+        for k, v in plain_out[i].items():
+            v.copy_(o[k], non_blocking=True)
+        torch.cuda.synchronize()
+
+    for i in range(len(tpl)):
+        plain_serve(i)
+    assert tacsl.check_errors() == 0
+    svc = []
+    for i in range(len(tpl)):
+        t0 = time.perf_counter()
+        plain_serve(i)
+        svc.append(time.perf_counter() - t0)
+    svc = np.array(svc)
+    plain_rate = len(tpl) / svc.sum()                       # requests/s at saturation
+    plain_sat = sum(n_taxel) / svc.sum()                    # taxel-points/s at saturation
+
+    # ---- the server ----
+    budget = min(120 << 30, int(torch.cuda.mem_get_info()[0] * 0.8))
+    srv = sv.Server(sdfs, sensors, taxels, w.layout_first, w.layout_count, hbm_budget_bytes=budget,
+                    max_pads=max_pads, n_streams=args.serve_streams, batch_timeout_ms=60000)
+    outs = [srv.outputs_for(t["layout"].numpy(), t["sensor"].numpy()) for t in tpl]
+
+    def submit(i):
+        t = tpl[i]
+        return srv.submit(out=outs[i], **{k: t[k] for k in keys})
+
+    for i in range(len(tpl)):                               # warm-up, and a check against plain
+        st, _ = srv.wait(submit(i))
+        assert st == 0
+        for k in ("depth", "f_n", "f_t", "wrench"):
+            assert torch.equal(outs[i][k], plain_out[i][k]), k
+    assert torch.equal(outs[0]["rgb"][:plain_out[0]["rgb"].shape[0]], plain_out[0]["rgb"])
+    # saturation: every request submitted at once
+    g = np.random.default_rng(args.seed + 500 + rank)
+    order = g.integers(0, len(tpl), size=args.serve_requests)
+    t0 = time.perf_counter()
+    ids = [submit(int(i)) for i in order]
+    for rid in ids:
+        srv.wait(rid)
+    srv_sat_s = time.perf_counter() - t0
+    srv_sat = sum(n_taxel[int(i)] for i in order) / srv_sat_s
+
+    def run_stream(rate, serve_fn):
+        gaps = g.exponential(1.0 / rate, size=len(order))
+        arrive = np.cumsum(gaps) - gaps[0]
+        lat = np.zeros(len(order))
+        start = time.perf_counter()
+        if serve_fn == "server":
+            ids = [None] * len(order)
+
+            def producer():
+                for k, i in enumerate(order):
+                    dt = start + arrive[k] - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    ids[k] = submit(int(i))
+            th = threading.Thread(target=producer)
+            th.start()
+            th.join()
+            for k in range(len(order)):
+                lat[k] = srv.wait(ids[k])[1]
+        else:
+            for k, i in enumerate(order):
+                dt = start + arrive[k] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                plain_serve(int(i))
+                lat[k] = 1e3 * (time.perf_counter() - (start + arrive[k]))
+        span = time.perf_counter() - start
+        return {"rate_req_per_s": rate, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "throughput": sum(n_taxel[int(i)] for i in order) / span}
+
+    streams = {}
+    for frac in (0.5, 0.8):
+        streams[f"{int(frac * 100)}%"] = {"server": run_stream(frac * plain_rate, "server"),
+                                          "plain": run_stream(frac * plain_rate, "plain")}
+    st = srv.stats()
+    srv.close()
+    assert tacsl.check_errors() == 0
+    mean_env = float(np.mean([t["n_env"] for t in w.templates]))
+    return {
+        "workload": SERVE_WORKLOAD, "templates": len(tpl), "requests_per_run": int(len(order)),
+        "template_envs": [t["n_env"] for t in w.templates], "mean_envs_per_request": mean_env,
+        "unit": "taxel-points/s", "generation_s": t_gen, "hbm_budget_bytes": budget, "n_streams": args.serve_streams,
+        "plain": {"saturation": plain_sat, "saturation_req_per_s": plain_rate,
+                  "service_ms": {"mean": float(1e3 * svc.mean()), "max": float(1e3 * svc.max())},
+                  "path": "per request: tacsl_batch_plan/upload, copies in, tacsl_batch_step, copies out, synchronise"},
+        "server": {"saturation": srv_sat, "saturation_speedup": srv_sat / plain_sat,
+                   "batches": st["batches"], "max_batch_requests": st["max_batch_requests"],
+                   "arena_peak_bytes": st["arena_peak_bytes"]},
+        "poisson": streams,
+        "latency": "from submission (arrival) to all outputs in pinned host memory",
+    }
+
+
 def _smi_id(ordinal):
     """nvidia-smi id of a CUDA ordinal (its UUID; ordinals differ under CUDA_VISIBLE_DEVICES)."""
     import torch
@@ -823,6 +973,18 @@ def main():
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
         dist = tdist
     try:
+        if args.only_serve:
+            import torch
+            torch.cuda.set_device(local_rank)
+            from paper_2408_06506_b300 import build
+            if rank == 0:
+                build.build()
+            if dist is not None:
+                dist.barrier()
+            out = run_serve(args, rank, world, local_rank, dist)
+            if rank == 0:
+                print(json.dumps({"impl": "ours", "section": "serve", "n_gpus": world, **out}), flush=True)
+            return
         if args.only_grad:
             import torch
             torch.cuda.set_device(local_rank)

@@ -620,3 +620,89 @@ def scene_batch(seed: int = 3, E: int = 16384, P: int = 2, grids: list | None = 
                     twist, k_n, k_d, k_t, mu, models, maps)
     sc.meta.update(E=E, P=P, n_layout=len(first), n_model=len(models), depth_maps=depth_maps)
     return sc
+
+
+# ---------------------------------------------------------------------------
+# Request streams for the server
+# ---------------------------------------------------------------------------
+
+@dataclass
+class ServeWorkload:
+    """Resident state (grids, sensor models, taxel-layout pool) and request templates.
+
+    Each template is a dict with per-pad obj_id, layout, sensor, pad_pose, pad_twist,
+    k_n, k_d, k_t, mu (float32 / int32 arrays), the packed depth maps of its pads with an
+    image (pad order) and n_env."""
+    grids: list
+    models: list                      # [(coeffs [6][3][H][W], pitch_x, pitch_y)]
+    taxels: np.ndarray                # pool [n_points][3]
+    layout_first: np.ndarray
+    layout_count: np.ndarray
+    templates: list
+
+
+def serve_workload(seed: int = 5, n_templates: int = 16, env_range=(1, 2048), P: int = 2, n_grid: int = 32,
+                   grid_sides=(64, 256), res_y=(10, 40), res_x=(12, 50), width=(160, 640), n_size_class: int = 16,
+                   maps_per_model: int = 2, vel_sigma: float = 0.05) -> ServeWorkload:
+    """Requests of log-uniform env counts in env_range (P pads per env), each env drawing
+    its pad resolution, object (from a resident pool of n_grid grids, sides log-uniform
+    in grid_sides) and image size class as in scene_batch; every resolution in the
+    res_y x res_x box is a resident layout.  Depth maps: maps_per_model heightfields per
+    sensor model (of a pad indenting a pool object), handed out in turn."""
+    g = rng(seed)
+    grids = grid_pool(seed + 1, n_grid, *grid_sides)
+    u = (np.arange(n_size_class) + g.random(n_size_class)) / n_size_class
+    ws = np.exp(np.log(width[0]) + u * (np.log(width[1]) - np.log(width[0])))
+    ws = np.maximum(4, 4 * np.rint(ws / 4.0).astype(np.int64))
+    hs = np.maximum(4, 4 * np.rint(0.75 * ws / 4.0).astype(np.int64))
+    models = []
+    for c in range(n_size_class):
+        H, W = int(hs[c]), int(ws[c])
+        for p in range(P):
+            co = shading_coeffs(1, H, W, seed * 1000 + P * c + p)[0]
+            models.append((co, PAD_EXTENT[0] / W, PAD_EXTENT[1] / H))
+    # every resolution of the box is resident
+    keys = [(ny, nx) for ny in range(res_y[0], res_y[1] + 1) for nx in range(res_x[0], res_x[1] + 1)]
+    index, pool, first, count = {}, [], [], []
+    n_points = 0
+    for key in keys:
+        t = taxel_grid(key[0], key[1], PAD_EXTENT[0] / (key[1] - 1), PAD_EXTENT[1] / (key[0] - 1))
+        index[key] = len(first)
+        first.append(n_points)
+        count.append(t.shape[0])
+        pool.append(t)
+        n_points += t.shape[0]
+    maps = {}
+    for m, (co, _, _) in enumerate(models):
+        H, W = co.shape[2], co.shape[3]
+        lst = []
+        for k in range(maps_per_model):
+            obj = int(g.integers(0, len(grids)))
+            pose = place_pad(grids[obj].shape, random_quaternion(g), g.uniform(0.5e-3, 2e-3), g.uniform(-2e-3, 2e-3, 2))
+            lst.append(depth_map(grids[obj].shape, pose, H, W, *PAD_EXTENT).reshape(-1))
+        maps[m] = lst
+    templates = []
+    for _ in range(n_templates):
+        E = int(log_uniform_int(g, env_range[0], env_range[1]))
+        ny = log_uniform_int(g, res_y[0], res_y[1], size=E)
+        nx = log_uniform_int(g, res_x[0], res_x[1], size=E)
+        obj_env = g.integers(0, len(grids), size=E)
+        cls_env = g.integers(0, n_size_class, size=E)
+        n = E * P
+        obj = np.repeat(obj_env, P).astype(np.int32)
+        layout = np.repeat([index[(int(a), int(b))] for a, b in zip(ny, nx)], P).astype(np.int32)
+        sensor = (P * np.repeat(cls_env, P) + np.tile(np.arange(P), E)).astype(np.int32)
+        pose = np.zeros((n, 7), np.float32)
+        twist = np.zeros((n, 6), np.float32)
+        for b in range(n):
+            pose[b] = place_pad(grids[obj[b]].shape, random_quaternion(g), g.uniform(-2e-3, 2e-3),
+                                g.uniform(-2e-3, 2e-3, size=2))
+            twist[b, :3] = g.normal(0.0, vel_sigma, size=3)
+        k_n = np.repeat(g.uniform(0.5e4, 1.5e4, size=E), P).astype(np.float32)
+        k_t = np.repeat(g.uniform(50.0, 150.0, size=E), P).astype(np.float32)
+        mu = np.repeat(g.uniform(0.3, 0.7, size=E), P).astype(np.float32)
+        dm = np.concatenate([maps[int(s)][b % maps_per_model] for b, s in enumerate(sensor)])
+        templates.append(dict(n_env=E, obj_id=obj, layout=layout, sensor=sensor, pad_pose=pose, pad_twist=twist,
+                              k_n=k_n, k_d=np.zeros(n, np.float32), k_t=k_t, mu=mu, depth_map=dm))
+    return ServeWorkload(grids, models, np.ascontiguousarray(np.concatenate(pool).astype(np.float32)),
+                         np.asarray(first, np.int64), np.asarray(count, np.int32), templates)
