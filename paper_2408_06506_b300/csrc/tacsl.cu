@@ -201,12 +201,26 @@ int plan_shade(const tacsl_shading* sh, int64_t B, const int32_t* sensor_id, con
         a.store_mode = kStoreWord;
     else
         a.store_mode = kStoreByte;
-    // Images per work item: the largest power of two in [32, 1024] that still leaves
-    // at least 24 items per CTA (a short tail), so coefficient reloads are amortised
-    // over as many images as the load balance allows.
+    // Images per work item: the CTAs take items round-robin, so the launch lasts about
+    // ceil(items / CTAs) items of M images each (plus about 8 images' worth of item
+    // switching).  M in [16, 1024] minimising that makespan - whole rounds with few item
+    // switches - among the choices that leave at least 16 items per CTA where the batch
+    // allows it (item times vary with the depth maps' content; many items average that
+    // out); ties go to the larger M.
     const int64_t per_blk = (int64_t)a.S * a.n_tiles;
-    int M = 1024;
-    while (M > 32 && ((B + M - 1) / M) * per_blk < 24LL * dev.sms) M /= 2;
+    const bool deep = ((B + 15) / 16) * per_blk >= 16LL * dev.sms;
+    int M = 16;
+    double best = 0.0;
+    for (int m = 1024; m >= 16; --m) {
+        const int64_t items = ((B + m - 1) / m) * per_blk;
+        const int64_t grid = std::min<int64_t>(items, dev.sms);
+        if (deep && items < 16LL * grid) continue;
+        const double cost = (double)((items + grid - 1) / grid) * (double)(std::min<int64_t>(m, B) + 8);
+        if (best == 0.0 || cost < best) {
+            best = cost;
+            M = m;
+        }
+    }
     const int64_t n_items = ((B + M - 1) / M) * per_blk;
     if (n_items >= (int64_t(1) << 31)) return fail(TACSL_ERR_UNSUPPORTED, "too many work items");
     a.M = M;
