@@ -87,19 +87,22 @@ __device__ __forceinline__ float column_phi(const DevSdf& S, float x, float y, f
     return sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
 }
 
+// Grid: (32 x 8 pixel tiles of the image, images); each warp marches 32 neighbouring
+// columns of one row, and every thread keeps its column across the images it takes.
 __global__ void __launch_bounds__(256) render_kernel(const SdfTable tab, int64_t B, int P,
                                                      const int32_t* __restrict__ obj_id,
                                                      const float* __restrict__ pad_pose, const CameraArgs cam,
                                                      float* __restrict__ depth) {
+    const int tiles_x = (cam.W + 31) / 32;
+    const int tile_y = static_cast<int>(blockIdx.x) / tiles_x, tile_x = static_cast<int>(blockIdx.x) - tile_y * tiles_x;
+    const int i = tile_x * 32 + static_cast<int>(threadIdx.x & 31), j = tile_y * 8 + static_cast<int>(threadIdx.x >> 5);
+    if (i >= cam.W || j >= cam.H) return;
     const int64_t HW = static_cast<int64_t>(cam.H) * cam.W;
-    const int64_t n = B * HW;
+    const int pix = j * cam.W + i;
     const uint64_t pol = policy_evict_last();
-    for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
-         k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t b = k / HW;
-        const int pix = static_cast<int>(k - b * HW);
-        const int j = pix / cam.W, i = pix - j * cam.W;
-        const int id = __ldg(obj_id + b / P);
+    for (int64_t b = blockIdx.y; b < B; b += gridDim.y) {
+        const int64_t k = b * HW + pix;
+        const int id = __ldg(obj_id + static_cast<int>(b) / P);
         if (id < 0 || id >= tab.count) {
             depth[k] = __int_as_float(0x7fc00000);
             raise_dev_error(TACSL_DEVERR_BAD_OBJ_ID);

@@ -280,9 +280,11 @@ int check_camera(const tacsl_camera* cam, CameraArgs& c) {
 
 int launch_render(const SdfTable& tab, int64_t B, int P, const int32_t* obj_id, const float* pad_pose,
                   const CameraArgs& c, float* depth_map, const DevInfo& dev, tacsl_stream_t stream) {
-    const int64_t n = B * c.H * c.W;
-    const int64_t blocks = (n + 255) / 256;
-    const int grid = static_cast<int>(blocks < (int64_t)dev.sms * 64 ? blocks : (int64_t)dev.sms * 64);
+    (void)dev;
+    const int64_t tiles = (int64_t)((c.W + 31) / 32) * ((c.H + 7) / 8);
+    if (tiles > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "camera image too large");
+    // each block loops over images: about (tiles x 64) blocks in all, whatever the batch
+    const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(std::min<int64_t>(B, 64)));
     render_kernel<<<grid, 256, 0, stream>>>(tab, B, P, obj_id, pad_pose, c, depth_map);
     return check_launch("render kernel");
 }
