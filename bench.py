@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-chunk", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -412,27 +413,31 @@ def run_ours(args, rank, world, local_rank, dist):
                          "d2h_bytes_per_step": h_wr.numel() * 4, "steps": n_r,
                          "path": "pinned pose+twist -> tacsl_render_step -> pinned wrench; images stay on device"}
 
-    # ---- end to end: pinned host inputs in, results back to pinned host, every step ----
+    # ---- end to end: through the C-ABI call with HOST buffers (tacsl_tactile_step_host):
+    # every step reads its inputs from pinned host memory and writes its results back there,
+    # pipelined in chunks of envs over the library's internal streams ----
     e2e = None
     if not args.no_e2e:
-        h_in = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory() for k, v in
-                (("pose", sc.pad_pose), ("twist", sc.pad_twist), ("depth_map", sc.depth_map),
-                 ("obj_id", sc.obj_id), ("sensor_id", sc.sensor_id))}
-        d_in = {"pose": pose, "twist": twist, "depth_map": depth_map, "obj_id": obj_id, "sensor_id": sensor_id}
+        h_in = {"obj_id": torch.as_tensor(sc.obj_id).pin_memory(), "pose": torch.as_tensor(sc.pad_pose).pin_memory(),
+                "twist": torch.as_tensor(sc.pad_twist).pin_memory(),
+                "sensor_id": torch.as_tensor(sc.sensor_id).pin_memory(),
+                "depth_map": torch.as_tensor(np.ascontiguousarray(sc.depth_map).reshape(-1, sc.H, sc.W)).pin_memory()}
         h_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs.items()}
         h2d = sum(t.numel() * t.element_size() for t in h_in.values())
         d2h = sum(t.numel() * t.element_size() for t in h_out.values())
+        ch = max(1, min(args.e2e_chunk, E))
+        ws = torch.empty(tacsl.load().tacsl_tactile_step_host_workspace(ch, P, T, sc.H, sc.W), dtype=torch.uint8,
+                         device="cuda")
 
         def e2e_step():
-            for k, t in h_in.items():
-                d_in[k].copy_(t, non_blocking=True)
-            tacsl.tactile_step(sdfs, params, taxels, d_in["obj_id"], d_in["pose"], d_in["twist"], shading,
-                               d_in["sensor_id"], d_in["depth_map"], **outs)
-            for k, t in outs.items():
-                h_out[k].copy_(t, non_blocking=True)
+            tacsl.tactile_step_host(sdfs, params, taxels, h_in["obj_id"], h_in["pose"], h_in["twist"], shading,
+                                    h_in["sensor_id"], h_in["depth_map"], out=h_out, chunk_envs=ch, workspace=ws)
 
+        step()                     # the device-buffer step on the same inputs, for the check below
         e2e_step()
         torch.cuda.synchronize()
+        for k in ("depth", "f_n", "f_t", "wrench", "rgb"):
+            assert torch.equal(h_out[k], outs[k].cpu()), k
         if dist is not None:
             dist.barrier()
         t0 = time.perf_counter()
@@ -443,7 +448,8 @@ def run_ours(args, rank, world, local_rank, dist):
         e2e = {"value": world * E * P * T * args.e2e_steps / el, "unit": "taxel-points/s",
                "images_per_s": world * E * P * args.e2e_steps / el, "ms_per_step": 1e3 * el / args.e2e_steps,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
-               "path": "pinned host -> cudaMemcpyAsync -> tacsl_tactile_step -> pinned host, one stream"}
+               "copy_gb_per_s": (h2d + d2h) * args.e2e_steps / el / 1e9, "chunk_envs": ch,
+               "path": "pinned host -> tacsl_tactile_step_host (chunks pipelined over 3 streams) -> pinned host"}
 
     batch = None if args.no_batch else run_batch(args, rank, world, local_rank, dist)
     grad = None if args.no_grad else run_grad(args, rank, world, local_rank, dist)

@@ -231,6 +231,30 @@ int tacsl_render_step(const tacsl_sdf_set* set, const tacsl_contact_params* para
                       const tacsl_camera* camera, const int32_t* sensor_id, float* depth_map,
                       uint8_t* rgb, tacsl_stream_t stream);
 
+/* Device workspace (bytes) tacsl_tactile_step_host needs for chunks of chunk_envs envs of
+ * P pads x T taxels and H x W images (H = W = 0: no images).  Negative sizes give -1. */
+int64_t tacsl_tactile_step_host_workspace(int32_t chunk_envs, int32_t P, int32_t T, int32_t H, int32_t W);
+
+/* tacsl_tactile_step with the per-step arrays in HOST memory: obj_id [E], pad_pose
+ * [E*P][7], pad_twist [E*P][6], sensor_id [E*P], depth_map [E*P][H][W] are read from
+ * the host, and depth, f_n, f_t, wrench (may be NULL), rgb are written to the host, in
+ * the layouts of tacsl_tactile_step; the SDFs, params, taxels and shading coefficients
+ * stay on the device.  The envs go through in chunks of chunk_envs, pipelined on three
+ * internal streams of this device: one chunk's inputs travel to the GPU while another
+ * chunk computes and a third's outputs travel back.  workspace: device memory of at least
+ * tacsl_tactile_step_host_workspace(chunk_envs, P, T, H, W) bytes, 256-byte aligned.  The
+ * call enqueues everything after the work already on `stream` and makes `stream` wait for
+ * it, so synchronising `stream` means the host outputs are complete.  Pinned (page-locked)
+ * host memory is needed for the copies to overlap; depth_map must be 16-byte aligned.  Calls on one device are enqueued one
+ * at a time (an internal lock). */
+int tacsl_tactile_step_host(const tacsl_sdf_set* set, const tacsl_contact_params* params, int32_t E,
+                            int32_t P, int32_t T, const float* taxels, const int32_t* obj_id,
+                            const float* pad_pose, const float* pad_twist, float* depth, float* f_n,
+                            float* f_t, float* wrench, const tacsl_shading* shading,
+                            const int32_t* sensor_id, const float* depth_map, uint8_t* rgb,
+                            int32_t chunk_envs, void* workspace, int64_t workspace_bytes,
+                            tacsl_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,7 +9,7 @@ module raises instead of falling back.
 
 Entry points (same names as the C ABI, without the ``tacsl_`` prefix):
 ``sdf_query``, ``penalty_forces``, ``pad_wrench``, ``shade_image``, ``tactile_step``,
-``render_depth``, ``render_step``, ``check_errors``.
+``tactile_step_host``, ``render_depth``, ``render_step``, ``check_errors``.
 """
 from __future__ import annotations
 
@@ -19,8 +19,8 @@ import os
 import torch
 
 __all__ = ["SdfSet", "ContactParams", "Shading", "Camera", "TacslError", "sdf_query", "penalty_forces",
-           "pad_wrench", "shade_image", "tactile_step", "render_depth", "render_step", "check_errors",
-           "library_path", "load"]
+           "pad_wrench", "shade_image", "tactile_step", "tactile_step_host", "render_depth", "render_step",
+           "check_errors", "library_path", "load"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "libtacsl.so")
@@ -95,6 +95,11 @@ def load():
                                            P, P, P, P, C.POINTER(_Shading), P, P, P, P]
         lib.tacsl_render_depth.restype = C.c_int
         lib.tacsl_render_depth.argtypes = [C.POINTER(_SdfSet), I32, I32, P, P, C.POINTER(_Camera), P, P]
+        lib.tacsl_tactile_step_host_workspace.restype = I64
+        lib.tacsl_tactile_step_host_workspace.argtypes = [I32, I32, I32, I32, I32]
+        lib.tacsl_tactile_step_host.restype = C.c_int
+        lib.tacsl_tactile_step_host.argtypes = [C.POINTER(_SdfSet), C.POINTER(_Params), I32, I32, I32, P, P, P, P,
+                                                P, P, P, P, C.POINTER(_Shading), P, P, P, I32, P, I64, P]
         lib.tacsl_render_step.restype = C.c_int
         lib.tacsl_render_step.argtypes = [C.POINTER(_SdfSet), C.POINTER(_Params), I32, I32, I32, P, P, P, P,
                                           P, P, P, P, C.POINTER(_Shading), C.POINTER(_Camera), P, P, P, P]
@@ -315,3 +320,44 @@ def render_step(sdfs: SdfSet, params: ContactParams, taxels, obj_id, pad_pose, p
                                     C.byref(shading.c), C.byref(camera.c), _ptr(sensor_id), _ptr(depth_map),
                                     _ptr(rgb), _stream(stream)))
     return depth, f_n, f_t, wrench, depth_map, rgb
+
+
+def _host_t(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    return t
+
+
+def tactile_step_host(sdfs: SdfSet, params: ContactParams, taxels, obj_id, pad_pose, pad_twist,
+                      shading: Shading | None = None, sensor_id=None, depth_map=None, out=None, chunk_envs=512,
+                      workspace=None, stream=None):
+    """tactile_step with the per-step arrays in host memory (pinned for overlap): obj_id,
+    pad_pose, pad_twist, sensor_id, depth_map in; (depth, f_n, f_t, wrench, rgb) host
+    tensors out, written when the stream reaches the end of the call."""
+    _dev(taxels, torch.float32, "taxels")
+    for t, n, dt in ((obj_id, "obj_id", torch.int32), (pad_pose, "pad_pose", torch.float32),
+                     (pad_twist, "pad_twist", torch.float32)):
+        _host_t(t, dt, n)
+    E, P = pad_pose.shape[0], pad_pose.shape[1]
+    T = taxels.shape[0]
+    H, W = (shading.H, shading.W) if shading is not None else (0, 0)
+    if shading is not None:
+        _host_t(sensor_id, torch.int32, "sensor_id")
+        _host_t(depth_map, torch.float32, "depth_map")
+    if out is None:
+        pin = lambda *sh, dtype=torch.float32: torch.empty(*sh, dtype=dtype).pin_memory()   # noqa: E731
+        out = {"depth": pin(E, P, T), "f_n": pin(E, P, T, 3), "f_t": pin(E, P, T, 3), "wrench": pin(E, P, 6),
+               "rgb": pin(E * P, H, W, 3, dtype=torch.uint8) if shading is not None else None}
+    ch = max(1, min(int(chunk_envs), E))
+    need = load().tacsl_tactile_step_host_workspace(ch, P, T, H, W)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=taxels.device)
+    _check(load().tacsl_tactile_step_host(
+        C.byref(sdfs.c), C.byref(params.c), E, P, T, _ptr(taxels), _ptr(obj_id), _ptr(pad_pose), _ptr(pad_twist),
+        _ptr(out["depth"]), _ptr(out["f_n"]), _ptr(out["f_t"]), _ptr(out.get("wrench")),
+        C.byref(shading.c) if shading is not None else None, _ptr(sensor_id) if shading is not None else None,
+        _ptr(depth_map) if shading is not None else None, _ptr(out.get("rgb")) if shading is not None else None,
+        ch, _ptr(workspace), workspace.numel(), _stream(stream)))
+    return out["depth"], out["f_n"], out["f_t"], out.get("wrench"), out.get("rgb")

@@ -57,6 +57,10 @@ struct DevInfo {
     bool shade_attr_set = false;
     bool batch_shade_attr_set = false;
     int batch_force_ctas[4] = {0, 0, 0, 0};   // resident CTAs per SM: [np == 4][dynamic]
+    // streams and events of tacsl_tactile_step_host, created on its first call here
+    cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t pipe_start = nullptr, pipe_done[3] = {nullptr, nullptr, nullptr};
+    std::mutex pipe_mu;
 };
 constexpr int kMaxDevices = 64;
 DevInfo g_dev[kMaxDevices];
@@ -1260,6 +1264,163 @@ int tacsl_shade_adjoint(const tacsl_shading* shading, int64_t B, const int32_t* 
                                                                        g_intensity, grad_depth);
         if ((rc = check_launch("tacsl_shade_adjoint (depth)"))) return rc;
     }
+    return ok();
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// The tactile step from and to host memory, pipelined (tacsl_tactile_step_host)
+// ===========================================================================
+namespace tacsl {
+namespace {
+
+struct HostChunk {   // offsets of one chunk's device arrays in a workspace slot
+    int64_t obj, pose, twist, sid, dmap, depth, fn, ft, wrench, rgb, bytes;
+};
+
+HostChunk host_chunk_layout(int64_t ec, int64_t P, int64_t T, int64_t HW) {
+    HostChunk c;
+    int64_t at = 0;
+    auto take = [&](int64_t n) {
+        const int64_t o = at;
+        at += (std::max<int64_t>(n, 1) + 255) / 256 * 256;
+        return o;
+    };
+    c.obj = take(4 * ec);
+    c.pose = take(28 * ec * P);
+    c.twist = take(24 * ec * P);
+    c.sid = take(4 * ec * P);
+    c.dmap = take(4 * ec * P * HW);
+    c.depth = take(4 * ec * P * T);
+    c.fn = take(12 * ec * P * T);
+    c.ft = take(12 * ec * P * T);
+    c.wrench = take(24 * ec * P);
+    c.rgb = take(3 * ec * P * HW);
+    c.bytes = at;
+    return c;
+}
+
+int pipe_setup(DevInfo& dev) {
+    if (dev.pipe[0] != nullptr) return TACSL_OK;
+    cudaError_t e = cudaEventCreateWithFlags(&dev.pipe_start, cudaEventDisableTiming);
+    for (int s = 0; s < 3 && e == cudaSuccess; ++s) {
+        e = cudaStreamCreateWithFlags(&dev.pipe[s], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&dev.pipe_done[s], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "pipeline streams: %s", cudaGetErrorString(e));
+    return TACSL_OK;
+}
+
+}  // namespace
+}  // namespace tacsl
+
+extern "C" {
+
+int64_t tacsl_tactile_step_host_workspace(int32_t chunk_envs, int32_t P, int32_t T, int32_t H, int32_t W) {
+    if (chunk_envs < 1 || P < 0 || T < 0 || H < 0 || W < 0) return -1;
+    return 3 * tacsl::host_chunk_layout(chunk_envs, P, T, (int64_t)H * W).bytes;
+}
+
+int tacsl_tactile_step_host(const tacsl_sdf_set* set, const tacsl_contact_params* params, int32_t E, int32_t P,
+                            int32_t T, const float* taxels, const int32_t* obj_id, const float* pad_pose,
+                            const float* pad_twist, float* depth, float* f_n, float* f_t, float* wrench,
+                            const tacsl_shading* shading, const int32_t* sensor_id, const float* depth_map,
+                            uint8_t* rgb, int32_t chunk_envs, void* workspace, int64_t workspace_bytes,
+                            tacsl_stream_t stream) {
+    SdfTable tab;
+    Params4 prm;
+    int rc = build_table(set, tab);
+    if (rc) return rc;
+    if ((rc = build_params(params, E, prm))) return rc;
+    if (E < 0 || P < 0 || T < 0) return fail(TACSL_ERR_INVALID_ARG, "negative size (E=%d P=%d T=%d)", E, P, T);
+    if (T > TACSL_MAX_TAXELS) return fail(TACSL_ERR_UNSUPPORTED, "T = %d > %d taxels per pad", T, TACSL_MAX_TAXELS);
+    if ((int64_t)E * P >= (int64_t(1) << 31)) return fail(TACSL_ERR_UNSUPPORTED, "E*P >= 2^31 pads");
+    if (chunk_envs < 1) return fail(TACSL_ERR_INVALID_ARG, "chunk_envs = %d < 1", chunk_envs);
+    if ((int64_t)E * P == 0) return ok();
+    const void* req[] = {taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t};
+    const char* rn[] = {"taxels", "obj_id", "pad_pose", "pad_twist", "depth", "f_n", "f_t"};
+    for (int i = 0; i < 7; ++i) {
+        if (req[i] == nullptr && !(i == 0 && T == 0)) return fail(TACSL_ERR_INVALID_ARG, "%s is NULL", rn[i]);
+        if (!aligned(req[i], 4)) return fail(TACSL_ERR_INVALID_ARG, "%s is not 4-byte aligned", rn[i]);
+    }
+    int64_t HW = 0;
+    if (shading != nullptr) {
+        // the image arguments as tacsl_shade_image checks them (host arrays here)
+        if ((rc = check_shade_args(shading, (int64_t)E * P, sensor_id, depth_map, rgb))) return rc;
+        HW = (int64_t)shading->H * shading->W;
+    }
+    const int32_t ch = std::min(chunk_envs, E);
+    const HostChunk L = host_chunk_layout(ch, P, T, HW);
+    if (workspace == nullptr || !aligned(workspace, 256) || workspace_bytes < 3 * L.bytes)
+        return fail(TACSL_ERR_INVALID_ARG, "workspace NULL, not 256-byte aligned or below %lld bytes",
+                    (long long)(3 * L.bytes));
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    std::lock_guard<std::mutex> lk(dev->pipe_mu);
+    if ((rc = pipe_setup(*dev))) return rc;
+    cudaError_t e = cudaEventRecord(dev->pipe_start, stream);
+    const int n_chunks = (E + ch - 1) / ch;
+    for (int s = 0; s < 3 && s < n_chunks && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(dev->pipe[s], dev->pipe_start, 0);
+    if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "pipeline start: %s", cudaGetErrorString(e));
+    auto h2d = [&](void* dst, const void* src, int64_t n, cudaStream_t st) {
+        return n > 0 ? cudaMemcpyAsync(dst, src, (size_t)n, cudaMemcpyHostToDevice, st) : cudaSuccess;
+    };
+    auto d2h = [&](void* dst, const void* src, int64_t n, cudaStream_t st) {
+        return n > 0 ? cudaMemcpyAsync(dst, src, (size_t)n, cudaMemcpyDeviceToHost, st) : cudaSuccess;
+    };
+    for (int c = 0; c < n_chunks; ++c) {
+        const int64_t e0 = (int64_t)c * ch, ec = std::min<int64_t>(ch, E - e0);
+        const int64_t b0 = e0 * P, bc = ec * P;
+        cudaStream_t st = dev->pipe[c % 3];
+        char* base = static_cast<char*>(workspace) + (int64_t)(c % 3) * L.bytes;
+        int32_t* d_obj = reinterpret_cast<int32_t*>(base + L.obj);
+        float* d_pose = reinterpret_cast<float*>(base + L.pose);
+        float* d_twist = reinterpret_cast<float*>(base + L.twist);
+        int32_t* d_sid = reinterpret_cast<int32_t*>(base + L.sid);
+        float* d_dmap = reinterpret_cast<float*>(base + L.dmap);
+        float* d_depth = reinterpret_cast<float*>(base + L.depth);
+        float* d_fn = reinterpret_cast<float*>(base + L.fn);
+        float* d_ft = reinterpret_cast<float*>(base + L.ft);
+        float* d_wr = reinterpret_cast<float*>(base + L.wrench);
+        uint8_t* d_rgb = reinterpret_cast<uint8_t*>(base + L.rgb);
+        // copies in (the slot's previous chunk is done with it: same stream)
+        e = h2d(d_obj, obj_id + e0, 4 * ec, st);
+        if (e == cudaSuccess) e = h2d(d_pose, pad_pose + 7 * b0, 28 * bc, st);
+        if (e == cudaSuccess) e = h2d(d_twist, pad_twist + 6 * b0, 24 * bc, st);
+        if (e == cudaSuccess && shading) e = h2d(d_sid, sensor_id + b0, 4 * bc, st);
+        if (e == cudaSuccess && shading) e = h2d(d_dmap, depth_map + b0 * HW, 4 * bc * HW, st);
+        if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "pipeline copy-in: %s", cudaGetErrorString(e));
+        // the step on this chunk
+        if (shading) {
+            ShadePlan plan;
+            if ((rc = plan_shade(shading, bc, d_sid, d_dmap, d_rgb, *dev, plan))) return rc;
+            if ((rc = launch_shade(plan, *dev, st))) return rc;
+        }
+        if (T > 0) {
+            Params4 pc = prm;
+            if (prm.count != 1) {
+                pc.k_n += e0; pc.k_d += e0; pc.k_t += e0; pc.mu += e0;
+                pc.count = static_cast<int>(ec);
+            }
+            if ((rc = launch_penalty(tab, pc, bc, P, T, taxels, d_obj, d_pose, d_twist, d_depth, d_fn, d_ft,
+                                     wrench ? d_wr : nullptr, *dev, st)))
+                return rc;
+        }
+        // copies out
+        e = d2h(depth + b0 * T, d_depth, 4 * bc * T, st);
+        if (e == cudaSuccess) e = d2h(f_n + 3 * b0 * T, d_fn, 12 * bc * T, st);
+        if (e == cudaSuccess) e = d2h(f_t + 3 * b0 * T, d_ft, 12 * bc * T, st);
+        if (e == cudaSuccess && wrench) e = d2h(wrench + 6 * b0, d_wr, 24 * bc, st);
+        if (e == cudaSuccess && shading) e = d2h(rgb + 3 * b0 * HW, d_rgb, 3 * bc * HW, st);
+        if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "pipeline copy-out: %s", cudaGetErrorString(e));
+    }
+    // the caller's stream waits for every chunk
+    for (int s = 0; s < 3 && s < n_chunks && e == cudaSuccess; ++s) {
+        e = cudaEventRecord(dev->pipe_done[s], dev->pipe[s]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, dev->pipe_done[s], 0);
+    }
+    if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "pipeline end: %s", cudaGetErrorString(e));
     return ok();
 }
 

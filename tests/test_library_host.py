@@ -230,3 +230,24 @@ def test_render_step_requires_matching_camera(lib):
     rc = lib.tacsl_render_step(C.byref(st), C.byref(prm), 2, 2, 10, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE,
                                C.byref(sh), C.byref(cam), FAKE, FAKE, FAKE, None)
     assert rc == INVALID and "camera" in lib.tacsl_last_error().decode()
+
+
+def test_host_step_workspace_and_rejections(lib):
+    ws = lib.tacsl_tactile_step_host_workspace
+    ws.restype = C.c_int64
+    ws.argtypes = [C.c_int32] * 5
+    assert ws(0, 2, 10, 8, 16) == -1 and ws(4, -1, 10, 8, 16) == -1
+    one, two = ws(1, 2, 10, 8, 16), ws(2, 2, 10, 8, 16)
+    assert one > 0 and two > one and one % 256 == 0
+    st, prm = _set(_sdf()), _params()
+    sh = _shading(H=8, W=16)
+    f = lib.tacsl_tactile_step_host
+
+    def call(chunk=2, wsp=FAKE, wsb=1 << 30, pose=FAKE, dmap=FAKE):
+        return f(C.byref(st), C.byref(prm), 4, 2, 10, FAKE, FAKE, pose, FAKE, FAKE, FAKE, FAKE, FAKE, C.byref(sh),
+                 FAKE, dmap, FAKE, chunk, wsp, wsb, None)
+    assert call(chunk=0) == INVALID
+    assert call(wsb=ws(2, 2, 10, 8, 16) - 1) == INVALID
+    assert call(wsp=FAKE + 16) == INVALID
+    assert call(pose=0) == INVALID
+    assert call(dmap=FAKE + 4) == INVALID
