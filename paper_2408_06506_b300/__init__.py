@@ -32,6 +32,7 @@ DEVERR_BAD_SENSOR_ID = 0x2
 DEVERR_TIMEOUT = 0x4
 MAX_SDF = 64
 MAX_SENSOR = 16
+MAX_TAXELS = 65536
 
 
 class TacslError(RuntimeError):

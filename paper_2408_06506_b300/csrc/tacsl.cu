@@ -283,8 +283,7 @@ int check_camera(const tacsl_camera* cam, CameraArgs& c) {
 }
 
 int launch_render(const SdfTable& tab, int64_t B, int P, const int32_t* obj_id, const float* pad_pose,
-                  const CameraArgs& c, float* depth_map, const DevInfo& dev, tacsl_stream_t stream) {
-    (void)dev;
+                  const CameraArgs& c, float* depth_map, const DevInfo& /*dev*/, tacsl_stream_t stream) {
     const int64_t tiles = (int64_t)((c.W + 31) / 32) * ((c.H + 7) / 8);
     if (tiles > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "camera image too large");
     // each block loops over images: about (tiles x 64) blocks in all, whatever the batch

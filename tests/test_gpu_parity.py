@@ -114,6 +114,17 @@ def test_penalty_forces_objects(orc, T_shape):
     _check_forces(sc, _oracle_forces(orc, sc), depth, fn, ft, wr)
 
 
+def test_penalty_forces_largest_pad(orc):
+    """T = 65536 taxels, the library's limit per pad (256 x 256 at 0.1 mm pitch)."""
+    sc = synth.scene_objects(seed=9, E=2, P=1, ny=256, nx=256, pitch=0.1e-3, n=64, depth_maps="none")
+    assert sc.T == tacsl.MAX_TAXELS
+    d = scene_to_device(sc)
+    depth, fn, ft, wr = tacsl.penalty_forces(d["sdfs"], d["params"], d["taxels"], d["obj_id"], d["pose"], d["twist"])
+    ref = _oracle_forces(orc, sc)
+    assert (ref["depth"] > 0).sum() > 100
+    _check_forces(sc, ref, depth, fn, ft, wr)
+
+
 def test_penalty_forces_bad_obj_id(orc):
     sc = synth.scene_objects(seed=5, E=8, P=2, n=48, depth_maps="none")
     ids = sc.obj_id.copy()
@@ -190,6 +201,8 @@ def _shade_case(orc, B, H, W, S, seed, sensor_id=None, rgb_offset=0):
     (11, 6, 4, 2),         # minimum width
     (3, 480, 640, 2),      # largest configured image (many tiles, wide halo)
     (1200, 8, 16, 1),      # more images than one run holds
+    (2, 6, 4096, 1),       # widest image the shared-memory ring takes (2 stages)
+    (1, 2048, 8, 1),       # tall and narrow: a tile spans many rows
 ])
 def test_shade_image_parity(orc, B, H, W, S):
     rgb, ref_rgb, ref_I, bad = _shade_case(orc, B, H, W, S, seed=B * 31 + H)
