@@ -15,7 +15,7 @@ from paper_2408_06506_b300 import autograd as ta
 from paper_2408_06506_b300 import synth
 
 from gpu_common import dev
-from grad_common import calibration_scene, upstream
+from grad_common import calibration_scene, safe_taxels, upstream
 
 pytestmark = pytest.mark.gpu
 RTOL = 1e-3
@@ -184,3 +184,35 @@ def test_calibration_step_reduces_the_loss():
         opt.step()
         losses.append(float(loss.detach()))
     assert losses[-1] < 0.2 * losses[0]
+
+
+def test_force_adjoint_full_calibration_size_sampled():
+    """1024 envs x 2 pads x 20x25 taxels against eight 128^3 grids (the calibration
+    workload), in the bench's launch; the oracle gradient on 48 sampled pads."""
+    sc = synth.scene_objects(seed=2, E=1024, P=2, depth_maps="none")
+    sc.k_d = np.random.default_rng(2).uniform(1.0, 5.0, size=sc.E).astype(np.float32)
+    rng = np.random.default_rng(7)
+    picks = rng.choice(sc.E * sc.P, 48, replace=False)
+    # upstream gradient on the sampled pads only (zero near kinks), zero elsewhere
+    gs = [np.zeros((sc.E, sc.P, sc.T), np.float32), np.zeros((sc.E, sc.P, sc.T, 3), np.float32),
+          np.zeros((sc.E, sc.P, sc.T, 3), np.float32), np.zeros((sc.E, sc.P, 6), np.float32)]
+    for b in picks:
+        e, p = divmod(int(b), sc.P)
+        m = safe_taxels(sc.grids[sc.obj_id[e]], sc.taxels, sc.pad_pose[e, p], sc.pad_twist[e, p], float(sc.k_n[e]),
+                        float(sc.k_d[e]), float(sc.k_t[e]), float(sc.mu[e]))
+        gs[0][e, p] = rng.normal(size=sc.T) * m * 1e3
+        gs[1][e, p] = rng.normal(size=(sc.T, 3)) * m[:, None]
+        gs[2][e, p] = rng.normal(size=(sc.T, 3)) * m[:, None]
+        if m.all():
+            gs[3][e, p] = rng.normal(size=6)
+    gp, gt, gk = _adjoint(sc, gs)
+    for b in picks:
+        e, p = divmod(int(b), sc.P)
+        one = [g[e:e + 1, p:p + 1] for g in gs]
+        prm = [np.array([v[e]], np.float32) for v in (sc.k_n, sc.k_d, sc.k_t, sc.mu)]
+        ref = G.force_gradients(sc.grids, sc.taxels, sc.obj_id[e:e + 1], sc.pad_pose[e:e + 1, p:p + 1],
+                                sc.pad_twist[e:e + 1, p:p + 1], *prm, *one)
+        scale = max(np.abs(ref["pose"]).max(), 1e-30)
+        assert np.abs(gp[e, p] - ref["pose"][0, 0]).max() <= RTOL * scale + 1e-9, (e, p)
+        scale = max(np.abs(ref["twist"]).max(), 1e-30)
+        assert np.abs(gt[e, p] - ref["twist"][0, 0]).max() <= RTOL * scale + 1e-9, (e, p)

@@ -12,9 +12,10 @@ import torch
 import paper_2408_06506_b300 as tacsl
 from paper_2408_06506_b300 import batch as tb
 from paper_2408_06506_b300 import serve as sv
+from paper_2408_06506_b300 import synth
 
 from batch_common import check_image, check_pad, oracle_pad, small_scene
-from gpu_common import dev
+from gpu_common import assert_forces_close, assert_rgb_close, dev
 
 pytestmark = pytest.mark.gpu
 TIMEOUT = 4
@@ -195,3 +196,43 @@ def test_bounded_waits_time_out_without_losing_work(scene):
     srv.close()                 # returns once every batch has finished
     assert _equal(out, ref)
     assert tacsl.check_errors() == 0
+
+
+def test_full_size_request_sampled(orc):
+    """A request of 2048 envs (the serving workload's largest) with uneven pads and
+    images up to 640x480, served next to small ones; sampled pads and images against the
+    oracle."""
+    w = synth.serve_workload(seed=9, n_templates=3, env_range=(2048, 2048), n_grid=8, grid_sides=(64, 128))
+    sdfs = tacsl.SdfSet.from_grids(w.grids)
+    sensors = tb.SensorSet([(dev(co), px, py) for co, px, py in w.models])
+    srv = sv.Server(sdfs, sensors, dev(w.taxels), w.layout_first, w.layout_count, hbm_budget_bytes=32 << 30,
+                    max_pads=1 << 16, n_streams=2)
+    keys = ("obj_id", "layout", "sensor", "pad_pose", "pad_twist", "k_n", "k_d", "k_t", "mu", "depth_map")
+    t = w.templates[0]
+    out = srv.outputs_for(t["layout"], t["sensor"])
+    rid = srv.submit(out=out, **{k: t[k] for k in keys})
+    assert srv.wait(rid)[0] == 0
+    srv.close()
+    T = w.layout_count[t["layout"]]
+    toff = np.concatenate([[0], np.cumsum(T)[:-1]])
+    hw = np.array([m[0].shape[2] * m[0].shape[3] for m in w.models])
+    px = np.where(t["sensor"] >= 0, hw[np.maximum(t["sensor"], 0)], 0)
+    poff = np.concatenate([[0], np.cumsum(px)[:-1]])
+    rng = np.random.default_rng(3)
+    for b in rng.choice(len(t["obj_id"]), 24, replace=False):
+        l = t["layout"][b]
+        tax = w.taxels[w.layout_first[l]:w.layout_first[l] + w.layout_count[l]]
+        ref = orc.penalty_forces(w.grids, tax, t["obj_id"][b:b + 1], t["pad_pose"][b][None, None],
+                                 t["pad_twist"][b][None, None], t["k_n"][b], t["k_d"][b], t["k_t"][b], t["mu"][b])
+        s0, n = int(toff[b]), int(T[b])
+        d = out["depth"][s0:s0 + n].numpy()
+        assert np.abs(d - ref["depth"][0, 0]).max() <= 1e-6
+        fl = 2e-8 * float(t["k_n"][b]) + 2e-7 * float(t["k_t"][b])
+        assert_forces_close(out["f_n"][s0:s0 + n].numpy()[None, None], ref["f_n"], "f_n", fl)
+        assert_forces_close(out["f_t"][s0:s0 + n].numpy()[None, None], ref["f_t"], "f_t", fl)
+        co, ppx, ppy = w.models[t["sensor"][b]]
+        H, W = co.shape[2], co.shape[3]
+        q = int(poff[b])
+        dm = t["depth_map"][q:q + H * W].reshape(1, H, W)
+        ref_rgb, ref_i, bad = orc.shade(co[None], ppx, ppy, [0], dm, with_intensity=True)
+        assert_rgb_close(out["rgb"][q:q + H * W].numpy().reshape(H, W, 3), ref_rgb[0], ref_i[0])
