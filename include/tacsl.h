@@ -14,7 +14,11 @@
  *     tacsl_shading) are HOST memory read during the call; the device pointers
  *     inside them are read by the kernels later, on the stream.
  *   - Calls enqueue work on `stream` (NULL = the legacy default stream) and return
- *     without synchronising.  They never allocate or free memory.
+ *     without synchronising (tacsl_check_errors, tacsl_batch_autotune and
+ *     tacsl_batch_graph_create do synchronise).  They never allocate or free device
+ *     memory: buffers and workspaces are the caller's.  The exceptions are the server
+ *     (tacsl_serve.h), which allocates one arena when it is created, and the CUDA streams
+ *     and events that tacsl_tactile_step_host creates on its first call on a device.
  *   - Arguments are checked on the host before anything is launched; on failure the
  *     call returns a nonzero status, launches nothing and writes no output, and
  *     tacsl_last_error() describes the problem.
@@ -240,7 +244,7 @@ int64_t tacsl_tactile_step_host_workspace(int32_t chunk_envs, int32_t P, int32_t
  * the host, and depth, f_n, f_t, wrench (may be NULL), rgb are written to the host, in
  * the layouts of tacsl_tactile_step; the SDFs, params, taxels and shading coefficients
  * stay on the device.  The envs go through in chunks of chunk_envs, pipelined on three
- * internal streams of this device: one chunk's inputs travel to the GPU while another
+ * internal streams of this device (created, with their events, on the first call there): one chunk's inputs travel to the GPU while another
  * chunk computes and a third's outputs travel back.  workspace: device memory of at least
  * tacsl_tactile_step_host_workspace(chunk_envs, P, T, H, W) bytes, 256-byte aligned.  The
  * call enqueues everything after the work already on `stream` and makes `stream` wait for
