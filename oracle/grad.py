@@ -27,10 +27,15 @@ interpolation cell, the intensity clamp) are taken on the values and carry no
 derivative, so a gradient is that of the piece the point lies in: meaningful away
 from the kinks between pieces, which the tests avoid.
 
+The depth maps of the column camera are differentiated w.r.t. the pad pose by the
+implicit function theorem at each column's first hit (render_gradients, reading c17).
+
 Pinned by tests/test_oracle_grad_pins.py: the forward equals the C oracle's, the
-gradients equal float64 central differences of the C oracle (h = 1e-6), and closed
-forms (d f_n / d k_n = depth n; stick and slip derivatives; a half-space whose field is
-exactly linear; d I / d A_k = m_k; the flat-gel derivative of I w.r.t. the depth).
+gradients equal float64 central differences of the C oracle (h = 1e-6; h = 1e-5 for the
+depth maps, whose hit search stops at voxel/65536), and closed forms (d f_n / d k_n =
+depth n; stick and slip derivatives; a half-space whose field is exactly linear, for the
+forces and for the depth maps; d I / d A_k = m_k; the flat-gel derivative of I w.r.t.
+the depth).
 """
 from __future__ import annotations
 
@@ -230,3 +235,74 @@ def shade_gradients(coeffs, pitch_x, pitch_y, sensor_id, depth, g_intensity):
         g_depth[b] = D.grad.numpy()
         inten[b] = I.detach().numpy()
     return {"coeffs": A.grad.numpy(), "depth": g_depth, "intensity": inten}
+
+
+
+GRAZING = 0.05   # |d phi / dz| below this: a grazing column, whose depth gradient is left out
+
+
+def render_gradients(grids, obj_id, pad_pose, H, W, pitch_x, pitch_y, x0, y0, d0, z_max, g_depth, depth=None):
+    """Gradient of L = sum(g_depth * D) w.r.t. the pad poses [E, P, 7], D [E, P, H, W] the
+    depth maps of the column camera (the C oracle's render_depth, Sec. III-B).
+
+    A column that meets the object at z_hit in (-z_max, 0) has D = d0 + z_hit, where z_hit
+    solves phi(R p + t) = 0 for the pad-frame point p = (x_i, y_j, z_hit).  By the implicit
+    function theorem d z_hit = -(d phi) / (d phi / dz) at the hit, with d phi / dz =
+    grad phi . R e_z (reading c17); phi is the trilinear interpolant and its derivatives
+    are taken by autograd at the hit point.  The columns are classified on the float32
+    value of D, the precision of the maps the library carries: D >= d0 (no hit) and
+    D <= d0 - z_max (the object reaches below the camera's range and D is clamped) carry
+    no derivative, and neither do grazing columns (|d phi / dz| < GRAZING) nor hit points
+    outside the grid's domain.
+
+    depth: the maps whose hit points are differentiated (default: the C oracle's render).
+    Returns dict pose [E, P, 7] (NaN for an env with a bad obj_id), depth [E, P, H, W] and
+    phi_z [E, P, H, W] (d phi / dz at each differentiated column, NaN elsewhere)."""
+    import oracle as orc_c
+    pad_pose = np.asarray(pad_pose, np.float32)
+    E, P = pad_pose.shape[0], pad_pose.shape[1]
+    obj_id = np.asarray(obj_id).reshape(-1)
+    if depth is None:
+        depth, _ = orc_c.render_depth(grids, obj_id, pad_pose, H, W, pitch_x, pitch_y, x0, y0, d0, z_max)
+    depth = np.asarray(depth, np.float64).reshape(E, P, H, W)
+    f32 = np.float32
+    d0f, zf = float(f32(d0)), float(f32(z_max))
+    top, bottom = f32(d0f), f32(f32(d0f) - f32(zf))
+    xs = float(f32(x0)) + np.arange(W) * float(f32(pitch_x))
+    ys = float(f32(y0)) + np.arange(H) * float(f32(pitch_y))
+    yy, xx = np.meshgrid(ys, xs, indexing="ij")
+    gd = np.asarray(g_depth, np.float64).reshape(E, P, H, W)
+    out = np.zeros((E, P, 7))
+    phi_z_map = np.full((E, P, H, W), np.nan)
+    cache = {}
+    for e in range(E):
+        oid = int(obj_id[e])
+        if oid < 0 or oid >= len(grids):
+            out[e] = np.nan
+            continue
+        if oid not in cache:
+            cache[oid] = grid_tensors(grids[oid])
+        grid = cache[oid]
+        for p in range(P):
+            D = depth[e, p]
+            D32 = D.astype(f32)
+            hit = (D32 < top) & (D32 > bottom)
+            if not hit.any():
+                continue
+            pose = _t(pad_pose[e, p].astype(np.float64), True)
+            R = rotation(pose[3:7])
+            z = torch.tensor(D[hit] - d0f, dtype=F64, requires_grad=True)
+            pts = torch.stack([torch.tensor(xx[hit], dtype=F64), torch.tensor(yy[hit], dtype=F64), z], dim=1)
+            x = pts @ R.T + pose[0:3]
+            phi, _, inside = sdf_eval(grid, x)
+            (phi_z,) = torch.autograd.grad(phi.sum(), z, retain_graph=True)
+            keep = inside & (phi_z.abs() >= GRAZING)
+            pz = phi_z.detach()
+            dz = -phi / torch.where(keep, pz, torch.ones_like(pz))
+            L = (torch.tensor(gd[e, p][hit], dtype=F64) * keep * dz).sum()
+            L.backward()
+            out[e, p] = pose.grad.numpy()
+            pzm = np.full(int(hit.sum()), np.nan)
+            pzm[keep.numpy()] = pz.numpy()[keep.numpy()]
+            phi_z_map[e, p][hit] = pzm
+    return {"pose": out, "depth": depth, "phi_z": phi_z_map}

@@ -6,6 +6,9 @@ lets autograd differentiate them.  It is pinned to things other than itself:
   * its gradients equal float64 central differences of the C oracle, h = 1e-6 (Sec. III-C
     force law; the differentiated step of the calibration workload), on pads whose
     taxels all lie away from kinks;
+  * the depth maps' gradient w.r.t. the pad pose equals central differences of the C
+    oracle's render (t: h = 1e-5, q: h = 1e-3) and, for a tilted half-space, the closed
+    form d D/d t = -n / (n . R e_z); grazing columns carry none;
   * closed forms: d f_n/d k_n = depth n; in stick d f_t/d k_t = f_t/k_t and in slip
     d f_t/d mu = f_t/mu; a half-space whose SDF is exactly linear; d I/d A_k = m_k; on an
     undeformed gel d I(q)/d D(q +- 1) = +-A_1(q)/(2 pitch_x), d I(q)/d D(q +- W) =
@@ -276,9 +279,133 @@ def check_shading_closed_forms(G):
     assert np.abs(gd - want).max() <= 1e-9 * np.abs(want).max()
 
 
+# ---------------------------------------------------------------------------
+# depth maps w.r.t. the pad pose (implicit function theorem at each column's hit)
+# ---------------------------------------------------------------------------
+
+CAM = dict(H=9, W=11, pitch_x=0.5e-3, pitch_y=0.5e-3, d0=0.02, z_max=3e-3)
+
+
+def _cam(H, W, pitch_x, pitch_y, d0, z_max):
+    return dict(H=H, W=W, pitch_x=pitch_x, pitch_y=pitch_y, x0=-(W - 1) / 2 * pitch_x, y0=-(H - 1) / 2 * pitch_y,
+                d0=d0, z_max=z_max)
+
+
+def _columns(c):
+    """float64 pad-frame (x, y) of every pixel, as the float32 camera defines them."""
+    f = np.float32
+    xs = float(f(c["x0"])) + np.arange(c["W"]) * float(f(c["pitch_x"]))
+    ys = float(f(c["y0"])) + np.arange(c["H"]) * float(f(c["pitch_y"]))
+    return np.meshgrid(ys, xs, indexing="ij")[::-1]
+
+
+def _quat_rot(q):
+    q = np.asarray(q, np.float64)
+    return synth.quat_to_matrix(q / np.linalg.norm(q))
+
+
+def _half_space(nrm, n=64, h=0.5e-3):
+    """phi(x) = nrm . x baked on a grid centred at the origin: trilinear interpolation is
+    exact for a linear field, so the column's hit is z = -nrm.(R p0 + t) / (nrm . R e_z)."""
+    nrm = np.asarray(nrm, np.float64) / np.linalg.norm(nrm)
+    return synth.bake_field(lambda x, y, z: nrm[0] * x + nrm[1] * y + nrm[2] * z, (n, n, n), h,
+                            [-(n - 1) * h / 2] * 3), nrm
+
+
+def _z_closed(nrm, pose, xx, yy):
+    R = _quat_rot(pose[3:7])
+    p0 = np.stack([xx, yy, np.zeros_like(xx)], -1) @ R.T + np.asarray(pose[:3], np.float64)
+    return -(p0 @ nrm) / (nrm @ R[:, 2])
+
+
+def check_render_tilted_half_space(G):
+    """Closed form of d D / d pose for a half-space tilted against the pad (every column
+    hits it): d D / d t = -nrm / (nrm . R e_z) per column; d D / d q is the central
+    difference (float64, h = 1e-7) of the closed-form hit depth itself."""
+    grid, nrm = _half_space([0.3, -0.2, 1.0])
+    q = synth.quat_multiply(synth.quat_multiply([0.0, 1.0, 0.0, 0.0], synth.quat_from_axis_angle([1.0, 0.5, 0.0], 0.1)),
+                            synth.quat_from_axis_angle([0.0, 0.0, 1.0], 0.7))
+    R = _quat_rot(q)
+    pose = np.concatenate([-1.5e-3 * nrm + R @ np.array([0.3e-3, -0.2e-3, 0.0]), q]).astype(np.float32)
+    c = _cam(**CAM)
+    xx, yy = _columns(c)
+    zc = _z_closed(nrm, pose.astype(np.float64), xx, yy)
+    assert zc.max() < -1e-4 and zc.min() > -c["z_max"] + 1e-4       # every column hits inside the range
+    rng = np.random.default_rng(8)
+    g = rng.uniform(0.5, 1.5, size=(1, 1, c["H"], c["W"]))
+    r = G.render_gradients([grid], [0], pose[None, None], g_depth=g, **c)
+    got = r["pose"][0, 0]
+    nd = nrm @ _quat_rot(pose[3:7].astype(np.float64))[:, 2]
+    want_t = -g.sum() * nrm / nd
+    assert np.abs(got[:3] - want_t).max() <= 1e-9 * np.abs(want_t).max()
+    want_q = np.zeros(4)
+    for j in range(4):
+        pp, pm = pose.astype(np.float64), pose.astype(np.float64)
+        pp[3 + j] += 1e-7
+        pm[3 + j] -= 1e-7
+        want_q[j] = np.sum(g[0, 0] * (_z_closed(nrm, pp, xx, yy) - _z_closed(nrm, pm, xx, yy))) / 2e-7
+    # the march resolves each hit to voxel * 2^-16, which moves p_z (and so d D / d q) by as much
+    assert np.abs(got[3:] - want_q).max() <= 1e-5 * np.abs(want_q).max()
+    assert np.abs(want_q).min() > 1e-3 * np.abs(want_q).max()        # every quaternion component is exercised
+    # grazing columns carry no derivative: the same half-space nearly along the column
+    # (|d phi / dz| = 0.04) gives an exactly zero gradient although the columns hit
+    q2 = synth.quat_multiply([0.0, 1.0, 0.0, 0.0], synth.quat_from_axis_angle([1.0, 0.0, 0.0], np.arccos(0.04)))
+    grid2, _ = _half_space([0.0, 0.0, 1.0])
+    pose2 = np.concatenate([[0.0, 0.0, -0.5e-3], q2]).astype(np.float32)
+    r2 = G.render_gradients([grid2], [0], pose2[None, None], g_depth=g, **c)
+    D2 = r2["depth"][0, 0]
+    assert ((D2 < np.float32(0.02)) & (D2 > np.float32(0.02 - 3e-3))).sum() >= 5
+    assert not r2["pose"].any()
+
+
+def check_render_central_differences(G):
+    """d(sum g D)/d pose against central differences of the C oracle's render (t: h = 1e-5 m,
+    q: h = 1e-3) on a sphere under a tilted pad, over columns whose hit points stay away
+    from interpolation cell faces by more than a step moves them.  Each rendered hit lies
+    within voxel * 2^-16 above the root, so a difference errs by at most
+    sum|g| voxel 2^-16 / (2 h) beyond its O(h^2) term."""
+    Rs, h = 5e-3, 0.5e-3
+    shape = synth.Shape("sphere", (Rs,))
+    grid = synth.bake(shape, 32, h)
+    q = synth.quat_multiply(synth.quat_from_axis_angle([0.3, 1.0, 0.0], 0.5), synth.quat_from_axis_angle([0, 0, 1], 1.1))
+    pose = synth.place_pad(shape, q, 1.6e-3, (0.3e-3, -0.4e-3)).astype(np.float32)
+    c = _cam(H=15, W=17, pitch_x=0.4e-3, pitch_y=0.4e-3, d0=0.02, z_max=3e-3)
+    D, _ = oracle.render_depth([grid], [0], pose[None, None], **c)
+    xx, yy = _columns(c)
+    z = D[0, 0] - float(np.float32(c["d0"]))
+    R = _quat_rot(pose[3:7])
+    sel = np.zeros(z.shape, bool)
+    for j in range(c["H"]):
+        for i in range(c["W"]):
+            if not (-c["z_max"] + 2e-4 < z[j, i] < -2e-4):
+                continue
+            x = R @ np.array([xx[j, i], yy[j, i], z[j, i]]) + pose[:3].astype(np.float64)
+            u = (x - np.asarray(grid.origin, np.float64)) / grid.voxel
+            if np.any(np.abs(u - np.rint(u)) < 0.12):
+                continue
+            dz = 1e-6
+            pz = (oracle.column_phi(grid, pose, xx[j, i], yy[j, i], z[j, i] + dz) -
+                  oracle.column_phi(grid, pose, xx[j, i], yy[j, i], z[j, i] - dz)) / (2 * dz)
+            sel[j, i] = abs(pz) > 0.3
+    assert sel.sum() >= 25, sel.sum()
+    rng = np.random.default_rng(12)
+    g = np.where(sel, rng.uniform(0.5, 1.5, size=sel.shape), 0.0)
+    got = G.render_gradients([grid], [0], pose[None, None], g_depth=g[None, None], **c)["pose"][0, 0]
+
+    def L(pz):
+        return float(np.sum(g * oracle.render_depth([grid], [0], pz[None, None], **c)[0][0, 0]))
+
+    eps = grid.voxel / 65536
+    for j in range(7):
+        hh = 1e-5 if j < 3 else 1e-3
+        fd = _fd(L, pose, j, hh)
+        tol = 1.2 * g.sum() * eps / (2 * hh) + 2e-3 * abs(got[j]) + 1e-9
+        assert abs(got[j] - fd) <= tol, (j, got[j], fd, tol)
+
+
 CHECKS = [check_forward_matches_c_oracle, check_intensity_matches_c_oracle,
           check_force_gradients_match_central_differences, check_closed_forms_kn_kt_mu, check_half_space,
-          check_shading_closed_forms]
+          check_shading_closed_forms, check_render_tilted_half_space, check_render_central_differences]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=[c.__name__ for c in CHECKS])
@@ -300,6 +427,11 @@ MUTATIONS = {
     "friction_cap_max": ("torch.where(cap.detach() < lim.detach(), cap, lim)",
                          "torch.where(cap.detach() > lim.detach(), cap, lim)"),
     "intensity_unclamped": ("return torch.clamp(I, 0.0, 255.0).permute(1, 2, 0)", "return I.permute(1, 2, 0)"),
+    "render_implicit_sign": ("dz = -phi / torch.where(", "dz = phi / torch.where("),
+    "render_pose_transposed": ("x = pts @ R.T + pose[0:3]", "x = pts @ R + pose[0:3]"),
+    "render_pixel_axes": ("torch.stack([torch.tensor(xx[hit], dtype=F64), torch.tensor(yy[hit], dtype=F64), z]",
+                          "torch.stack([torch.tensor(yy[hit], dtype=F64), torch.tensor(xx[hit], dtype=F64), z]"),
+    "render_grazing_kept": ("keep = inside & (phi_z.abs() >= GRAZING)", "keep = inside & (phi_z.abs() >= 0.0)"),
     "monomial_swap": ("m = torch.stack([torch.ones_like(nx), nx, ny, nx * nx, ny * ny, nx * ny])",
                       "m = torch.stack([torch.ones_like(nx), ny, nx, nx * nx, ny * ny, nx * ny])"),
 }
