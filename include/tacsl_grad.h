@@ -8,7 +8,8 @@
  * give the gradients such a fit needs, computed by hand-written adjoint kernels:
  *   - of the force field and wrenches (Sec. III-C) w.r.t. each pad's pose and twist and
  *     the contact parameters k_n, k_d, k_t, mu;
- *   - of the image w.r.t. the per-pixel shading coefficients and the depth maps.
+ *   - of the image w.r.t. the per-pixel shading coefficients and the depth maps;
+ *   - of the rendered depth maps w.r.t. each pad's pose.
  * The differentiable image is the clamped intensity clamp(sum_k A_k m_k, 0, 255), the
  * continuous quantity the uint8 image rounds.  Gradients are those of the smooth piece
  * a point lies in: contact on/off, the unilateral clamp, stick/slip, the interpolation
@@ -53,6 +54,22 @@ int tacsl_shade_intensity(const tacsl_shading* shading, int64_t B, const int32_t
 int tacsl_shade_adjoint(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id,
                         const float* depth_map, const float* g_intensity, float* grad_coeffs,
                         float* grad_depth, tacsl_stream_t stream);
+
+/* Adjoint of tacsl_render_depth w.r.t. the pad poses (the pose -> depth -> image chain;
+ * same set, E, P, obj_id, pad_pose, camera).  depth_map [E*P][H][W] (device) is the
+ * render of these poses and g_depth [E*P][H][W] (device) the upstream gradient; grad_pose
+ * [E*P][7] (device, overwritten) receives dL/dt and dL/dq for the raw quaternion, as
+ * tacsl_penalty_forces_adjoint gives them.  A column that hits the object at z_hit in
+ * (-z_max, 0) has D = d0 + z_hit with phi(R p + t) = 0, p = (x_i, y_j, z_hit), so (implicit
+ * function theorem) dD = -(grad phi . (dR p + dt)) / (grad phi . R e_z), grad phi the
+ * analytic gradient of the trilinear interpolant at the hit.  Columns are classed on D:
+ * D >= d0 (miss), D <= d0 - z_max (clamped at the bottom of the range), grazing columns
+ * (|grad phi . R e_z| < 0.05) and hits outside the grid's domain carry no derivative.
+ * Each pad's sums are reduced in a fixed order (bitwise reproducible).  A bad obj_id
+ * gives NaN for its pads and sets TACSL_DEVERR_BAD_OBJ_ID. */
+int tacsl_render_depth_adjoint(const tacsl_sdf_set* set, int32_t E, int32_t P, const int32_t* obj_id,
+                               const float* pad_pose, const tacsl_camera* camera, const float* depth_map,
+                               const float* g_depth, float* grad_pose, tacsl_stream_t stream);
 
 #ifdef __cplusplus
 }

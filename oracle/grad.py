@@ -257,7 +257,8 @@ def render_gradients(grids, obj_id, pad_pose, H, W, pitch_x, pitch_y, x0, y0, d0
 
     depth: the maps whose hit points are differentiated (default: the C oracle's render).
     Returns dict pose [E, P, 7] (NaN for an env with a bad obj_id), depth [E, P, H, W] and
-    phi_z [E, P, H, W] (d phi / dz at each differentiated column, NaN elsewhere)."""
+    phi_z [E, P, H, W] (d phi / dz at each column whose hit lies in the grid's domain,
+    grazing or not; NaN elsewhere)."""
     import oracle as orc_c
     pad_pose = np.asarray(pad_pose, np.float32)
     E, P = pad_pose.shape[0], pad_pose.shape[1]
@@ -302,7 +303,6 @@ def render_gradients(grids, obj_id, pad_pose, H, W, pitch_x, pitch_y, x0, y0, d0
             L = (torch.tensor(gd[e, p][hit], dtype=F64) * keep * dz).sum()
             L.backward()
             out[e, p] = pose.grad.numpy()
-            pzm = np.full(int(hit.sum()), np.nan)
-            pzm[keep.numpy()] = pz.numpy()[keep.numpy()]
+            pzm = np.where(inside.numpy(), pz.numpy(), np.nan)
             phi_z_map[e, p][hit] = pzm
     return {"pose": out, "depth": depth, "phi_z": phi_z_map}

@@ -1,10 +1,11 @@
 """torch.autograd bindings of the tactile step's adjoint kernels (``include/tacsl_grad.h``).
 
-``force_field`` and ``shade_intensity`` behave like differentiable torch functions:
+``force_field``, ``shade_intensity`` and ``render_depth`` behave like differentiable torch
+functions:
 their forward runs the library's forward kernels and their backward the hand-written
 adjoint kernels, so a calibration loss over force fields, wrenches and images can be
 minimised with any torch optimiser over pad poses, twists, contact parameters and
-shading coefficients.  Argument marshalling only; every step runs in ``libtacsl.so``.
+shading coefficients; with ``render_depth`` the images depend on the pad poses too.  Argument marshalling only; every step runs in ``libtacsl.so``.
 """
 from __future__ import annotations
 
@@ -12,8 +13,9 @@ import ctypes as C
 
 import torch
 
-from . import (ContactParams, SdfSet, Shading, _check, _dev, _Params, _ptr, _SdfSet, _Shading, _stream, load,
-               penalty_forces)
+from . import (Camera, ContactParams, SdfSet, Shading, _Camera, _check, _dev, _Params, _ptr, _SdfSet, _Shading,
+               _stream, load, penalty_forces)
+from . import render_depth as _render_forward
 
 _bound = False
 
@@ -30,6 +32,8 @@ def _lib():
         lib.tacsl_shade_intensity.argtypes = [C.POINTER(_Shading), I64, P, P, P, P]
         lib.tacsl_shade_adjoint.restype = C.c_int
         lib.tacsl_shade_adjoint.argtypes = [C.POINTER(_Shading), I64, P, P, P, P, P, P]
+        lib.tacsl_render_depth_adjoint.restype = C.c_int
+        lib.tacsl_render_depth_adjoint.argtypes = [C.POINTER(_SdfSet), I32, I32, P, P, C.POINTER(_Camera), P, P, P, P]
         _bound = True
     return lib
 
@@ -113,3 +117,41 @@ def shade_intensity(coeffs, depth_map, sensor_id, pitch_x, pitch_y):
     _dev(depth_map.detach(), torch.float32, "depth_map")
     _dev(sensor_id, torch.int32, "sensor_id")
     return _ShadeIntensity.apply(coeffs, depth_map, sensor_id, float(pitch_x), float(pitch_y))
+
+
+def render_depth_adjoint(sdfs: SdfSet, camera: Camera, obj_id, pad_pose, depth_map, g_depth, grad_pose=None,
+                         stream=None):
+    """dL/d pad_pose [E, P, 7] of L = sum(g_depth * depth_map), depth_map [E, P, H, W] the
+    render of pad_pose (``tacsl_render_depth_adjoint``)."""
+    _dev(obj_id, torch.int32, "obj_id")
+    _dev(pad_pose, torch.float32, "pad_pose")
+    _dev(depth_map, torch.float32, "depth_map")
+    _dev(g_depth, torch.float32, "g_depth")
+    E, P = pad_pose.shape[0], pad_pose.shape[1]
+    if grad_pose is None:
+        grad_pose = torch.empty(E, P, 7, dtype=torch.float32, device=pad_pose.device)
+    _check(_lib().tacsl_render_depth_adjoint(C.byref(sdfs.c), E, P, _ptr(obj_id), _ptr(pad_pose), C.byref(camera.c),
+                                             _ptr(depth_map), _ptr(g_depth), _ptr(grad_pose), _stream(stream)))
+    return grad_pose
+
+
+class _RenderDepth(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, pose, sdfs, camera, obj_id):
+        depth = _render_forward(sdfs, camera, obj_id, pose.detach())
+        ctx.save_for_backward(pose, depth)
+        ctx.sdfs, ctx.camera, ctx.obj_id = sdfs, camera, obj_id
+        return depth
+
+    @staticmethod
+    def backward(ctx, g):
+        pose, depth = ctx.saved_tensors
+        grad_pose = render_depth_adjoint(ctx.sdfs, ctx.camera, ctx.obj_id, pose.detach(), depth, g.contiguous())
+        return grad_pose, None, None, None
+
+
+def render_depth(sdfs: SdfSet, camera: Camera, obj_id, pose):
+    """Differentiable depth maps [E, P, H, W] of the column camera (as the library's
+    ``render_depth``); gradients flow to pose [E, P, 7]."""
+    _dev(pose.detach(), torch.float32, "pose")
+    return _RenderDepth.apply(pose, sdfs, camera, obj_id)

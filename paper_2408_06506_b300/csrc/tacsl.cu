@@ -19,6 +19,7 @@
 #include "batch.cuh"
 #include "common.cuh"
 #include "render.cuh"
+#include "render_adjoint.cuh"
 #include "shade.cuh"
 #include "taxel.cuh"
 #include "tacsl_batch.h"
@@ -1264,6 +1265,52 @@ int tacsl_shade_adjoint(const tacsl_shading* shading, int64_t B, const int32_t* 
         if ((rc = check_launch("tacsl_shade_adjoint (depth)"))) return rc;
     }
     return ok();
+}
+
+int tacsl_render_depth_adjoint(const tacsl_sdf_set* set, int32_t E, int32_t P, const int32_t* obj_id,
+                               const float* pad_pose, const tacsl_camera* camera, const float* depth_map,
+                               const float* g_depth, float* grad_pose, tacsl_stream_t stream) {
+    SdfTable tab;
+    int rc = build_table(set, tab);
+    if (rc) return rc;
+    CameraArgs c;
+    if ((rc = check_camera(camera, c))) return rc;
+    if (E < 0 || P < 0) return fail(TACSL_ERR_INVALID_ARG, "negative size (E=%d P=%d)", E, P);
+    const int64_t B = (int64_t)E * P;
+    if (B == 0) return ok();
+    if (obj_id == nullptr || !aligned(obj_id, 4) || pad_pose == nullptr || !aligned(pad_pose, 4))
+        return fail(TACSL_ERR_INVALID_ARG, "obj_id and pad_pose must be non-NULL and 4-byte aligned");
+    if (depth_map == nullptr || !aligned(depth_map, 4) || g_depth == nullptr || !aligned(g_depth, 4) ||
+        grad_pose == nullptr || !aligned(grad_pose, 4))
+        return fail(TACSL_ERR_INVALID_ARG, "depth_map, g_depth and grad_pose must be non-NULL and 4-byte aligned");
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    // CTAs per pad: one when the batch alone gives every SM a few CTAs, else up to a
+    // cluster of 8, each CTA keeping at least 2048 pixels
+    const int64_t HW = (int64_t)c.H * c.W;
+    const int64_t want = 4 * (int64_t)dev->sms;
+    int C = 1;
+    if (B < want) {
+        const int64_t by_batch = (want + B - 1) / B, by_pixels = std::max<int64_t>(1, HW / 2048);
+        C = (int)std::min<int64_t>({(int64_t)kRenderAdjMaxCluster, by_batch, by_pixels});
+    }
+    if (B * C > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "E*P = %lld pads in one call", (long long)B);
+    RenderAdjointArgs A{tab, B, P, C, obj_id, pad_pose, c, depth_map, g_depth, grad_pose};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(B * C));
+    cfg.blockDim = dim3(kRenderAdjThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(C);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, render_adjoint_kernel, A);
+    if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "render adjoint launch: %s", cudaGetErrorString(e));
+    return check_launch("render adjoint kernel");
 }
 
 }  // extern "C"

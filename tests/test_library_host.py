@@ -224,6 +224,21 @@ def test_render_depth_rejects_pointers(lib):
     assert lib.tacsl_render_depth(C.byref(st), 0, 2, FAKE, FAKE, C.byref(cam), FAKE, None) == 0
 
 
+def test_render_adjoint_rejects(lib):
+    from paper_2408_06506_b300 import autograd as ta
+    f = ta._lib().tacsl_render_depth_adjoint
+    st, cam = _set(_sdf()), _camera()
+    assert f(C.byref(st), 2, 2, FAKE, FAKE, C.byref(_camera(W=18)), FAKE, FAKE, FAKE, None) == INVALID
+    assert f(C.byref(st), 2, 2, FAKE, FAKE, None, FAKE, FAKE, FAKE, None) == INVALID
+    assert f(C.byref(st), -1, 2, FAKE, FAKE, C.byref(cam), FAKE, FAKE, FAKE, None) == INVALID
+    for k in range(5):         # obj_id, pad_pose, depth_map, g_depth, grad_pose: NULL or misaligned
+        for bad in (0, FAKE + 2):
+            args = [FAKE] * 5
+            args[k] = bad
+            assert f(C.byref(st), 2, 2, args[0], args[1], C.byref(cam), *args[2:], None) == INVALID, (k, bad)
+    assert f(C.byref(st), 0, 2, FAKE, FAKE, C.byref(cam), FAKE, FAKE, FAKE, None) == 0
+
+
 def test_render_step_requires_matching_camera(lib):
     st, prm, cam = _set(_sdf()), _params(), _camera(H=8, W=16)
     sh = _shading(H=12, W=16)
