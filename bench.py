@@ -748,6 +748,34 @@ def run_grad(args, rank, world, local_rank, dist):
     if dist is not None:
         dist.barrier()
     ms = max_over_ranks(timed(step, K, warm=0), dist, device="cuda")
+    # the pose -> image chain: the images rendered from the poses (column camera) instead
+    # of given depth maps, against the images of poses perturbed by 0.2 mm / 0.01 rad
+    from paper_2408_06506_b300 import synth
+    cam = tacsl.Camera(sc.H, sc.W, sc.pitch_x, sc.pitch_y, -sc.pitch_x * sc.W / 2 + 0.5 * sc.pitch_x,
+                       -sc.pitch_y * sc.H / 2 + 0.5 * sc.pitch_y, synth.D0, 3e-3)
+    with torch.no_grad():
+        tpose = sc.pad_pose.copy()
+        tpose[..., :3] += g.normal(0, 2e-4, size=tpose[..., :3].shape)
+        tpose[..., 3:] += g.normal(0, 5e-3, size=tpose[..., 3:].shape)
+        tI_pose = ta.shade_intensity(tco, tacsl.render_depth(sdfs, cam, obj, dev(tpose.astype(np.float32))),
+                                     sid, sc.pitch_x, sc.pitch_y)
+
+    def pose_step():
+        for t in leaves:
+            t.grad = None
+        _, fn, ft, _ = ta.force_field(sdfs, taxels, obj, pose, twist, *ks)
+        D = ta.render_depth(sdfs, cam, obj, pose)
+        I = ta.shade_intensity(coeffs, D.reshape(-1, sc.H, sc.W), sid, sc.pitch_x, sc.pitch_y)
+        loss = ((fn - tgt[1]) ** 2).mean() + ((ft - tgt[2]) ** 2).mean() + 1e-4 * ((I - tI_pose) ** 2).mean()
+        loss.backward()
+
+    for _ in range(3):
+        pose_step()
+    torch.cuda.synchronize()
+    assert tacsl.check_errors() == 0 and torch.isfinite(pose.grad).all()
+    if dist is not None:
+        dist.barrier()
+    ms_pose = max_over_ranks(timed(pose_step, K, warm=0), dist, device="cuda")
     # the kernels alone: forward force field and intensity, and their adjoints for fixed
     # upstream gradients
     params = tacsl.ContactParams(*[k.detach() for k in ks])
@@ -775,6 +803,13 @@ def run_grad(args, rank, world, local_rank, dist):
             C.byref(shading.c), E * P, tacsl._ptr(sid), tacsl._ptr(depth_map), tacsl._ptr(gI), tacsl._ptr(gc), None,
             None), 5),
     }
+    del gI
+    rendered = tacsl.render_depth(sdfs, cam, obj, pz)
+    gD = torch.randn(E, P, sc.H, sc.W, device="cuda")
+    k_ms["render_kernel"] = timed(lambda: tacsl.render_depth(sdfs, cam, obj, pz, depth_map=rendered), 10)
+    n_hit = int(((rendered < np.float32(synth.D0)) & (rendered > np.float32(synth.D0) - np.float32(3e-3))).sum())
+    k_ms["render_adjoint_kernel"] = timed(
+        lambda: ta.render_depth_adjoint(sdfs, cam, obj, pz, rendered, gD, grad_pose=gp), 20)
     assert tacsl.check_errors() == 0
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak = float(json.load(open(peaks_path))["hbm_gbs"]) if os.path.exists(peaks_path) else 6400.0
@@ -785,17 +820,27 @@ def run_grad(args, rank, world, local_rank, dist):
     # the coefficient gradient once
     inten_bytes = 16 * npx + coef_bytes
     cgrad_bytes = 16 * npx + 2 * coef_bytes
+    # the render adjoint reads the depth map (4 B/px), the upstream gradient at hit
+    # columns (4 B per hit), each pad's pose, and writes its gradient (56 B/pad); the SDF
+    # cells of hit columns come from L2 (the grids are resident) and are not counted
+    radj_bytes = 4 * npx + 4 * n_hit + 56 * E * P
     return {
         "workload": GRAD_WORKLOAD, "envs_per_gpu": E, "steps": K,
         "ms_per_step": ms, "unit": "taxel-points/s", "value": world * E * P * T / (ms * 1e-3),
         "images_per_s": world * E * P / (ms * 1e-3),
         "path": "force_field + shade_intensity (torch.autograd.Function over the C ABI), MSE in torch, backward",
+        "pose_chain": {"ms_per_step": ms_pose, "value": world * E * P * T / (ms_pose * 1e-3),
+                       "images_per_s": world * E * P / (ms_pose * 1e-3), "gpu_launches_per_step": 7,
+                       "path": "force_field + render_depth -> shade_intensity (images from the poses), MSE, "
+                               "backward to pose, twist, contact parameters and coefficients"},
         "kernel_ms": k_ms,
         "roofline": {
             "shade_intensity_kernel": {"algorithmic_bytes": inten_bytes,
                                        "frac": inten_bytes / (k_ms["shade_intensity_kernel"] * 1e-3) / 1e9 / peak},
             "shade_coeff_grad_kernel": {"algorithmic_bytes": cgrad_bytes,
                                         "frac": cgrad_bytes / (k_ms["shade_coeff_grad_kernel"] * 1e-3) / 1e9 / peak},
+            "render_adjoint_kernel": {"algorithmic_bytes": radj_bytes, "hit_columns": n_hit,
+                                      "frac": radj_bytes / (k_ms["render_adjoint_kernel"] * 1e-3) / 1e9 / peak},
             "peak_gbs": peak},
         "gpu_launches_per_step": 4,
     }

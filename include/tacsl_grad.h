@@ -56,8 +56,9 @@ int tacsl_shade_adjoint(const tacsl_shading* shading, int64_t B, const int32_t* 
                         float* grad_depth, tacsl_stream_t stream);
 
 /* Adjoint of tacsl_render_depth w.r.t. the pad poses (the pose -> depth -> image chain;
- * same set, E, P, obj_id, pad_pose, camera).  depth_map [E*P][H][W] (device) is the
- * render of these poses and g_depth [E*P][H][W] (device) the upstream gradient; grad_pose
+ * same set, E, P, obj_id, pad_pose, camera).  depth_map [E*P][H][W] (device, 16-byte
+ * aligned) is the render of these poses and g_depth [E*P][H][W] (device) the upstream
+ * gradient, read only at the columns that carry a derivative; grad_pose
  * [E*P][7] (device, overwritten) receives dL/dt and dL/dq for the raw quaternion, as
  * tacsl_penalty_forces_adjoint gives them.  A column that hits the object at z_hit in
  * (-z_max, 0) has D = d0 + z_hit with phi(R p + t) = 0, p = (x_i, y_j, z_hit), so (implicit

@@ -11,8 +11,10 @@
 // camera's range (D <= d0 - z_max), grazing columns (|phi_z| < 0.05) and hits outside the
 // grid's domain.  dL/dR is mapped to the raw quaternion through its normalisation.
 //
-// Launch: CTA clusters of C CTAs per pad (C = 1 when the batch alone fills the GPU).  The
-// C CTAs take contiguous pixel ranges of the pad's image; each reduces its 12 sums (t, R)
+// Launch: CTA clusters of C CTAs per pad, C chosen on the host so that the launch fills
+// whole waves of resident CTAs (C = 1 when the batch alone does).  The C CTAs take
+// contiguous pixel ranges of the pad's image, streaming the depth map as float4 (the
+// upstream gradient is read only at hit columns); each reduces its 12 sums (t, R)
 // in a fixed order (shuffles, then warps in order); the cluster's rank 0 reads the other
 // ranks' sums from their shared memory (DSMEM) in rank order after a cluster barrier, so
 // the result does not depend on scheduling.
@@ -26,6 +28,7 @@
 namespace tacsl {
 
 constexpr int kRenderAdjThreads = 256;
+constexpr int kRenderAdjUnroll = 4;     // float4 depth loads in flight per thread
 constexpr int kRenderAdjMaxCluster = 8;
 constexpr float kGrazing = 0.05f;   // |d phi / dz| below this: no derivative (grazing column)
 
@@ -114,7 +117,7 @@ __device__ __forceinline__ void render_pixel_adjoint(const DevSdf& S, const floa
     }
 }
 
-__global__ void __launch_bounds__(kRenderAdjThreads) render_adjoint_kernel(const RenderAdjointArgs A) {
+__global__ void __launch_bounds__(kRenderAdjThreads, 4) render_adjoint_kernel(const RenderAdjointArgs A) {
     __shared__ float warp_sum[kRenderAdjThreads / 32][12];
     __shared__ float cta_sum[12];
     const int C = A.cluster;
@@ -125,28 +128,68 @@ __global__ void __launch_bounds__(kRenderAdjThreads) render_adjoint_kernel(const
     float acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = 0.f;
+    __shared__ float rt_s[12];              // the pad's R (row-major) and t, one copy per CTA
+    if (!bad && threadIdx.x == 0) {
+        const float* pose = A.pad_pose + b * 7;
+        quat_to_rot(__ldg(pose + 3), __ldg(pose + 4), __ldg(pose + 5), __ldg(pose + 6), rt_s);
+        rt_s[9] = __ldg(pose);
+        rt_s[10] = __ldg(pose + 1);
+        rt_s[11] = __ldg(pose + 2);
+    }
+    __syncthreads();
     if (!bad) {
         const DevSdf& S = A.tab.s[id];
-        const float* pose = A.pad_pose + b * 7;
-        float r[9];
-        quat_to_rot(__ldg(pose + 3), __ldg(pose + 4), __ldg(pose + 5), __ldg(pose + 6), r);
-        const float t[3] = {__ldg(pose), __ldg(pose + 1), __ldg(pose + 2)};
         const CameraArgs& cam = A.cam;
-        const int HW = cam.H * cam.W;
+        const int HW = cam.H * cam.W;            // a multiple of 4 (W is)
         const float bottom = cam.d0 - cam.z_max;
-        const int beg = static_cast<int>(static_cast<int64_t>(HW) * rank / C);
-        const int end = static_cast<int>(static_cast<int64_t>(HW) * (rank + 1) / C);
+        const int n4 = HW >> 2;
+        const int beg = static_cast<int>(static_cast<int64_t>(n4) * rank / C);
+        const int end = static_cast<int>(static_cast<int64_t>(n4) * (rank + 1) / C);
         const float* D = A.depth + b * HW;
         const float* G = A.g_depth + b * HW;
+        const float4* D4 = reinterpret_cast<const float4*>(D);
         const uint64_t pol = policy_evict_last();
-        for (int k = beg + static_cast<int>(threadIdx.x); k < end; k += kRenderAdjThreads) {
-            const float d = __ldcs(D + k);
-            const float g = __ldcs(G + k);
-            if (!(d < cam.d0 && d > bottom) || g == 0.f) continue;
-            const int j = k / cam.W, i = k - j * cam.W;
-            const float px = fmaf(static_cast<float>(i), cam.pitch_x, cam.x0);
-            const float py = fmaf(static_cast<float>(j), cam.pitch_y, cam.y0);
-            render_pixel_adjoint(S, r, t, px, py, d - cam.d0, g, pol, acc);
+        // Stream the depth map 16 pixels per thread per pass (kRenderAdjUnroll float4
+        // loads in flight); the upstream gradient is read only at hit columns.
+        for (int k4 = beg + static_cast<int>(threadIdx.x); k4 < end; k4 += kRenderAdjUnroll * kRenderAdjThreads) {
+            float4 dv[kRenderAdjUnroll];
+#pragma unroll
+            for (int u = 0; u < kRenderAdjUnroll; ++u) {
+                const int q = k4 + u * kRenderAdjThreads;
+                dv[u] = q < end ? __ldcs(D4 + q) : make_float4(cam.d0, cam.d0, cam.d0, cam.d0);
+            }
+            uint32_t hits = 0;
+#pragma unroll
+            for (int u = 0; u < kRenderAdjUnroll; ++u) {
+                const float c4[4] = {dv[u].x, dv[u].y, dv[u].z, dv[u].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (c4[c] < cam.d0 && c4[c] > bottom) hits |= 1u << (4 * u + c);
+            }
+            while (hits != 0u) {
+                const int h = __ffs(hits) - 1;
+                hits &= hits - 1u;
+                const int k = 4 * (k4 + (h >> 2) * kRenderAdjThreads) + (h & 3);
+                const float g = __ldcs(G + k);
+                if (g == 0.f) continue;
+                float d = 0.f;                     // dv's element h, selected without local memory
+#pragma unroll
+                for (int u = 0; u < kRenderAdjUnroll; ++u) {
+                    d = h == 4 * u ? dv[u].x : d;
+                    d = h == 4 * u + 1 ? dv[u].y : d;
+                    d = h == 4 * u + 2 ? dv[u].z : d;
+                    d = h == 4 * u + 3 ? dv[u].w : d;
+                }
+                const int j = k / cam.W, i = k - j * cam.W;
+                const float px = fmaf(static_cast<float>(i), cam.pitch_x, cam.x0);
+                const float py = fmaf(static_cast<float>(j), cam.pitch_y, cam.y0);
+                float r[9], t[3];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) r[q] = rt_s[q];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) t[q] = rt_s[9 + q];
+                render_pixel_adjoint(S, r, t, px, py, d - cam.d0, g, pol, acc);
+            }
         }
     }
     // CTA reduction in a fixed order: lanes by xor shuffles, then warps in index order

@@ -58,6 +58,7 @@ struct DevInfo {
     bool shade_attr_set = false;
     bool batch_shade_attr_set = false;
     int batch_force_ctas[4] = {0, 0, 0, 0};   // resident CTAs per SM: [np == 4][dynamic]
+    int render_adj_ctas = 0;                    // resident render-adjoint CTAs per SM
     // streams and events of tacsl_tactile_step_host, created on its first call here
     cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t pipe_start = nullptr, pipe_done[3] = {nullptr, nullptr, nullptr};
@@ -1280,19 +1281,33 @@ int tacsl_render_depth_adjoint(const tacsl_sdf_set* set, int32_t E, int32_t P, c
     if (B == 0) return ok();
     if (obj_id == nullptr || !aligned(obj_id, 4) || pad_pose == nullptr || !aligned(pad_pose, 4))
         return fail(TACSL_ERR_INVALID_ARG, "obj_id and pad_pose must be non-NULL and 4-byte aligned");
-    if (depth_map == nullptr || !aligned(depth_map, 4) || g_depth == nullptr || !aligned(g_depth, 4) ||
-        grad_pose == nullptr || !aligned(grad_pose, 4))
-        return fail(TACSL_ERR_INVALID_ARG, "depth_map, g_depth and grad_pose must be non-NULL and 4-byte aligned");
+    if (depth_map == nullptr || !aligned(depth_map, 16))
+        return fail(TACSL_ERR_INVALID_ARG, "depth_map must be non-NULL and 16-byte aligned");
+    if (g_depth == nullptr || !aligned(g_depth, 4) || grad_pose == nullptr || !aligned(grad_pose, 4))
+        return fail(TACSL_ERR_INVALID_ARG, "g_depth and grad_pose must be non-NULL and 4-byte aligned");
     DevInfo* dev;
     if ((rc = device_info(&dev))) return rc;
-    // CTAs per pad: one when the batch alone gives every SM a few CTAs, else up to a
-    // cluster of 8, each CTA keeping at least 2048 pixels
+    if (dev->render_adj_ctas == 0) {
+        int n = 0;
+        const cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_adjoint_kernel,
+                                                                             kRenderAdjThreads, 0);
+        if (oe != cudaSuccess || n < 1) return fail(TACSL_ERR_CUDA, "render adjoint occupancy query failed");
+        dev->render_adj_ctas = n;
+    }
+    // CTAs per pad: the C in 1..8 (each CTA keeping at least 2048 pixels) whose launch
+    // of B*C CTAs, each taking 1/C of an image, ends soonest on the resident CTA slots:
+    // minimise ceil(B*C / slots) / C, ties to the smaller C
     const int64_t HW = (int64_t)c.H * c.W;
-    const int64_t want = 4 * (int64_t)dev->sms;
+    const int64_t slots = (int64_t)dev->render_adj_ctas * dev->sms;
+    const int64_t c_max = std::min<int64_t>(kRenderAdjMaxCluster, std::max<int64_t>(1, HW / 2048));
     int C = 1;
-    if (B < want) {
-        const int64_t by_batch = (want + B - 1) / B, by_pixels = std::max<int64_t>(1, HW / 2048);
-        C = (int)std::min<int64_t>({(int64_t)kRenderAdjMaxCluster, by_batch, by_pixels});
+    double best = (double)((B + slots - 1) / slots);
+    for (int64_t cc = 2; cc <= c_max; ++cc) {
+        const double t = (double)((B * cc + slots - 1) / slots) / (double)cc;
+        if (t < best - 1e-9) {
+            best = t;
+            C = (int)cc;
+        }
     }
     if (B * C > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "E*P = %lld pads in one call", (long long)B);
     RenderAdjointArgs A{tab, B, P, C, obj_id, pad_pose, c, depth_map, g_depth, grad_pose};
