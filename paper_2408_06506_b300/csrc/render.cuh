@@ -10,7 +10,11 @@
 // domain (kappa = 1/sqrt 3: the trilinear interpolant of a 1-Lipschitz field is at most
 // sqrt 3-Lipschitz, so a step cannot pass the surface), the exact distance to the
 // domain box outside it, never less than voxel/8 - then bisection of the first bracket
-// down to voxel * 2^-16; z_hit is the bracket's upper end.  The current trilinear cell
+// down to voxel * 2^-16; z_hit is the bracket's upper end.  When that distance bound
+// already covers the rest of the column (with a 1e-4 relative margin) the column
+// misses without a last sample at z = 0: by the same Lipschitz bound that sample could
+// not be inside the object.  Samples are taken in grid-index space (u = (x - origin) /
+// voxel, affine in the column's height), not by posing each point.  The current trilinear cell
 // and its 8 nodes stay in registers while samples remain in it.  phi is the 8-node cell value of the
 // force-field path (phi_cell8), so image and force field see the same SDF.  Outside the
 // grid's domain the SDF is undefined (as for the force field), so a point there is never
@@ -70,94 +74,139 @@ struct CameraArgs {
     float pitch_x, pitch_y, x0, y0, d0, z_max;
 };
 
-// phi the march sees at object-frame point (x, y, z): trilinear in the domain, else the
+// phi the march sees at continuous grid index u: trilinear in the domain, else the
 // distance to the domain box (inside_out reports which).  Outside the domain the SDF is
 // undefined, so such a point is never inside the object: callers test inside && phi <= 0.
-__device__ __forceinline__ float column_phi(const DevSdf& S, float x, float y, float z, uint64_t pol,
-                                            bool& inside_out, CellCache& cc) {
-    const GridPos g = grid_pos(S, x, y, z);
-    inside_out = g.inside;
-    if (g.inside) return phi_cell8_cached(S, g, pol, cc);
-    const float lox = S.ox + 0.5f * S.h, hix = S.ox + (static_cast<float>(S.n0) - 1.5f) * S.h;
-    const float loy = S.oy + 0.5f * S.h, hiy = S.oy + (static_cast<float>(S.n1) - 1.5f) * S.h;
-    const float loz = S.oz + 0.5f * S.h, hiz = S.oz + (static_cast<float>(S.n2) - 1.5f) * S.h;
-    const float ex = fmaxf(fmaxf(lox - x, x - hix), 0.f);
-    const float ey = fmaxf(fmaxf(loy - y, y - hiy), 0.f);
-    const float ez = fmaxf(fmaxf(loz - z, z - hiz), 0.f);
-    return sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+__device__ __forceinline__ float column_phi_u(const DevSdf& S, float ux, float uy, float uz, uint64_t pol,
+                                              bool& inside_out, CellCache& cc) {
+    GridPos g;
+    g.ux = ux;
+    g.uy = uy;
+    g.uz = uz;
+    const float hx = static_cast<float>(S.n0) - 1.5f, hy = static_cast<float>(S.n1) - 1.5f,
+                hz = static_cast<float>(S.n2) - 1.5f;
+    inside_out = ux >= 0.5f && ux <= hx && uy >= 0.5f && uy <= hy && uz >= 0.5f && uz <= hz;
+    if (inside_out) return phi_cell8_cached(S, g, pol, cc);
+    const float ex = fmaxf(fmaxf(0.5f - ux, ux - hx), 0.f);
+    const float ey = fmaxf(fmaxf(0.5f - uy, uy - hy), 0.f);
+    const float ez = fmaxf(fmaxf(0.5f - uz, uz - hz), 0.f);
+    return sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) * S.h;
 }
 
-// Grid: (32 x 8 pixel tiles of the image, images); each warp marches 32 neighbouring
-// columns of one row, and every thread keeps its column across the images it takes.
+// One image's column frame in grid-index space: the continuous grid index of pixel
+// (i, j) at height z is u = u00 + i ui + j uj + z du, i.e. (R (x_i, y_j, z) + t - origin)
+// / voxel with x_i = x0 + i pitch_x, y_j = y0 + j pitch_y.
+struct RenderFrame {
+    float u00[3];
+    int id;          // object id, -1 when out of range
+    float ui[3], pad0;
+    float uj[3], pad1;
+    float du[3], pad2;
+};
+constexpr int kRenderFrames = 256;   // frames a block keeps in shared memory at a time
+
+__device__ __forceinline__ void render_frame(const SdfTable& tab, const int32_t* obj_id, const float* pad_pose,
+                                             int64_t b, int P, const CameraArgs& cam, RenderFrame& f) {
+    const int id = __ldg(obj_id + static_cast<int>(b / P));
+    if (id < 0 || id >= tab.count) {
+        f.id = -1;
+        return;
+    }
+    const DevSdf& S = tab.s[id];
+    const float* pose = pad_pose + b * 7;
+    float r[9];
+    quat_to_rot(__ldg(pose + 3), __ldg(pose + 4), __ldg(pose + 5), __ldg(pose + 6), r);
+    const float t[3] = {__ldg(pose), __ldg(pose + 1), __ldg(pose + 2)};
+    const float o[3] = {S.ox, S.oy, S.oz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f.u00[a] = (fmaf(r[3 * a], cam.x0, fmaf(r[3 * a + 1], cam.y0, t[a])) - o[a]) * S.inv_h;
+        f.ui[a] = r[3 * a] * cam.pitch_x * S.inv_h;
+        f.uj[a] = r[3 * a + 1] * cam.pitch_y * S.inv_h;
+        f.du[a] = r[3 * a + 2] * S.inv_h;
+    }
+    f.id = id;
+}
+
+// Grid: (32 x 8 pixel tiles of the image, up to 64 image slots); block y takes images
+// y, y + gridDim.y, ...  Each thread keeps its column across those images.  The images'
+// frames are computed up front, kRenderFrames at a time, into shared memory, so a
+// column's set-up is 6 FMAs and each sample of the march 3.
 __global__ void __launch_bounds__(256) render_kernel(const SdfTable tab, int64_t B, int P,
                                                      const int32_t* __restrict__ obj_id,
                                                      const float* __restrict__ pad_pose, const CameraArgs cam,
                                                      float* __restrict__ depth) {
+    __shared__ RenderFrame frames[kRenderFrames];
     const int tiles_x = (cam.W + 31) / 32;
     const int tile_y = static_cast<int>(blockIdx.x) / tiles_x, tile_x = static_cast<int>(blockIdx.x) - tile_y * tiles_x;
     const int i = tile_x * 32 + static_cast<int>(threadIdx.x & 31), j = tile_y * 8 + static_cast<int>(threadIdx.x >> 5);
-    if (i >= cam.W || j >= cam.H) return;
+    const bool live = i < cam.W && j < cam.H;
     const int64_t HW = static_cast<int64_t>(cam.H) * cam.W;
     const int pix = j * cam.W + i;
     const uint64_t pol = policy_evict_last();
-    for (int64_t b = blockIdx.y; b < B; b += gridDim.y) {
-        const int64_t k = b * HW + pix;
-        const int id = __ldg(obj_id + static_cast<int>(b) / P);
-        if (id < 0 || id >= tab.count) {
-            depth[k] = __int_as_float(0x7fc00000);
-            raise_dev_error(TACSL_DEVERR_BAD_OBJ_ID);
-            continue;
-        }
-        const DevSdf& S = tab.s[id];
-        const float* pose = pad_pose + b * 7;
-        float r[9];
-        quat_to_rot(__ldg(pose + 3), __ldg(pose + 4), __ldg(pose + 5), __ldg(pose + 6), r);
-        const float tx = __ldg(pose), ty = __ldg(pose + 1), tz = __ldg(pose + 2);
-        const float px = fmaf(static_cast<float>(i), cam.pitch_x, cam.x0);
-        const float py = fmaf(static_cast<float>(j), cam.pitch_y, cam.y0);
-        // column point R (px, py, z) + t
-        auto point = [&](float z, float& x, float& y, float& w) {
-            x = fmaf(r[0], px, fmaf(r[1], py, fmaf(r[2], z, tx)));
-            y = fmaf(r[3], px, fmaf(r[4], py, fmaf(r[5], z, ty)));
-            w = fmaf(r[6], px, fmaf(r[7], py, fmaf(r[8], z, tz)));
-        };
-        const float dmin = S.h * 0.125f, kappa = 0.57735026918962576f;
-        float x, y, w;
-        bool in;
-        float z = -cam.z_max;
-        point(z, x, y, w);
-        CellCache cc;
-        float phi = column_phi(S, x, y, w, pol, in, cc);
-        float zhit = 1.f;   // > 0: no hit
-        if (in && phi <= 0.f) {
-            zhit = z;
-        } else {
-            for (int it = 0; it < kMarchMax; ++it) {
-                const float step = fmaxf(in ? kappa * phi : phi, dmin);
-                const float zn = fminf(z + step, 0.f);
-                point(zn, x, y, w);
-                bool in_n;
-                const float phin = column_phi(S, x, y, w, pol, in_n, cc);
-                if (in_n && phin <= 0.f) {
-                    float lo = z, hi = zn;
-                    const float eps = S.h * (1.f / 65536.f);
-                    for (int q = 0; q < kBisectMax && hi - lo > eps; ++q) {
-                        const float mid = 0.5f * (lo + hi);
-                        point(mid, x, y, w);
-                        bool im;
-                        const float pm = column_phi(S, x, y, w, pol, im, cc);
-                        if (im && pm <= 0.f) hi = mid; else lo = mid;
-                    }
-                    zhit = hi;
-                    break;
-                }
-                if (zn >= 0.f) break;
-                z = zn;
-                phi = phin;
-                in = in_n;
+    const float fi = static_cast<float>(i), fj = static_cast<float>(j);
+    const int64_t n_img = (B - static_cast<int64_t>(blockIdx.y) + gridDim.y - 1) / gridDim.y;
+    for (int64_t base = 0; base < n_img; base += kRenderFrames) {
+        const int n_here = static_cast<int>(n_img - base < kRenderFrames ? n_img - base : kRenderFrames);
+        __syncthreads();       // the previous frames are no longer read
+        if (static_cast<int>(threadIdx.x) < n_here)
+            render_frame(tab, obj_id, pad_pose, static_cast<int64_t>(blockIdx.y) + (base + threadIdx.x) * gridDim.y,
+                         P, cam, frames[threadIdx.x]);
+        __syncthreads();
+        if (!live) continue;
+        for (int m = 0; m < n_here; ++m) {
+            const int64_t b = static_cast<int64_t>(blockIdx.y) + (base + m) * gridDim.y;
+            const int64_t k = b * HW + pix;
+            const RenderFrame& F = frames[m];
+            if (F.id < 0) {
+                depth[k] = __int_as_float(0x7fc00000);
+                raise_dev_error(TACSL_DEVERR_BAD_OBJ_ID);
+                continue;
             }
+            const DevSdf& S = tab.s[F.id];
+            const float du0 = F.du[0], du1 = F.du[1], du2 = F.du[2];
+            const float u0 = fmaf(fj, F.uj[0], fmaf(fi, F.ui[0], F.u00[0]));
+            const float u1 = fmaf(fj, F.uj[1], fmaf(fi, F.ui[1], F.u00[1]));
+            const float u2 = fmaf(fj, F.uj[2], fmaf(fi, F.ui[2], F.u00[2]));
+            const float dmin = S.h * 0.125f, kappa = 0.57735026918962576f;
+            CellCache cc;
+            bool in;
+            float z = -cam.z_max;
+            float phi = column_phi_u(S, fmaf(z, du0, u0), fmaf(z, du1, u1), fmaf(z, du2, u2), pol, in, cc);
+            float zhit = 1.f;   // > 0: no hit
+            if (in && phi <= 0.f) {
+                zhit = z;
+            } else {
+                for (int it = 0; it < kMarchMax; ++it) {
+                    // no point of the object within the distance bound of the sample:
+                    // when that covers the rest of the column, the column misses
+                    const float bound = in ? kappa * phi : phi;
+                    if (bound > -z * 1.0001f) break;
+                    const float zn = fminf(z + fmaxf(bound, dmin), 0.f);
+                    bool in_n;
+                    const float phin =
+                        column_phi_u(S, fmaf(zn, du0, u0), fmaf(zn, du1, u1), fmaf(zn, du2, u2), pol, in_n, cc);
+                    if (in_n && phin <= 0.f) {
+                        float lo = z, hi = zn;
+                        const float eps = S.h * (1.f / 65536.f);
+                        for (int q = 0; q < kBisectMax && hi - lo > eps; ++q) {
+                            const float mid = 0.5f * (lo + hi);
+                            bool im;
+                            const float pm = column_phi_u(S, fmaf(mid, du0, u0), fmaf(mid, du1, u1),
+                                                          fmaf(mid, du2, u2), pol, im, cc);
+                            if (im && pm <= 0.f) hi = mid; else lo = mid;
+                        }
+                        zhit = hi;
+                        break;
+                    }
+                    if (zn >= 0.f) break;
+                    z = zn;
+                    phi = phin;
+                    in = in_n;
+                }
+            }
+            depth[k] = cam.d0 - ((zhit < 0.f) ? -zhit : 0.f);
         }
-        depth[k] = cam.d0 - ((zhit < 0.f) ? -zhit : 0.f);
     }
 }
 
