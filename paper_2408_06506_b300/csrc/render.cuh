@@ -8,17 +8,20 @@
 //
 // March: conservative sphere tracing up the column - step kappa*phi inside the grid
 // domain (kappa = 1/sqrt 3: the trilinear interpolant of a 1-Lipschitz field is at most
-// sqrt 3-Lipschitz, so a step cannot pass the surface), the exact distance to the
-// domain box outside it, never less than voxel/8 - then bisection of the first bracket
-// down to voxel * 2^-16; z_hit is the bracket's upper end.  When that distance bound
-// already covers the rest of the column (with a 1e-4 relative margin) the column
-// misses without a last sample at z = 0: by the same Lipschitz bound that sample could
-// not be inside the object.  Samples are taken in grid-index space (u = (x - origin) /
-// voxel, affine in the column's height), not by posing each point.  The current trilinear cell
-// and its 8 nodes stay in registers while samples remain in it.  phi is the 8-node cell value of the
-// force-field path (phi_cell8), so image and force field see the same SDF.  Outside the
-// grid's domain the SDF is undefined (as for the force field), so a point there is never
-// inside the object; the distance to the domain box only sizes the step.
+// sqrt 3-Lipschitz, so a step cannot pass the surface), never less than voxel/8 - then
+// bisection of the first bracket down to voxel * 2^-16; z_hit is the bracket's upper
+// end.  phi is the trilinear interpolant of the force field (same cell rule and FMA
+// order as phi_cell8), so image and force field see the same SDF; outside the grid's
+// domain the SDF is undefined and no point there counts as inside the object.
+//
+// Two shortcuts leave the result unchanged.  The march runs over the part of the column
+// inside the domain alone, found by a slab test: outside it the reference march's
+// box-distance steps can only end in a miss or reach that part.  And when the distance
+// bound already covers the rest of that part (with a 1e-4 relative margin) the column
+// misses without further samples: by the same Lipschitz bound none of them could be
+// inside the object.  Samples are taken in grid-index space (u = (x - origin) / voxel,
+// affine in the column's height), not by posing each point; the current trilinear cell
+// and its 8 nodes stay in registers while samples remain in it.
 //
 // One thread per column: a warp takes 32 neighbouring columns of a row, whose marches
 // take similar paths and whose SDF reads fall on neighbouring nodes.
@@ -32,33 +35,40 @@ namespace tacsl {
 constexpr int kMarchMax = 1024;   // safety cap on march steps (never reached in practice)
 constexpr int kBisectMax = 40;    // bisection stops at a bracket <= voxel * 2^-16 (~13 halvings)
 
-// The trilinear cell of the last sample and its 8 node values: successive samples of a
-// column (small steps, bisection) mostly stay in one cell, so its nodes are read once.
-// The value is computed exactly as phi_cell8 computes it (same nodes, same FMA order).
-struct CellCache {
-    int ix = -1, iy = -1, iz = -1;
+struct CameraArgs {
+    int H, W;
+    float pitch_x, pitch_y, x0, y0, d0, z_max;
+};
+
+// The trilinear cell of the last sample (as float indices) and its 8 node values.
+struct CellCacheF {
+    float cx = -1.f, cy = -1.f, cz = -1.f;
     float v[2][2][2];
 };
 
-__device__ __forceinline__ float phi_cell8_cached(const DevSdf& S, const GridPos& g, uint64_t pol, CellCache& cc) {
-    const int ix = min(static_cast<int>(floorf(g.ux)), S.n0 - 2);
-    const int iy = min(static_cast<int>(floorf(g.uy)), S.n1 - 2);
-    const int iz = min(static_cast<int>(floorf(g.uz)), S.n2 - 2);
-    if (ix != cc.ix || iy != cc.iy || iz != cc.iz) {
+// phi at a continuous grid index u inside the domain: trilinear in the cell
+// min(floor(u), n - 2) (clamped at 0, which also keeps the loads in bounds whatever u
+// rounds to), nodes re-read only when the cell changes.
+__device__ __forceinline__ float column_phi_in(const DevSdf& S, float ux, float uy, float uz, uint64_t pol,
+                                               CellCacheF& cc) {
+    const float cx = fminf(fmaxf(floorf(ux), 0.f), static_cast<float>(S.n0 - 2));
+    const float cy = fminf(fmaxf(floorf(uy), 0.f), static_cast<float>(S.n1 - 2));
+    const float cz = fminf(fmaxf(floorf(uz), 0.f), static_cast<float>(S.n2 - 2));
+    if (cx != cc.cx || cy != cc.cy || cz != cc.cz) {
         const int n0 = S.n0, n01 = S.n0 * S.n1;
-        const float* b = S.data + (static_cast<int64_t>(iz) * n01 + static_cast<int64_t>(iy) * n0 + ix);
+        const float* b = S.data + (static_cast<int64_t>(static_cast<int>(cz)) * n01 +
+                                   static_cast<int64_t>(static_cast<int>(cy)) * n0 + static_cast<int>(cx));
 #pragma unroll
         for (int k = 0; k < 2; ++k)
 #pragma unroll
             for (int j = 0; j < 2; ++j)
 #pragma unroll
                 for (int i = 0; i < 2; ++i) cc.v[k][j][i] = ldg_f_hint(b + k * n01 + j * n0 + i, pol);
-        cc.ix = ix;
-        cc.iy = iy;
-        cc.iz = iz;
+        cc.cx = cx;
+        cc.cy = cy;
+        cc.cz = cz;
     }
-    const float fx = g.ux - static_cast<float>(ix), fy = g.uy - static_cast<float>(iy),
-                fz = g.uz - static_cast<float>(iz);
+    const float fx = ux - cx, fy = uy - cy, fz = uz - cz;
     float c[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -69,39 +79,17 @@ __device__ __forceinline__ float phi_cell8_cached(const DevSdf& S, const GridPos
     return fmaf(fz, c[1], (1.f - fz) * c[0]);
 }
 
-struct CameraArgs {
-    int H, W;
-    float pitch_x, pitch_y, x0, y0, d0, z_max;
-};
-
-// phi the march sees at continuous grid index u: trilinear in the domain, else the
-// distance to the domain box (inside_out reports which).  Outside the domain the SDF is
-// undefined, so such a point is never inside the object: callers test inside && phi <= 0.
-__device__ __forceinline__ float column_phi_u(const DevSdf& S, float ux, float uy, float uz, uint64_t pol,
-                                              bool& inside_out, CellCache& cc) {
-    GridPos g;
-    g.ux = ux;
-    g.uy = uy;
-    g.uz = uz;
-    const float hx = static_cast<float>(S.n0) - 1.5f, hy = static_cast<float>(S.n1) - 1.5f,
-                hz = static_cast<float>(S.n2) - 1.5f;
-    inside_out = ux >= 0.5f && ux <= hx && uy >= 0.5f && uy <= hy && uz >= 0.5f && uz <= hz;
-    if (inside_out) return phi_cell8_cached(S, g, pol, cc);
-    const float ex = fmaxf(fmaxf(0.5f - ux, ux - hx), 0.f);
-    const float ey = fmaxf(fmaxf(0.5f - uy, uy - hy), 0.f);
-    const float ez = fmaxf(fmaxf(0.5f - uz, uz - hz), 0.f);
-    return sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) * S.h;
-}
-
 // One image's column frame in grid-index space: the continuous grid index of pixel
 // (i, j) at height z is u = u00 + i ui + j uj + z du, i.e. (R (x_i, y_j, z) + t - origin)
-// / voxel with x_i = x0 + i pitch_x, y_j = y0 + j pitch_y.
+// / voxel with x_i = x0 + i pitch_x, y_j = y0 + j pitch_y; inv_du = 1 / du (+-inf for a
+// zero component) gives the heights where the column crosses the domain's faces.
 struct RenderFrame {
     float u00[3];
     int id;          // object id, -1 when out of range
     float ui[3], pad0;
     float uj[3], pad1;
     float du[3], pad2;
+    float inv_du[3], pad3;
 };
 constexpr int kRenderFrames = 256;   // frames a block keeps in shared memory at a time
 
@@ -124,14 +112,17 @@ __device__ __forceinline__ void render_frame(const SdfTable& tab, const int32_t*
         f.ui[a] = r[3 * a] * cam.pitch_x * S.inv_h;
         f.uj[a] = r[3 * a + 1] * cam.pitch_y * S.inv_h;
         f.du[a] = r[3 * a + 2] * S.inv_h;
+        f.inv_du[a] = 1.f / f.du[a];
     }
     f.id = id;
 }
 
 // Grid: (32 x 8 pixel tiles of the image, up to 64 image slots); block y takes images
 // y, y + gridDim.y, ...  Each thread keeps its column across those images.  The images'
-// frames are computed up front, kRenderFrames at a time, into shared memory, so a
-// column's set-up is 6 FMAs and each sample of the march 3.
+// frames are computed up front, kRenderFrames at a time, into shared memory.  Per
+// column: the part of [-z_max, 0] inside the grid's domain (slab test on the affine
+// u(z)); outside it the SDF is undefined and no point counts as inside the object, so
+// the march runs over that part alone, 3 FMAs per sample.
 __global__ void __launch_bounds__(256) render_kernel(const SdfTable tab, int64_t B, int P,
                                                      const int32_t* __restrict__ obj_id,
                                                      const float* __restrict__ pad_pose, const CameraArgs cam,
@@ -168,41 +159,52 @@ __global__ void __launch_bounds__(256) render_kernel(const SdfTable tab, int64_t
             const float u0 = fmaf(fj, F.uj[0], fmaf(fi, F.ui[0], F.u00[0]));
             const float u1 = fmaf(fj, F.uj[1], fmaf(fi, F.ui[1], F.u00[1]));
             const float u2 = fmaf(fj, F.uj[2], fmaf(fi, F.ui[2], F.u00[2]));
-            const float dmin = S.h * 0.125f, kappa = 0.57735026918962576f;
-            CellCache cc;
-            bool in;
-            float z = -cam.z_max;
-            float phi = column_phi_u(S, fmaf(z, du0, u0), fmaf(z, du1, u1), fmaf(z, du2, u2), pol, in, cc);
+            // heights where the column is inside the domain: u_a(z) in [0.5, n_a - 1.5]
+            float zlo = -cam.z_max, zhi = 0.f;
+            {
+                const float ua[3] = {u0, u1, u2}, hi[3] = {static_cast<float>(S.n0) - 1.5f,
+                                                           static_cast<float>(S.n1) - 1.5f,
+                                                           static_cast<float>(S.n2) - 1.5f};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float ta = (0.5f - ua[a]) * F.inv_du[a], tb = (hi[a] - ua[a]) * F.inv_du[a];
+                    zlo = fmaxf(zlo, fminf(ta, tb));
+                    zhi = fminf(zhi, fmaxf(ta, tb));
+                }
+            }
             float zhit = 1.f;   // > 0: no hit
-            if (in && phi <= 0.f) {
-                zhit = z;
-            } else {
-                for (int it = 0; it < kMarchMax; ++it) {
-                    // no point of the object within the distance bound of the sample:
-                    // when that covers the rest of the column, the column misses
-                    const float bound = in ? kappa * phi : phi;
-                    if (bound > -z * 1.0001f) break;
-                    const float zn = fminf(z + fmaxf(bound, dmin), 0.f);
-                    bool in_n;
-                    const float phin =
-                        column_phi_u(S, fmaf(zn, du0, u0), fmaf(zn, du1, u1), fmaf(zn, du2, u2), pol, in_n, cc);
-                    if (in_n && phin <= 0.f) {
-                        float lo = z, hi = zn;
-                        const float eps = S.h * (1.f / 65536.f);
-                        for (int q = 0; q < kBisectMax && hi - lo > eps; ++q) {
-                            const float mid = 0.5f * (lo + hi);
-                            bool im;
-                            const float pm = column_phi_u(S, fmaf(mid, du0, u0), fmaf(mid, du1, u1),
-                                                          fmaf(mid, du2, u2), pol, im, cc);
-                            if (im && pm <= 0.f) hi = mid; else lo = mid;
+            if (zlo <= zhi) {
+                const float dmin = S.h * 0.125f, kappa = 0.57735026918962576f;
+                CellCacheF cc;
+                float z = zlo;
+                float phi = column_phi_in(S, fmaf(z, du0, u0), fmaf(z, du1, u1), fmaf(z, du2, u2), pol, cc);
+                if (phi <= 0.f) {
+                    zhit = z;
+                } else {
+                    for (int it = 0; it < kMarchMax; ++it) {
+                        // no point of the object within the distance bound of the sample:
+                        // when that covers the rest of the column's in-domain part, it misses
+                        const float bound = kappa * phi;
+                        if (bound > (zhi - z) * 1.0001f) break;
+                        const float zn = fminf(z + fmaxf(bound, dmin), zhi);
+                        const float phin =
+                            column_phi_in(S, fmaf(zn, du0, u0), fmaf(zn, du1, u1), fmaf(zn, du2, u2), pol, cc);
+                        if (phin <= 0.f) {
+                            float lo = z, hi = zn;
+                            const float eps = S.h * (1.f / 65536.f);
+                            for (int q = 0; q < kBisectMax && hi - lo > eps; ++q) {
+                                const float mid = 0.5f * (lo + hi);
+                                const float pm = column_phi_in(S, fmaf(mid, du0, u0), fmaf(mid, du1, u1),
+                                                               fmaf(mid, du2, u2), pol, cc);
+                                if (pm <= 0.f) hi = mid; else lo = mid;
+                            }
+                            zhit = hi;
+                            break;
                         }
-                        zhit = hi;
-                        break;
+                        if (zn >= zhi) break;
+                        z = zn;
+                        phi = phin;
                     }
-                    if (zn >= 0.f) break;
-                    z = zn;
-                    phi = phin;
-                    in = in_n;
                 }
             }
             depth[k] = cam.d0 - ((zhit < 0.f) ? -zhit : 0.f);
