@@ -83,7 +83,7 @@ __device__ __forceinline__ float column_phi_in(const DevSdf& S, float ux, float 
 // (i, j) at height z is u = u00 + i ui + j uj + z du, i.e. (R (x_i, y_j, z) + t - origin)
 // / voxel with x_i = x0 + i pitch_x, y_j = y0 + j pitch_y; inv_du = 1 / du (+-inf for a
 // zero component) gives the heights where the column crosses the domain's faces.
-struct RenderFrame {
+struct __align__(16) RenderFrame {
     float u00[3];
     int id;          // object id, -1 when out of range
     float ui[3], pad0;
