@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--e2e-chunk", type=int, default=256)
+    ap.add_argument("--oracle-seconds", type=float, default=6.0,
+                    help="seconds of FP64 oracle time per NEXT-row baseline (render, batch, grad)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -250,6 +252,93 @@ def oracle_rate(sc, n_env, seconds_target, max_passes=1000):
     return E * sc.P * sc.T * passes / el, E * sc.P * passes / el, nt, passes, el
 
 
+def oracle_loop(fn, seconds_target, max_passes=100000):
+    """Call fn(k) for k = 0, 1, ... until about seconds_target has elapsed; returns
+    (passes, seconds)."""
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        fn(k)
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_target or k >= max_passes:
+            return k, el
+
+
+def oracle_render_rate(sc, cam, seconds_target):
+    """The FP64 oracle's render step (column march, images, forces) one env at a time."""
+    import oracle
+    oracle.build()
+    nt = oracle.default_threads()
+    kp = [np.broadcast_to(v, (sc.E,)) for v in (sc.k_n, sc.k_d, sc.k_t, sc.mu)]
+
+    def one(k):
+        e = k % sc.E
+        sl = slice(e, e + 1)
+        D, _ = oracle.render_depth(sc.grids, sc.obj_id[sl], sc.pad_pose[sl], cam["H"], cam["W"], cam["pitch_x"],
+                                   cam["pitch_y"], cam["x0"], cam["y0"], cam["d0"], cam["z_max"], nthreads=nt)
+        oracle.shade(sc.coeffs, sc.pitch_x, sc.pitch_y, sc.sensor_id[sc.P * e:sc.P * (e + 1)],
+                     D.reshape(sc.P, cam["H"], cam["W"]).astype(np.float32), nthreads=nt)
+        oracle.penalty_forces(sc.grids, sc.taxels, sc.obj_id[sl], sc.pad_pose[sl], sc.pad_twist[sl],
+                              *[v[sl] for v in kp], nthreads=nt)
+
+    n, el = oracle_loop(one, seconds_target)
+    return {"value": n * sc.P * sc.T / el, "unit": "taxel-points/s", "images_per_s": n * sc.P / el, "cores": nt,
+            "kind": "oracle", "sample": f"{n} envs (x{sc.P} pads and images), one per call, in {el:.1f} s (FP64)"}
+
+
+def oracle_grad_rate(sc, seconds_target, seed):
+    """The FP64 gradient oracle (torch.autograd in float64) on one env at a time: force,
+    wrench and image gradients for fixed upstream gradients."""
+    import torch
+    from oracle import grad as G
+    g = np.random.default_rng(seed)
+    T, HW = sc.T, sc.H * sc.W
+    up = (g.normal(size=(1, sc.P, T)), g.normal(size=(1, sc.P, T, 3)), g.normal(size=(1, sc.P, T, 3)),
+          g.normal(size=(1, sc.P, 6)))
+    gI = g.normal(size=(sc.P, sc.H, sc.W, 3))
+    kp = [np.broadcast_to(v, (sc.E,)) for v in (sc.k_n, sc.k_d, sc.k_t, sc.mu)]
+    dm = sc.depth_map.reshape(-1, sc.H, sc.W)
+
+    def one(k):
+        e = k % sc.E
+        sl = slice(e, e + 1)
+        G.force_gradients(sc.grids, sc.taxels, sc.obj_id[sl], sc.pad_pose[sl], sc.pad_twist[sl],
+                          *[v[sl] for v in kp], *up)
+        G.shade_gradients(sc.coeffs, sc.pitch_x, sc.pitch_y, sc.sensor_id[sc.P * e:sc.P * (e + 1)],
+                          dm[sc.P * e:sc.P * (e + 1)], gI)
+
+    n, el = oracle_loop(one, seconds_target)
+    return {"value": n * sc.P * T / el, "unit": "taxel-points/s", "images_per_s": n * sc.P / el,
+            "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{n} envs (x{sc.P} pads and {HW}-pixel images), one per call, in {el:.1f} s (FP64 autograd)"}
+
+
+def oracle_batch_rate(sc, seconds_target):
+    """The FP64 oracle on the uneven batch, one pad (its own layout, object and image) per
+    call."""
+    import oracle
+    oracle.build()
+    nt = oracle.default_threads()
+    n_tax = [0]
+
+    def one(k):
+        b = k % sc.n_pad
+        lay = sc.layout[b]
+        f0, cnt = int(sc.layout_first[lay]), int(sc.layout_count[lay])
+        oracle.penalty_forces(sc.grids, sc.taxels[f0:f0 + cnt], sc.obj_id[b:b + 1], sc.pad_pose[b][None, None],
+                              sc.pad_twist[b][None, None], sc.k_n[b:b + 1], sc.k_d[b:b + 1], sc.k_t[b:b + 1],
+                              sc.mu[b:b + 1], nthreads=nt)
+        n_tax[0] += cnt
+        if sc.sensor[b] >= 0:
+            co, px, py = sc.models[sc.sensor[b]]
+            oracle.shade(co[None], px, py, [0], sc.depth_maps[b].reshape(1, co.shape[2], co.shape[3]), nthreads=nt)
+
+    n, el = oracle_loop(one, seconds_target)
+    return {"value": n_tax[0] / el, "unit": "taxel-points/s", "cores": nt, "kind": "oracle",
+            "sample": f"{n} pads with their images, one per call, in {el:.1f} s (FP64)"}
+
+
 def run_reference(args, rank):
     """Reference arm: the FP64 oracle as it stands, timed on the host cores."""
     if rank != 0:
@@ -384,6 +473,10 @@ def run_ours(args, rank, world, local_rank, dist):
     render = {"ms_per_step": breakdown["render_step_ms"],
               "taxel_points_per_s": world * E * P * T / (breakdown["render_step_ms"] * 1e-3),
               "images_per_s": world * E * P / (breakdown["render_step_ms"] * 1e-3)}
+    if rank == 0 and not args.no_cpu_baseline:
+        render["cpu_baseline"] = oracle_render_rate(
+            sc, dict(H=sc.H, W=sc.W, pitch_x=sc.pitch_x, pitch_y=sc.pitch_y, x0=cam.c.x0, y0=cam.c.y0, d0=cam.c.d0,
+                     z_max=cam.c.z_max), args.oracle_seconds)
     if not args.no_e2e:
         # the RL loop: pose/twist of this step in from pinned host memory, observations stay on
         # the device, the per-pad wrench comes back to the host
@@ -445,10 +538,33 @@ def run_ours(args, rank, world, local_rank, dist):
             e2e_step()
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
+        # the link's ceiling for these bytes: the same pinned buffers copied in both
+        # directions at once on two streams, with no kernel (plain cudaMemcpyAsync copies)
+        d_in = torch.empty(h_in["depth_map"].shape, dtype=torch.float32, device="cuda")
+        s_up, s_dn = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def copies_only():
+            with torch.cuda.stream(s_up):
+                for k, v in h_in.items():
+                    (d_in if k == "depth_map" else torch.empty_like(v, device="cuda")).copy_(v, non_blocking=True)
+            with torch.cuda.stream(s_dn):
+                for k, v in h_out.items():
+                    v.copy_(outs[k], non_blocking=True)
+
+        copies_only()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            copies_only()
+        torch.cuda.synchronize()
+        ceil_s = (time.perf_counter() - t0) / 3
+        del d_in
         e2e = {"value": world * E * P * T * args.e2e_steps / el, "unit": "taxel-points/s",
                "images_per_s": world * E * P * args.e2e_steps / el, "ms_per_step": 1e3 * el / args.e2e_steps,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                "copy_gb_per_s": (h2d + d2h) * args.e2e_steps / el / 1e9, "chunk_envs": ch,
+               "copy_only_ms": 1e3 * ceil_s, "copy_only_gb_per_s": (h2d + d2h) / ceil_s / 1e9,
+               "frac_of_copy_only": ceil_s / (el / args.e2e_steps),
                "path": "pinned host -> tacsl_tactile_step_host (chunks pipelined over 3 streams) -> pinned host"}
 
     batch = None if args.no_batch else run_batch(args, rank, world, local_rank, dist)
@@ -651,7 +767,9 @@ def run_batch(args, rank, world, local_rank, dist):
     force_bytes = (28 * nt + 12 * int(sc.layout_count.sum()) + (52 + 24 + 16 + 32) * sc.n_pad + sdf_bytes)
     taxel_pts = world * nt
     images = world * plan.plan.n_image
+    cpu = oracle_batch_rate(sc, args.oracle_seconds) if rank == 0 and not args.no_cpu_baseline else None
     return {
+        "cpu_baseline": cpu,
         "workload": BATCH_WORKLOAD, "envs_per_gpu": args.batch_envs, "pads_per_gpu": sc.n_pad,
         "taxel_points_per_gpu": int(nt), "images_per_gpu": int(plan.plan.n_image), "pixels_per_gpu": int(npx),
         "distinct_layouts": len(sc.layout_count), "sensor_models": len(sc.models),
@@ -843,6 +961,8 @@ def run_grad(args, rank, world, local_rank, dist):
                                       "frac": radj_bytes / (k_ms["render_adjoint_kernel"] * 1e-3) / 1e9 / peak},
             "peak_gbs": peak},
         "gpu_launches_per_step": 4,
+        "cpu_baseline": (oracle_grad_rate(sc, args.oracle_seconds, args.seed + 500)
+                         if rank == 0 and not args.no_cpu_baseline else None),
     }
 
 
