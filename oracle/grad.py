@@ -35,7 +35,8 @@ gradients equal float64 central differences of the C oracle (h = 1e-6; h = 1e-5 
 depth maps, whose hit search stops at voxel/65536), and closed forms (d f_n / d k_n =
 depth n; stick and slip derivatives; a half-space whose field is exactly linear, for the
 forces and for the depth maps; d I / d A_k = m_k; the flat-gel derivative of I w.r.t.
-the depth).
+the depth).  The image loss (shade_mse) is pinned by its value from the C oracle's
+intensities and by central differences of that value.
 """
 from __future__ import annotations
 
@@ -236,6 +237,31 @@ def shade_gradients(coeffs, pitch_x, pitch_y, sensor_id, depth, g_intensity):
         inten[b] = I.detach().numpy()
     return {"coeffs": A.grad.numpy(), "depth": g_depth, "intensity": inten}
 
+
+
+def shade_mse(coeffs, pitch_x, pitch_y, sensor_id, depth, target):
+    """Squared error of the clamped intensities against target images [B, H, W, 3]:
+    L = sum_s loss_map[s], loss_map[s, y, x] = sum over the images b of sensor s and the
+    channels c of (clamp(I_c(b, y, x), 0, 255) - target[b, y, x, c])^2 (the image loss of
+    sensor calibration, Sec. VI-A, on the intensity of reading c16).  Returns dict
+    loss_map [S, H, W], coeffs [S, 6, 3, H, W] and depth [B, H, W] (gradients of L)."""
+    coeffs = np.asarray(coeffs, np.float32)
+    S, _, _, H, W = coeffs.shape
+    depth = np.asarray(depth, np.float32).reshape(-1, H, W)
+    B = depth.shape[0]
+    T = torch.from_numpy(np.asarray(target, np.float64).reshape(B, H, W, 3))
+    A = torch.tensor(coeffs.astype(np.float64), requires_grad=True)
+    px, py = float(np.float32(pitch_x)), float(np.float32(pitch_y))
+    loss_map = np.zeros((S, H, W))
+    g_depth = np.zeros((B, H, W))
+    for b in range(B):
+        s = int(np.asarray(sensor_id).reshape(-1)[b])
+        D = torch.tensor(depth[b].astype(np.float64), requires_grad=True)
+        err = (shade_intensity(A[s], D, px, py) - T[b]) ** 2
+        loss_map[s] += err.detach().sum(dim=2).numpy()
+        err.sum().backward()
+        g_depth[b] = D.grad.numpy()
+    return {"loss_map": loss_map, "coeffs": A.grad.numpy(), "depth": g_depth}
 
 
 GRAZING = 0.05   # |d phi / dz| below this: a grazing column, whose depth gradient is left out

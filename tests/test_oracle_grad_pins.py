@@ -403,9 +403,59 @@ def check_render_central_differences(G):
         assert abs(got[j] - fd) <= tol, (j, got[j], fd, tol)
 
 
+def check_shade_mse(G):
+    """The image loss: its per-pixel map equals sum_b sum_c (I - T)^2 from the C oracle's
+    float64 intensities; its gradient w.r.t. sampled coefficients (L is quadratic in them
+    away from the clamp, so a central difference is exact up to rounding) and sampled
+    depth pixels equals central differences of that C-oracle loss."""
+    rng = np.random.default_rng(14)
+    H, W, S, B = 6, 8, 2, 4
+    px, py = 2e-4, 3e-4
+    co = synth.shading_coeffs(S, H, W, 21)
+    dm = (synth.D0 + 2e-5 * rng.normal(size=(B, H, W))).astype(np.float32)
+    sid = np.array([0, 1, 1, 0], np.int32)
+    _, inten, _ = oracle.shade(co, px, py, sid, dm, with_intensity=True)
+    tgt = inten + rng.normal(0, 20, size=inten.shape)
+    live = (inten > 0) & (inten < 255)
+    assert live.mean() > 0.5
+    r = G.shade_mse(co, px, py, sid, dm, tgt)
+    want = np.zeros((S, H, W))
+    for b in range(B):
+        want[sid[b]] += ((inten[b] - tgt[b]) ** 2).sum(-1)
+    assert np.abs(r["loss_map"] - want).max() <= 1e-9 * want.max()
+
+    def L(c, d):
+        _, i2, _ = oracle.shade(c, px, py, sid, d, with_intensity=True)
+        return float(((i2 - tgt) ** 2).sum())
+
+    checked = 0
+    for _ in range(12):
+        s_, k, c, y, x = rng.integers(S), rng.integers(6), rng.integers(3), rng.integers(H), rng.integers(W)
+        if not live[sid == s_][..., c][:, y, x].all() or checked == 4:
+            continue
+        checked += 1
+        h = 0.05
+        cp, cm = co.copy(), co.copy()
+        cp[s_, k, c, y, x] += np.float32(h)
+        cm[s_, k, c, y, x] -= np.float32(h)
+        fd = (L(cp, dm) - L(cm, dm)) / (float(cp[s_, k, c, y, x]) - float(cm[s_, k, c, y, x]))
+        got = r["coeffs"][s_, k, c, y, x]
+        assert abs(got - fd) <= 1e-6 * max(abs(fd), 1.0), (got, fd)
+    assert checked == 4
+    for _ in range(4):
+        b, y, x = rng.integers(B), rng.integers(H), rng.integers(W)
+        dp, dmn = dm.copy(), dm.copy()
+        dp[b, y, x] += np.float32(2e-7)
+        dmn[b, y, x] -= np.float32(2e-7)
+        fd = (L(co, dp) - L(co, dmn)) / (float(dp[b, y, x]) - float(dmn[b, y, x]))
+        got = r["depth"][b, y, x]
+        assert abs(got - fd) <= 2e-3 * max(abs(fd), 1e-3 * np.abs(r["depth"]).max()), (got, fd)
+
+
 CHECKS = [check_forward_matches_c_oracle, check_intensity_matches_c_oracle,
           check_force_gradients_match_central_differences, check_closed_forms_kn_kt_mu, check_half_space,
-          check_shading_closed_forms, check_render_tilted_half_space, check_render_central_differences]
+          check_shading_closed_forms, check_render_tilted_half_space, check_render_central_differences,
+          check_shade_mse]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=[c.__name__ for c in CHECKS])
@@ -432,6 +482,9 @@ MUTATIONS = {
     "render_pixel_axes": ("torch.stack([torch.tensor(xx[hit], dtype=F64), torch.tensor(yy[hit], dtype=F64), z]",
                           "torch.stack([torch.tensor(yy[hit], dtype=F64), torch.tensor(xx[hit], dtype=F64), z]"),
     "render_grazing_kept": ("keep = inside & (phi_z.abs() >= GRAZING)", "keep = inside & (phi_z.abs() >= 0.0)"),
+    "mse_target_sign": ("err = (shade_intensity(A[s], D, px, py) - T[b]) ** 2",
+                        "err = (shade_intensity(A[s], D, px, py) + T[b]) ** 2"),
+    "mse_map_sensor": ("loss_map[s] += err.detach().sum(dim=2).numpy()", "loss_map[0] += err.detach().sum(dim=2).numpy()"),
     "monomial_swap": ("m = torch.stack([torch.ones_like(nx), nx, ny, nx * nx, ny * ny, nx * ny])",
                       "m = torch.stack([torch.ones_like(nx), ny, nx, nx * nx, ny * ny, nx * ny])"),
 }
