@@ -838,7 +838,19 @@ def run_grad(args, rank, world, local_rank, dist):
     leaves = [pose, twist, *ks, coeffs]
     stream = torch.cuda.current_stream()
 
+    n_img = E * P * HW * 3
+
     def step():
+        # the image term through the fused squared-error kernel (no intensity tensor)
+        for t in leaves:
+            t.grad = None
+        _, fn, ft, _ = ta.force_field(sdfs, taxels, obj, pose, twist, *ks)
+        L_img = ta.shade_mse(coeffs, depth_map, sid, sc.pitch_x, sc.pitch_y, tI)
+        loss = ((fn - tgt[1]) ** 2).mean() + ((ft - tgt[2]) ** 2).mean() + 1e-4 * L_img / n_img
+        loss.backward()
+
+    def step_unfused():
+        # the same loss with the intensities materialised and the error taken in PyTorch
         for t in leaves:
             t.grad = None
         _, fn, ft, _ = ta.force_field(sdfs, taxels, obj, pose, twist, *ks)
@@ -866,6 +878,7 @@ def run_grad(args, rank, world, local_rank, dist):
     if dist is not None:
         dist.barrier()
     ms = max_over_ranks(timed(step, K, warm=0), dist, device="cuda")
+    ms_unfused = max_over_ranks(timed(step_unfused, K), dist, device="cuda")
     # the pose -> image chain: the images rendered from the poses (column camera) instead
     # of given depth maps, against the images of poses perturbed by 0.2 mm / 0.01 rad
     from paper_2408_06506_b300 import synth
@@ -883,6 +896,15 @@ def run_grad(args, rank, world, local_rank, dist):
             t.grad = None
         _, fn, ft, _ = ta.force_field(sdfs, taxels, obj, pose, twist, *ks)
         D = ta.render_depth(sdfs, cam, obj, pose)
+        L_img = ta.shade_mse(coeffs, D.reshape(-1, sc.H, sc.W), sid, sc.pitch_x, sc.pitch_y, tI_pose)
+        loss = ((fn - tgt[1]) ** 2).mean() + ((ft - tgt[2]) ** 2).mean() + 1e-4 * L_img / n_img
+        loss.backward()
+
+    def pose_step_unfused():
+        for t in leaves:
+            t.grad = None
+        _, fn, ft, _ = ta.force_field(sdfs, taxels, obj, pose, twist, *ks)
+        D = ta.render_depth(sdfs, cam, obj, pose)
         I = ta.shade_intensity(coeffs, D.reshape(-1, sc.H, sc.W), sid, sc.pitch_x, sc.pitch_y)
         loss = ((fn - tgt[1]) ** 2).mean() + ((ft - tgt[2]) ** 2).mean() + 1e-4 * ((I - tI_pose) ** 2).mean()
         loss.backward()
@@ -894,6 +916,7 @@ def run_grad(args, rank, world, local_rank, dist):
     if dist is not None:
         dist.barrier()
     ms_pose = max_over_ranks(timed(pose_step, K, warm=0), dist, device="cuda")
+    ms_pose_unfused = max_over_ranks(timed(pose_step_unfused, K), dist, device="cuda")
     # the kernels alone: forward force field and intensity, and their adjoints for fixed
     # upstream gradients
     params = tacsl.ContactParams(*[k.detach() for k in ks])
@@ -921,6 +944,13 @@ def run_grad(args, rank, world, local_rank, dist):
             C.byref(shading.c), E * P, tacsl._ptr(sid), tacsl._ptr(depth_map), tacsl._ptr(gI), tacsl._ptr(gc), None,
             None), 5),
     }
+    lmap = torch.empty(coeffs.shape[0], sc.H, sc.W, device="cuda")
+    k_ms["shade_mse_kernel (loss map)"] = timed(lambda: lib.tacsl_shade_mse(
+        C.byref(shading.c), E * P, tacsl._ptr(sid), tacsl._ptr(depth_map), tacsl._ptr(tI), None, tacsl._ptr(lmap),
+        None, None, None), 5)
+    k_ms["shade_mse_kernel (loss map + coefficient gradient)"] = timed(lambda: lib.tacsl_shade_mse(
+        C.byref(shading.c), E * P, tacsl._ptr(sid), tacsl._ptr(depth_map), tacsl._ptr(tI), None, tacsl._ptr(lmap),
+        tacsl._ptr(gc), None, None), 5)
     del gI
     rendered = tacsl.render_depth(sdfs, cam, obj, pz)
     gD = torch.randn(E, P, sc.H, sc.W, device="cuda")
@@ -942,21 +972,31 @@ def run_grad(args, rank, world, local_rank, dist):
     # columns (4 B per hit), each pad's pose, and writes its gradient (56 B/pad); the SDF
     # cells of hit columns come from L2 (the grids are resident) and are not counted
     radj_bytes = 4 * npx + 4 * n_hit + 56 * E * P
+    # the fused loss reads the depth (4 B/px) and the target (12 B/px), the coefficients
+    # once, and writes the loss map (and the coefficient gradient) once
+    mse_bytes = 16 * npx + coef_bytes + coef_bytes // 18
     return {
         "workload": GRAD_WORKLOAD, "envs_per_gpu": E, "steps": K,
         "ms_per_step": ms, "unit": "taxel-points/s", "value": world * E * P * T / (ms * 1e-3),
         "images_per_s": world * E * P / (ms * 1e-3),
-        "path": "force_field + shade_intensity (torch.autograd.Function over the C ABI), MSE in torch, backward",
+        "path": "force_field + shade_mse (torch.autograd.Function over the C ABI; fused image loss), force MSE "
+                "in torch, backward",
+        "unfused": {"ms_per_step": ms_unfused, "value": world * E * P * T / (ms_unfused * 1e-3),
+                    "path": "shade_intensity, then ((I - target)^2).mean() in torch", "gpu_launches_per_step": 4},
         "pose_chain": {"ms_per_step": ms_pose, "value": world * E * P * T / (ms_pose * 1e-3),
                        "images_per_s": world * E * P / (ms_pose * 1e-3), "gpu_launches_per_step": 7,
-                       "path": "force_field + render_depth -> shade_intensity (images from the poses), MSE, "
-                               "backward to pose, twist, contact parameters and coefficients"},
+                       "unfused_ms_per_step": ms_pose_unfused,
+                       "path": "force_field + render_depth -> shade_mse (images from the poses), backward to pose, "
+                               "twist, contact parameters and coefficients"},
         "kernel_ms": k_ms,
         "roofline": {
             "shade_intensity_kernel": {"algorithmic_bytes": inten_bytes,
                                        "frac": inten_bytes / (k_ms["shade_intensity_kernel"] * 1e-3) / 1e9 / peak},
             "shade_coeff_grad_kernel": {"algorithmic_bytes": cgrad_bytes,
                                         "frac": cgrad_bytes / (k_ms["shade_coeff_grad_kernel"] * 1e-3) / 1e9 / peak},
+            "shade_mse_kernel (loss map)": {
+                "algorithmic_bytes": mse_bytes,
+                "frac": mse_bytes / (k_ms["shade_mse_kernel (loss map)"] * 1e-3) / 1e9 / peak},
             "render_adjoint_kernel": {"algorithmic_bytes": radj_bytes, "hit_columns": n_hit,
                                       "frac": radj_bytes / (k_ms["render_adjoint_kernel"] * 1e-3) / 1e9 / peak},
             "peak_gbs": peak},

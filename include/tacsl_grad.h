@@ -55,6 +55,21 @@ int tacsl_shade_adjoint(const tacsl_shading* shading, int64_t B, const int32_t* 
                         const float* depth_map, const float* g_intensity, float* grad_coeffs,
                         float* grad_depth, tacsl_stream_t stream);
 
+/* Squared error of the clamped intensities against target images, and its gradient,
+ * without writing the intensities (the image loss of sensor calibration: fitting the
+ * shading model and the depth maps to observed images):
+ *   loss_map [S][H][W] (device, may be NULL): for each sensor s and pixel, the sum over
+ *     the images b with sensor_id[b] = s, in image order, and the channels c of
+ *     (clamp(I_c(b, y, x), 0, 255) - target[b][y][x][c])^2;
+ *   with L = scale * sum(loss_map) (scale: device float[1], NULL = 1), grad_coeffs
+ *     [S][6][3][H][W] and grad_depth [B][H][W] (device, may be NULL) receive dL/dA and
+ *     dL/dD as tacsl_shade_adjoint gives them for dL/dI = 2 scale (clamp(I) - target).
+ * target [B][H][W][3] (device) in the layout of tacsl_shade_intensity's output.  An image
+ * with a bad sensor_id contributes nothing (its grad_depth is zero). */
+int tacsl_shade_mse(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id, const float* depth_map,
+                    const float* target, const float* scale, float* loss_map, float* grad_coeffs,
+                    float* grad_depth, tacsl_stream_t stream);
+
 /* Adjoint of tacsl_render_depth w.r.t. the pad poses (the pose -> depth -> image chain;
  * same set, E, P, obj_id, pad_pose, camera).  depth_map [E*P][H][W] (device, 16-byte
  * aligned) is the render of these poses and g_depth [E*P][H][W] (device) the upstream

@@ -1,7 +1,7 @@
 """torch.autograd bindings of the tactile step's adjoint kernels (``include/tacsl_grad.h``).
 
-``force_field``, ``shade_intensity`` and ``render_depth`` behave like differentiable torch
-functions:
+``force_field``, ``shade_intensity``, ``shade_mse`` and ``render_depth`` behave like
+differentiable torch functions:
 their forward runs the library's forward kernels and their backward the hand-written
 adjoint kernels, so a calibration loss over force fields, wrenches and images can be
 minimised with any torch optimiser over pad poses, twists, contact parameters and
@@ -32,6 +32,8 @@ def _lib():
         lib.tacsl_shade_intensity.argtypes = [C.POINTER(_Shading), I64, P, P, P, P]
         lib.tacsl_shade_adjoint.restype = C.c_int
         lib.tacsl_shade_adjoint.argtypes = [C.POINTER(_Shading), I64, P, P, P, P, P, P]
+        lib.tacsl_shade_mse.restype = C.c_int
+        lib.tacsl_shade_mse.argtypes = [C.POINTER(_Shading), I64, P, P, P, P, P, P, P, P]
         lib.tacsl_render_depth_adjoint.restype = C.c_int
         lib.tacsl_render_depth_adjoint.argtypes = [C.POINTER(_SdfSet), I32, I32, P, P, C.POINTER(_Camera), P, P, P, P]
         _bound = True
@@ -117,6 +119,45 @@ def shade_intensity(coeffs, depth_map, sensor_id, pitch_x, pitch_y):
     _dev(depth_map.detach(), torch.float32, "depth_map")
     _dev(sensor_id, torch.int32, "sensor_id")
     return _ShadeIntensity.apply(coeffs, depth_map, sensor_id, float(pitch_x), float(pitch_y))
+
+
+class _ShadeMse(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, coeffs, depth_map, sensor_id, target, pitch_x, pitch_y):
+        S, _, _, H, W = coeffs.shape
+        B = depth_map.numel() // (H * W)
+        sh = Shading(coeffs.detach().contiguous(), pitch_x, pitch_y)
+        loss_map = torch.empty(S, H, W, dtype=torch.float32, device=depth_map.device)
+        _check(_lib().tacsl_shade_mse(C.byref(sh.c), B, _ptr(sensor_id), _ptr(depth_map.detach()), _ptr(target),
+                                      None, _ptr(loss_map), None, None, _stream(None)))
+        ctx.save_for_backward(coeffs, depth_map, sensor_id, target)
+        ctx.pitch = (pitch_x, pitch_y)
+        return loss_map.sum()
+
+    @staticmethod
+    def backward(ctx, g):
+        coeffs, depth_map, sensor_id, target = ctx.saved_tensors
+        need = ctx.needs_input_grad
+        S, _, _, H, W = coeffs.shape
+        B = depth_map.numel() // (H * W)
+        sh = Shading(coeffs.detach().contiguous(), *ctx.pitch)
+        gc = torch.empty_like(coeffs) if need[0] else None
+        gd = torch.empty(depth_map.shape, dtype=torch.float32, device=depth_map.device) if need[1] else None
+        scale = g.reshape(1).to(torch.float32).contiguous()
+        _check(_lib().tacsl_shade_mse(C.byref(sh.c), B, _ptr(sensor_id), _ptr(depth_map.detach()), _ptr(target),
+                                      _ptr(scale), None, _ptr(gc), _ptr(gd), _stream(None)))
+        return gc, gd, None, None, None, None
+
+
+def shade_mse(coeffs, depth_map, sensor_id, pitch_x, pitch_y, target):
+    """Differentiable squared error sum((clamp(I) - target)^2) over the B images [B, H, W]
+    against target intensities [B, H, W, 3], without materialising I (one fused pass
+    forward, two backward); gradients flow to coeffs and depth_map."""
+    _dev(coeffs.detach(), torch.float32, "coeffs")
+    _dev(depth_map.detach(), torch.float32, "depth_map")
+    _dev(sensor_id, torch.int32, "sensor_id")
+    _dev(target, torch.float32, "target")
+    return _ShadeMse.apply(coeffs, depth_map, sensor_id, target.contiguous(), float(pitch_x), float(pitch_y))
 
 
 def render_depth_adjoint(sdfs: SdfSet, camera: Camera, obj_id, pad_pose, depth_map, g_depth, grad_pose=None,

@@ -489,9 +489,12 @@ __global__ void __launch_bounds__(256) flag_bad_sensors_kernel(int64_t B, int S,
     }
 }
 
-// dL/dm_k at one pixel for upstream g[3], and (dL/dD_x, dL/dD_y) through the normal.
-__device__ __forceinline__ void pixel_backward(const float* A, int64_t HW, const PixelState& st, const float g[3],
-                                               float gm[6], float& gDx, float& gDy) {
+// dL/dm_k at one pixel, and (dL/dD_x, dL/dD_y) through the normal.  kMse = false: u[3]
+// is the upstream gradient dL/dI; kMse = true: u[3] is the target intensity and the
+// upstream gradient is w2 (I - u) (a squared error scaled by w2 / 2).
+template <bool kMse>
+__device__ __forceinline__ void pixel_backward(const float* A, int64_t HW, const PixelState& st, const float u[3],
+                                               float w2, float gm[6], float& gDx, float& gDy) {
     const float m[6] = {1.f, st.nx, st.ny, st.nx * st.nx, st.ny * st.ny, st.nx * st.ny};
 #pragma unroll
     for (int kk = 0; kk < 6; ++kk) gm[kk] = 0.f;
@@ -504,8 +507,9 @@ __device__ __forceinline__ void pixel_backward(const float* A, int64_t HW, const
             I = fmaf(a[kk], m[kk], I);
         }
         if (I > 0.f && I < 255.f) {            // the clamp passes the gradient only inside
+            const float gc = kMse ? w2 * (I - u[c]) : u[c];
 #pragma unroll
-            for (int kk = 0; kk < 6; ++kk) gm[kk] = fmaf(g[c], a[kk], gm[kk]);
+            for (int kk = 0; kk < 6; ++kk) gm[kk] = fmaf(gc, a[kk], gm[kk]);
         }
     }
     const float gnx = fmaf(2.f * st.nx, gm[3], fmaf(st.ny, gm[5], gm[1]));
@@ -519,18 +523,26 @@ __device__ __forceinline__ void pixel_backward(const float* A, int64_t HW, const
 // dL/dA[s][k][c][px] = sum over images b of sensor s of g[b][px][c] m_k(b, px) (where the
 // clamp passes).  Grid (pixel tiles, sensors); each warp sums its slice of the images in
 // order and the eight partial sums are added in warp order (deterministic).
+// kMse = false: g is read from u = dL/dI.  kMse = true: u is the target intensity, g =
+// w2 (I - u), and loss_map[s][px] (if not NULL) receives sum_b sum_c (clamp(I) - u)^2 in
+// the same order; grad_coeffs may then be NULL.
+template <bool kMse>
 __global__ void __launch_bounds__(256) shade_coeff_grad_kernel(ShadeGeom G, int64_t B, const float* __restrict__ coeffs,
                                                                 const int32_t* __restrict__ sensor_id,
                                                                 const float* __restrict__ depth,
-                                                                const float* __restrict__ g_inten,
-                                                                float* __restrict__ grad_coeffs) {
-    __shared__ float part[kImgWarps][18][kPxTile];
+                                                                const float* __restrict__ u_inten,
+                                                                const float* __restrict__ scale,
+                                                                float* __restrict__ grad_coeffs,
+                                                                float* __restrict__ loss_map) {
+    constexpr int kTerms = kMse ? 19 : 18;
+    __shared__ float part[kImgWarps][kTerms][kPxTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s = blockIdx.y;
     const int64_t px = static_cast<int64_t>(blockIdx.x) * kPxTile + lane;
     const bool valid = px < G.HW;
     const int y = valid ? static_cast<int>(px / G.W) : 0, x = valid ? static_cast<int>(px - static_cast<int64_t>(y) * G.W) : 0;
-    float a[6][3], acc[6][3];
+    const float w2 = kMse ? 2.f * (scale != nullptr ? __ldg(scale) : 1.f) : 1.f;
+    float a[6][3], acc[6][3], lacc = 0.f;
 #pragma unroll
     for (int kk = 0; kk < 6; ++kk)
 #pragma unroll
@@ -548,8 +560,8 @@ __global__ void __launch_bounds__(256) shade_coeff_grad_kernel(ShadeGeom G, int6
         float g0[3], g1[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            g0[c] = __ldg(g_inten + (b0 * G.HW + px) * 3 + c);
-            g1[c] = b1 >= 0 ? __ldg(g_inten + (bb1 * G.HW + px) * 3 + c) : 0.f;
+            g0[c] = __ldg(u_inten + (b0 * G.HW + px) * 3 + c);
+            g1[c] = b1 >= 0 ? __ldg(u_inten + (bb1 * G.HW + px) * 3 + c) : 0.f;
         }
 #pragma unroll
         for (int i = 0; i < 2; ++i) {          // image b0, then b1: the summation order is the image order
@@ -561,8 +573,13 @@ __global__ void __launch_bounds__(256) shade_coeff_grad_kernel(ShadeGeom G, int6
                 float I = 0.f;
 #pragma unroll
                 for (int kk = 0; kk < 6; ++kk) I = fmaf(a[kk][c], m[kk], I);
+                const float uc = i ? g1[c] : g0[c];
+                if (kMse) {
+                    const float e = fminf(fmaxf(I, 0.f), 255.f) - uc;
+                    lacc = fmaf(e, e, lacc);
+                }
                 if (I > 0.f && I < 255.f) {
-                    const float gc = i ? g1[c] : g0[c];
+                    const float gc = kMse ? w2 * (I - uc) : uc;
 #pragma unroll
                     for (int kk = 0; kk < 6; ++kk) acc[kk][c] = fmaf(gc, m[kk], acc[kk][c]);
                 }
@@ -573,28 +590,37 @@ __global__ void __launch_bounds__(256) shade_coeff_grad_kernel(ShadeGeom G, int6
     for (int kk = 0; kk < 6; ++kk)
 #pragma unroll
         for (int c = 0; c < 3; ++c) part[warp][kk * 3 + c][lane] = acc[kk][c];
+    if (kMse) part[warp][kTerms - 1][lane] = lacc;
     __syncthreads();
-    // 18 x 32 sums over the 8 warps, in warp order; 256 threads take them in turn
-    for (int i = threadIdx.x; i < 18 * kPxTile; i += blockDim.x) {
+    // kTerms x 32 sums over the 8 warps, in warp order; 256 threads take them in turn
+    for (int i = threadIdx.x; i < kTerms * kPxTile; i += blockDim.x) {
         const int term = i / kPxTile, l = i - term * kPxTile;
         const int64_t p = static_cast<int64_t>(blockIdx.x) * kPxTile + l;
         if (p >= G.HW) continue;
         float sum = 0.f;
 #pragma unroll
         for (int w = 0; w < kImgWarps; ++w) sum += part[w][term][l];
-        grad_coeffs[(static_cast<int64_t>(s) * 18 + term) * G.HW + p] = sum;
+        if (term < 18) {
+            if (grad_coeffs != nullptr) grad_coeffs[(static_cast<int64_t>(s) * 18 + term) * G.HW + p] = sum;
+        } else if (loss_map != nullptr) {
+            loss_map[static_cast<int64_t>(s) * G.HW + p] = sum;
+        }
     }
 }
 
 // dL/dD[b][p]: the transpose of the difference stencils, gathered from the pixels q whose
 // D_x (q in p's row, |q - p| <= 1) or D_y (q in p's column) reads D[p].
+// kMse as for shade_coeff_grad_kernel (u = dL/dI, or the target with g = w2 (I - u)).
+template <bool kMse>
 __global__ void __launch_bounds__(128) shade_depth_grad_kernel(ShadeGeom G, int64_t B, const float* __restrict__ coeffs,
                                                                 const int32_t* __restrict__ sensor_id,
                                                                 const float* __restrict__ depth,
-                                                                const float* __restrict__ g_inten,
+                                                                const float* __restrict__ u_inten,
+                                                                const float* __restrict__ scale,
                                                                 float* __restrict__ grad_depth) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= G.W) return;
+    const float w2 = kMse ? 2.f * (scale != nullptr ? __ldg(scale) : 1.f) : 1.f;
     const int64_t px = static_cast<int64_t>(y) * G.W + x;
     for (int64_t b = blockIdx.z; b < B; b += gridDim.z) {
         const int64_t k = b * G.HW + px;
@@ -605,7 +631,7 @@ __global__ void __launch_bounds__(128) shade_depth_grad_kernel(ShadeGeom G, int6
         }
         const float* D = depth + b * G.HW;
         const float* Ab = coeffs + static_cast<int64_t>(s) * 18 * G.HW;
-        const float* gI = g_inten + b * G.HW * 3;
+        const float* gI = u_inten + b * G.HW * 3;
         float acc = 0.f;
         // row neighbours: D_x(q) for q = (x + dq, y)
         for (int dq = -1; dq <= 1; ++dq) {
@@ -620,7 +646,7 @@ __global__ void __launch_bounds__(128) shade_depth_grad_kernel(ShadeGeom G, int6
             const PixelState st = pixel_state(D, G, qx, y);
             const float g[3] = {__ldg(gI + q * 3), __ldg(gI + q * 3 + 1), __ldg(gI + q * 3 + 2)};
             float gm[6], gDx, gDy;
-            pixel_backward(Ab + q, G.HW, st, g, gm, gDx, gDy);
+            pixel_backward<kMse>(Ab + q, G.HW, st, g, w2, gm, gDx, gDy);
             acc = fmaf(w, gDx, acc);
         }
         // column neighbours: D_y(q) for q = (x, y + dq)
@@ -636,7 +662,7 @@ __global__ void __launch_bounds__(128) shade_depth_grad_kernel(ShadeGeom G, int6
             const PixelState st = pixel_state(D, G, x, qy);
             const float g[3] = {__ldg(gI + q * 3), __ldg(gI + q * 3 + 1), __ldg(gI + q * 3 + 2)};
             float gm[6], gDx, gDy;
-            pixel_backward(Ab + q, G.HW, st, g, gm, gDx, gDy);
+            pixel_backward<kMse>(Ab + q, G.HW, st, g, w2, gm, gDx, gDy);
             acc = fmaf(w, gDy, acc);
         }
         grad_depth[k] = acc;

@@ -167,6 +167,7 @@ int check_shade_args(const tacsl_shading* sh, int64_t B, const int32_t* sensor_i
         return fail(TACSL_ERR_INVALID_ARG, "pixel pitch must be positive and finite");
     if (sh->coeffs == nullptr || !aligned(sh->coeffs, 16))
         return fail(TACSL_ERR_INVALID_ARG, "shading coeffs must be non-NULL and 16-byte aligned");
+    if (B == 0) return TACSL_OK;          // no images: the per-image arrays are not read
     if (sensor_id == nullptr || !aligned(sensor_id, 4))
         return fail(TACSL_ERR_INVALID_ARG, "sensor_id must be non-NULL and 4-byte aligned");
     if (depth_map == nullptr || !aligned(depth_map, 16))
@@ -1256,14 +1257,48 @@ int tacsl_shade_adjoint(const tacsl_shading* shading, int64_t B, const int32_t* 
     if (grad_coeffs != nullptr) {
         const int64_t tiles = (G.HW + kPxTile - 1) / kPxTile;
         if (tiles > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "image too large");
-        shade_coeff_grad_kernel<<<dim3(static_cast<unsigned>(tiles), static_cast<unsigned>(G.S)), 256, 0, stream>>>(
-            G, B, shading->coeffs, sensor_id, depth_map, g_intensity, grad_coeffs);
+        shade_coeff_grad_kernel<false><<<dim3(static_cast<unsigned>(tiles), static_cast<unsigned>(G.S)), 256, 0,
+                                         stream>>>(G, B, shading->coeffs, sensor_id, depth_map, g_intensity, nullptr,
+                                                   grad_coeffs, nullptr);
         if ((rc = check_launch("tacsl_shade_adjoint (coefficients)"))) return rc;
     }
     if (grad_depth != nullptr && B > 0) {
-        shade_depth_grad_kernel<<<pixel_grid(G, B), 128, 0, stream>>>(G, B, shading->coeffs, sensor_id, depth_map,
-                                                                       g_intensity, grad_depth);
+        shade_depth_grad_kernel<false><<<pixel_grid(G, B), 128, 0, stream>>>(G, B, shading->coeffs, sensor_id,
+                                                                              depth_map, g_intensity, nullptr,
+                                                                              grad_depth);
         if ((rc = check_launch("tacsl_shade_adjoint (depth)"))) return rc;
+    }
+    return ok();
+}
+
+int tacsl_shade_mse(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id, const float* depth_map,
+                    const float* target, const float* scale, float* loss_map, float* grad_coeffs, float* grad_depth,
+                    tacsl_stream_t stream) {
+    const bool per_sensor = loss_map != nullptr || grad_coeffs != nullptr;
+    if (shading != nullptr && B == 0 && !per_sensor) return ok();
+    // the image checks of tacsl_shade_image, with the target in the place of the output
+    int rc = check_shade_args(shading, B, sensor_id, depth_map, reinterpret_cast<const uint8_t*>(target));
+    if (rc) return rc;
+    if (!aligned(target, 4) || !aligned(scale, 4) || !aligned(loss_map, 4) || !aligned(grad_coeffs, 4) ||
+        !aligned(grad_depth, 4))
+        return fail(TACSL_ERR_INVALID_ARG, "target, scale, loss_map and gradient arrays must be 4-byte aligned");
+    if (shading->H > 65535) return fail(TACSL_ERR_UNSUPPORTED, "image height %d > 65535", shading->H);
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    ShadeGeom G;
+    shade_geom(shading, G);
+    if (per_sensor) {
+        const int64_t tiles = (G.HW + kPxTile - 1) / kPxTile;
+        if (tiles > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "image too large");
+        shade_coeff_grad_kernel<true><<<dim3(static_cast<unsigned>(tiles), static_cast<unsigned>(G.S)), 256, 0,
+                                        stream>>>(G, B, shading->coeffs, sensor_id, depth_map, target, scale,
+                                                  grad_coeffs, loss_map);
+        if ((rc = check_launch("tacsl_shade_mse (loss map / coefficients)"))) return rc;
+    }
+    if (grad_depth != nullptr && B > 0) {
+        shade_depth_grad_kernel<true><<<pixel_grid(G, B), 128, 0, stream>>>(G, B, shading->coeffs, sensor_id,
+                                                                             depth_map, target, scale, grad_depth);
+        if ((rc = check_launch("tacsl_shade_mse (depth)"))) return rc;
     }
     return ok();
 }
