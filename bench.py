@@ -879,6 +879,25 @@ def run_grad(args, rank, world, local_rank, dist):
         dist.barrier()
     ms = max_over_ranks(timed(step, K, warm=0), dist, device="cuda")
     ms_unfused = max_over_ranks(timed(step_unfused, K), dist, device="cuda")
+
+    def captured(fn):
+        # whole-step capture (forward and backward) after warm-up on a side stream; the
+        # gradients then live in the graph's memory and are rewritten by every replay
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                fn()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            fn()
+        return graph
+
+    g_step = captured(step)
+    ms_graph = max_over_ranks(timed(g_step.replay, K), dist, device="cuda")
+    assert tacsl.check_errors() == 0
     # the pose -> image chain: the images rendered from the poses (column camera) instead
     # of given depth maps, against the images of poses perturbed by 0.2 mm / 0.01 rad
     from paper_2408_06506_b300 import synth
@@ -917,6 +936,10 @@ def run_grad(args, rank, world, local_rank, dist):
         dist.barrier()
     ms_pose = max_over_ranks(timed(pose_step, K, warm=0), dist, device="cuda")
     ms_pose_unfused = max_over_ranks(timed(pose_step_unfused, K), dist, device="cuda")
+    g_pose = captured(pose_step)
+    ms_pose_graph = max_over_ranks(timed(g_pose.replay, K), dist, device="cuda")
+    assert tacsl.check_errors() == 0 and torch.isfinite(pose.grad).all()
+    del g_step, g_pose
     # the kernels alone: forward force field and intensity, and their adjoints for fixed
     # upstream gradients
     params = tacsl.ContactParams(*[k.detach() for k in ks])
@@ -951,7 +974,11 @@ def run_grad(args, rank, world, local_rank, dist):
     k_ms["shade_mse_kernel (loss map + coefficient gradient)"] = timed(lambda: lib.tacsl_shade_mse(
         C.byref(shading.c), E * P, tacsl._ptr(sid), tacsl._ptr(depth_map), tacsl._ptr(tI), None, tacsl._ptr(lmap),
         tacsl._ptr(gc), None, None), 5)
-    del gI
+    gdep = torch.empty(E * P, sc.H, sc.W, device="cuda")
+    k_ms["shade_mse_kernel (depth gradient)"] = timed(lambda: lib.tacsl_shade_mse(
+        C.byref(shading.c), E * P, tacsl._ptr(sid), tacsl._ptr(depth_map), tacsl._ptr(tI), None, None, None,
+        tacsl._ptr(gdep), None), 5)
+    del gI, gdep
     rendered = tacsl.render_depth(sdfs, cam, obj, pz)
     gD = torch.randn(E, P, sc.H, sc.W, device="cuda")
     k_ms["render_kernel"] = timed(lambda: tacsl.render_depth(sdfs, cam, obj, pz, depth_map=rendered), 10)
@@ -981,11 +1008,14 @@ def run_grad(args, rank, world, local_rank, dist):
         "images_per_s": world * E * P / (ms * 1e-3),
         "path": "force_field + shade_mse (torch.autograd.Function over the C ABI; fused image loss), force MSE "
                 "in torch, backward",
+        "graph": {"ms_per_step": ms_graph, "value": world * E * P * T / (ms_graph * 1e-3),
+                  "images_per_s": world * E * P / (ms_graph * 1e-3),
+                  "path": "the same step (forward and backward) captured once in a CUDA graph and replayed"},
         "unfused": {"ms_per_step": ms_unfused, "value": world * E * P * T / (ms_unfused * 1e-3),
                     "path": "shade_intensity, then ((I - target)^2).mean() in torch", "gpu_launches_per_step": 4},
         "pose_chain": {"ms_per_step": ms_pose, "value": world * E * P * T / (ms_pose * 1e-3),
                        "images_per_s": world * E * P / (ms_pose * 1e-3), "gpu_launches_per_step": 7,
-                       "unfused_ms_per_step": ms_pose_unfused,
+                       "unfused_ms_per_step": ms_pose_unfused, "graph_ms_per_step": ms_pose_graph,
                        "path": "force_field + render_depth -> shade_mse (images from the poses), backward to pose, "
                                "twist, contact parameters and coefficients"},
         "kernel_ms": k_ms,
@@ -997,6 +1027,9 @@ def run_grad(args, rank, world, local_rank, dist):
             "shade_mse_kernel (loss map)": {
                 "algorithmic_bytes": mse_bytes,
                 "frac": mse_bytes / (k_ms["shade_mse_kernel (loss map)"] * 1e-3) / 1e9 / peak},
+            "shade_mse_kernel (depth gradient)": {
+                "algorithmic_bytes": mse_bytes + 4 * npx,
+                "frac": (mse_bytes + 4 * npx) / (k_ms["shade_mse_kernel (depth gradient)"] * 1e-3) / 1e9 / peak},
             "render_adjoint_kernel": {"algorithmic_bytes": radj_bytes, "hit_columns": n_hit,
                                       "frac": radj_bytes / (k_ms["render_adjoint_kernel"] * 1e-3) / 1e9 / peak},
             "peak_gbs": peak},

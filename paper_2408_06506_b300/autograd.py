@@ -128,9 +128,13 @@ class _ShadeMse(torch.autograd.Function):
         B = depth_map.numel() // (H * W)
         sh = Shading(coeffs.detach().contiguous(), pitch_x, pitch_y)
         loss_map = torch.empty(S, H, W, dtype=torch.float32, device=depth_map.device)
+        # the coefficient gradient costs the loss pass nothing extra: take it here (for a
+        # unit upstream gradient) and scale it in backward
+        gc = torch.empty_like(coeffs) if coeffs.requires_grad else None
         _check(_lib().tacsl_shade_mse(C.byref(sh.c), B, _ptr(sensor_id), _ptr(depth_map.detach()), _ptr(target),
-                                      None, _ptr(loss_map), None, None, _stream(None)))
+                                      None, _ptr(loss_map), _ptr(gc), None, _stream(None)))
         ctx.save_for_backward(coeffs, depth_map, sensor_id, target)
+        ctx.gc = gc
         ctx.pitch = (pitch_x, pitch_y)
         return loss_map.sum()
 
@@ -140,19 +144,23 @@ class _ShadeMse(torch.autograd.Function):
         need = ctx.needs_input_grad
         S, _, _, H, W = coeffs.shape
         B = depth_map.numel() // (H * W)
-        sh = Shading(coeffs.detach().contiguous(), *ctx.pitch)
-        gc = torch.empty_like(coeffs) if need[0] else None
-        gd = torch.empty(depth_map.shape, dtype=torch.float32, device=depth_map.device) if need[1] else None
-        scale = g.reshape(1).to(torch.float32).contiguous()
-        _check(_lib().tacsl_shade_mse(C.byref(sh.c), B, _ptr(sensor_id), _ptr(depth_map.detach()), _ptr(target),
-                                      _ptr(scale), None, _ptr(gc), _ptr(gd), _stream(None)))
+        gc = ctx.gc * g if need[0] and ctx.gc is not None else None
+        gd = None
+        if need[1]:
+            sh = Shading(coeffs.detach().contiguous(), *ctx.pitch)
+            gd = torch.empty(depth_map.shape, dtype=torch.float32, device=depth_map.device)
+            scale = g.reshape(1).to(torch.float32).contiguous()
+            _check(_lib().tacsl_shade_mse(C.byref(sh.c), B, _ptr(sensor_id), _ptr(depth_map.detach()), _ptr(target),
+                                          _ptr(scale), None, None, _ptr(gd), _stream(None)))
+        ctx.gc = None
         return gc, gd, None, None, None, None
 
 
 def shade_mse(coeffs, depth_map, sensor_id, pitch_x, pitch_y, target):
     """Differentiable squared error sum((clamp(I) - target)^2) over the B images [B, H, W]
-    against target intensities [B, H, W, 3], without materialising I (one fused pass
-    forward, two backward); gradients flow to coeffs and depth_map."""
+    against target intensities [B, H, W, 3], without materialising I: one fused pass
+    forward (which also takes the coefficient gradient when coeffs require grad) and one
+    backward for the depth gradient; gradients flow to coeffs and depth_map."""
     _dev(coeffs.detach(), torch.float32, "coeffs")
     _dev(depth_map.detach(), torch.float32, "depth_map")
     _dev(sensor_id, torch.int32, "sensor_id")

@@ -489,37 +489,6 @@ __global__ void __launch_bounds__(256) flag_bad_sensors_kernel(int64_t B, int S,
     }
 }
 
-// dL/dm_k at one pixel, and (dL/dD_x, dL/dD_y) through the normal.  kMse = false: u[3]
-// is the upstream gradient dL/dI; kMse = true: u[3] is the target intensity and the
-// upstream gradient is w2 (I - u) (a squared error scaled by w2 / 2).
-template <bool kMse>
-__device__ __forceinline__ void pixel_backward(const float* A, int64_t HW, const PixelState& st, const float u[3],
-                                               float w2, float gm[6], float& gDx, float& gDy) {
-    const float m[6] = {1.f, st.nx, st.ny, st.nx * st.nx, st.ny * st.ny, st.nx * st.ny};
-#pragma unroll
-    for (int kk = 0; kk < 6; ++kk) gm[kk] = 0.f;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float a[6], I = 0.f;
-#pragma unroll
-        for (int kk = 0; kk < 6; ++kk) {
-            a[kk] = __ldg(A + (kk * 3 + c) * HW);
-            I = fmaf(a[kk], m[kk], I);
-        }
-        if (I > 0.f && I < 255.f) {            // the clamp passes the gradient only inside
-            const float gc = kMse ? w2 * (I - u[c]) : u[c];
-#pragma unroll
-            for (int kk = 0; kk < 6; ++kk) gm[kk] = fmaf(gc, a[kk], gm[kk]);
-        }
-    }
-    const float gnx = fmaf(2.f * st.nx, gm[3], fmaf(st.ny, gm[5], gm[1]));
-    const float gny = fmaf(2.f * st.ny, gm[4], fmaf(st.nx, gm[5], gm[2]));
-    // n_x = D_x r, n_y = D_y r, r = (1 + D_x^2 + D_y^2)^(-1/2)
-    const float r3 = st.r * st.r * st.r;
-    gDx = gnx * (st.r - st.dx * st.dx * r3) - gny * st.dx * st.dy * r3;
-    gDy = gny * (st.r - st.dy * st.dy * r3) - gnx * st.dx * st.dy * r3;
-}
-
 // dL/dA[s][k][c][px] = sum over images b of sensor s of g[b][px][c] m_k(b, px) (where the
 // clamp passes).  Grid (pixel tiles, sensors); each warp sums its slice of the images in
 // order and the eight partial sums are added in warp order (deterministic).
@@ -609,63 +578,199 @@ __global__ void __launch_bounds__(256) shade_coeff_grad_kernel(ShadeGeom G, int6
 }
 
 // dL/dD[b][p]: the transpose of the difference stencils, gathered from the pixels q whose
-// D_x (q in p's row, |q - p| <= 1) or D_y (q in p's column) reads D[p].
-// kMse as for shade_coeff_grad_kernel (u = dL/dI, or the target with g = w2 (I - u)).
+// D_x (q in p's row, |q - p| <= 1) or D_y (q in p's column) reads D[p].  Along each axis
+// at most two such q carry a nonzero weight (central inside; one-sided on the border), so
+// a pixel has at most four "slots" (q, axis, weight); their coefficients are kept in
+// registers while the warps walk the sensor's images (grid and image split as in
+// shade_coeff_grad_kernel).  Images with a bad sensor id are zeroed by
+// zero_bad_sensor_images_kernel.
+struct DepthSlot {
+    int qx, qy;
+    float w;       // weight of D[p] in D_x(q) (axis 0) or D_y(q) (axis 1); 0 = unused
+};
+
+// The weight of D[me] in the derivative at c along an axis of length len.
+__device__ __forceinline__ float stencil_weight(int c, int me, int len, float pitch) {
+    int lo, hi;
+    float cc;
+    axis_stencil(c, len, pitch, lo, hi, cc);
+    return (hi == me ? cc : 0.f) - (lo == me ? cc : 0.f);
+}
+
+// Per axis the two pixels whose derivative can read D[p]: the left one (x - 1, or p
+// itself on the left border) and the right one (x + 1, or p itself on the right border);
+// every other pixel's stencil misses p.
+__device__ __forceinline__ void depth_slots(const ShadeGeom& G, int x, int y, DepthSlot (&sl)[4]) {
+    const int xl = x >= 1 ? x - 1 : x, xr = x + 1 < G.W ? x + 1 : x;
+    const int yl = y >= 1 ? y - 1 : y, yr = y + 1 < G.H ? y + 1 : y;
+    sl[0] = DepthSlot{xl, y, stencil_weight(xl, x, G.W, G.px)};
+    sl[1] = DepthSlot{xr, y, xr != xl ? stencil_weight(xr, x, G.W, G.px) : 0.f};
+    sl[2] = DepthSlot{x, yl, stencil_weight(yl, y, G.H, G.py)};
+    sl[3] = DepthSlot{x, yr, yr != yl ? stencil_weight(yr, y, G.H, G.py) : 0.f};
+}
+
+// (dL/dD_x, dL/dD_y) at one pixel from its coefficients a[k][c] (registers), its state
+// and u (dL/dI, or the target when kMse).
 template <bool kMse>
-__global__ void __launch_bounds__(128) shade_depth_grad_kernel(ShadeGeom G, int64_t B, const float* __restrict__ coeffs,
+__device__ __forceinline__ void pixel_backward_reg(const float (&a)[6][3], const PixelState& st, const float u[3],
+                                                   float w2, float& gDx, float& gDy) {
+    const float m[6] = {1.f, st.nx, st.ny, st.nx * st.nx, st.ny * st.ny, st.nx * st.ny};
+    float gm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float I = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 6; ++kk) I = fmaf(a[kk][c], m[kk], I);
+        if (I > 0.f && I < 255.f) {
+            const float gc = kMse ? w2 * (I - u[c]) : u[c];
+#pragma unroll
+            for (int kk = 0; kk < 6; ++kk) gm[kk] = fmaf(gc, a[kk][c], gm[kk]);
+        }
+    }
+    const float gnx = fmaf(2.f * st.nx, gm[3], fmaf(st.ny, gm[5], gm[1]));
+    const float gny = fmaf(2.f * st.ny, gm[4], fmaf(st.nx, gm[5], gm[2]));
+    const float r3 = st.r * st.r * st.r;
+    gDx = gnx * (st.r - st.dx * st.dx * r3) - gny * st.dx * st.dy * r3;
+    gDy = gny * (st.r - st.dy * st.dy * r3) - gnx * st.dx * st.dy * r3;
+}
+
+// Tile of the depth-gradient kernel: 32 x 8 pixels of one sensor's image plane, one per
+// thread, plus a one-pixel halo whose (dL/dD_x, dL/dD_y) the stencils of the tile read.
+constexpr int kDgTx = 32, kDgTy = 8, kDgHalo = 2 * kDgTx + 2 * kDgTy;
+
+template <bool kMse>
+__device__ __forceinline__ void load_coeffs18(const float* As, int64_t HW, int64_t q, bool ok, float (&a)[6][3]) {
+#pragma unroll
+    for (int kk = 0; kk < 6; ++kk)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a[kk][c] = ok ? __ldg(As + (kk * 3 + c) * HW + q) : 0.f;
+}
+
+// Grid (tiles, sensors, image chunks), 256 threads.  For each image of sensor s in the
+// chunk (all warps walk the same list, found 32 ids at a time by ballot): every thread
+// evaluates (dL/dD_x, dL/dD_y) at its pixel and threads 0..79 at one halo pixel each,
+// into shared memory; then each pixel sums its four stencil-transpose terms.  The
+// coefficients of a thread's pixel and halo pixel stay in registers across the images.
+template <bool kMse>
+__global__ void __launch_bounds__(256, 3) shade_depth_grad_kernel(ShadeGeom G, int64_t B, const float* __restrict__ coeffs,
                                                                 const int32_t* __restrict__ sensor_id,
                                                                 const float* __restrict__ depth,
                                                                 const float* __restrict__ u_inten,
                                                                 const float* __restrict__ scale,
                                                                 float* __restrict__ grad_depth) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= G.W) return;
+    __shared__ float gx_s[2][kDgTy][kDgTx + 2];   // dL/dD_x at columns x0 - 1 .. x0 + 32, two images
+    __shared__ float gy_s[2][kDgTy + 2][kDgTx];   // dL/dD_y at rows y0 - 1 .. y0 + 8
+    const int t = threadIdx.x, lane = t & 31;
+    const int tiles_x = (G.W + kDgTx - 1) / kDgTx;
+    const int x0 = (static_cast<int>(blockIdx.x) % tiles_x) * kDgTx, y0 = (static_cast<int>(blockIdx.x) / tiles_x) * kDgTy;
+    const int tx = t & (kDgTx - 1), ty = t / kDgTx;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool valid = x < G.W && y < G.H;
+    const int s = blockIdx.y;
     const float w2 = kMse ? 2.f * (scale != nullptr ? __ldg(scale) : 1.f) : 1.f;
-    const int64_t px = static_cast<int64_t>(y) * G.W + x;
-    for (int64_t b = blockIdx.z; b < B; b += gridDim.z) {
-        const int64_t k = b * G.HW + px;
+    const float* As = coeffs + static_cast<int64_t>(s) * 18 * G.HW;
+    // own pixel and its four slots
+    DepthSlot sl[4];
+    depth_slots(G, valid ? x : 0, valid ? y : 0, sl);
+    float a[6][3];
+    load_coeffs18<kMse>(As, G.HW, static_cast<int64_t>(y) * G.W + x, valid, a);
+    // halo pixel of threads 0..79: rows y0 - 1 and y0 + 8 (their D_y), columns x0 - 1 and
+    // x0 + 32 (their D_x); absent outside the image
+    int hx = 0, hy = 0, haxis = -1;
+    if (t < kDgTx) { hx = x0 + t; hy = y0 - 1; haxis = 1; }
+    else if (t < 2 * kDgTx) { hx = x0 + t - kDgTx; hy = y0 + kDgTy; haxis = 1; }
+    else if (t < 2 * kDgTx + kDgTy) { hx = x0 - 1; hy = y0 + t - 2 * kDgTx; haxis = 0; }
+    else if (t < kDgHalo) { hx = x0 + kDgTx; hy = y0 + t - 2 * kDgTx - kDgTy; haxis = 0; }
+    const bool hvalid = haxis >= 0 && hx >= 0 && hx < G.W && hy >= 0 && hy < G.H;
+    float ah[6][3];
+    load_coeffs18<kMse>(As, G.HW, hvalid ? static_cast<int64_t>(hy) * G.W + hx : 0, hvalid, ah);
+    const int64_t qo = static_cast<int64_t>(y) * G.W + x, qh = static_cast<int64_t>(hy) * G.W + hx;
+    // images two at a time: both images' loads are issued before either is used
+    auto process = [&](int64_t b0, int64_t b1) {
+        const int n = b1 >= 0 ? 2 : 1;
+        if (valid) {
+            PixelState st[2];
+            float u[2][3];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int64_t b = i == 0 || n == 1 ? b0 : b1;
+                st[i] = pixel_state(depth + b * G.HW, G, x, y);
+                const float* U = u_inten + (b * G.HW + qo) * 3;
+                u[i][0] = __ldg(U);
+                u[i][1] = __ldg(U + 1);
+                u[i][2] = __ldg(U + 2);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                float gx, gy;
+                pixel_backward_reg<kMse>(a, st[i], u[i], w2, gx, gy);
+                gx_s[i][ty][tx + 1] = gx;
+                gy_s[i][ty + 1][tx] = gy;
+            }
+        }
+        if (hvalid) {
+            PixelState st[2];
+            float u[2][3];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int64_t b = i == 0 || n == 1 ? b0 : b1;
+                st[i] = pixel_state(depth + b * G.HW, G, hx, hy);
+                const float* U = u_inten + (b * G.HW + qh) * 3;
+                u[i][0] = __ldg(U);
+                u[i][1] = __ldg(U + 1);
+                u[i][2] = __ldg(U + 2);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                float gx, gy;
+                pixel_backward_reg<kMse>(ah, st[i], u[i], w2, gx, gy);
+                if (haxis == 0) gx_s[i][hy - y0][hx - x0 + 1] = gx;
+                else gy_s[i][hy - y0 + 1][hx - x0] = gy;
+            }
+        }
+        __syncthreads();
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                if (i == 1 && n == 1) break;
+                float acc = sl[0].w * gx_s[i][ty][sl[0].qx - x0 + 1];
+                acc = fmaf(sl[1].w, gx_s[i][ty][sl[1].qx - x0 + 1], acc);
+                acc = fmaf(sl[2].w, gy_s[i][sl[2].qy - y0 + 1][tx], acc);
+                acc = fmaf(sl[3].w, gy_s[i][sl[3].qy - y0 + 1][tx], acc);
+                grad_depth[(i ? b1 : b0) * G.HW + qo] = acc;
+            }
+        }
+        __syncthreads();
+    };
+    const int64_t chunk = (B + gridDim.z - 1) / gridDim.z;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.z) * chunk, c1 = min(c0 + chunk, B);
+    int64_t pending = -1;
+    for (int64_t base = c0; base < c1; base += 32) {
+        const int sid = base + lane < c1 ? __ldg(sensor_id + base + lane) : -1;
+        unsigned mask = __ballot_sync(0xffffffffu, sid == s);     // the same in every warp
+        while (mask != 0u) {
+            const int j = __ffs(mask) - 1;
+            mask &= mask - 1u;
+            if (pending < 0) {
+                pending = base + j;
+            } else {
+                process(pending, base + j);
+                pending = -1;
+            }
+        }
+    }
+    if (pending >= 0) process(pending, int64_t(-1));
+}
+
+// Zeroes the depth gradient of every image whose sensor id is out of range (the
+// per-sensor kernels never visit such images).  One block per image slot.
+__global__ void __launch_bounds__(256) zero_bad_sensor_images_kernel(int64_t B, int S, int64_t HW,
+                                                                      const int32_t* __restrict__ sensor_id,
+                                                                      float* __restrict__ grad_depth) {
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
         const int s = __ldg(sensor_id + b);
-        if (s < 0 || s >= G.S) {
-            grad_depth[k] = 0.f;
-            continue;
-        }
-        const float* D = depth + b * G.HW;
-        const float* Ab = coeffs + static_cast<int64_t>(s) * 18 * G.HW;
-        const float* gI = u_inten + b * G.HW * 3;
-        float acc = 0.f;
-        // row neighbours: D_x(q) for q = (x + dq, y)
-        for (int dq = -1; dq <= 1; ++dq) {
-            const int qx = x + dq;
-            if (qx < 0 || qx >= G.W) continue;
-            int lo, hi;
-            float c;
-            axis_stencil(qx, G.W, G.px, lo, hi, c);
-            const float w = (hi == x ? c : 0.f) - (lo == x ? c : 0.f);
-            if (w == 0.f) continue;
-            const int64_t q = static_cast<int64_t>(y) * G.W + qx;
-            const PixelState st = pixel_state(D, G, qx, y);
-            const float g[3] = {__ldg(gI + q * 3), __ldg(gI + q * 3 + 1), __ldg(gI + q * 3 + 2)};
-            float gm[6], gDx, gDy;
-            pixel_backward<kMse>(Ab + q, G.HW, st, g, w2, gm, gDx, gDy);
-            acc = fmaf(w, gDx, acc);
-        }
-        // column neighbours: D_y(q) for q = (x, y + dq)
-        for (int dq = -1; dq <= 1; ++dq) {
-            const int qy = y + dq;
-            if (qy < 0 || qy >= G.H) continue;
-            int lo, hi;
-            float c;
-            axis_stencil(qy, G.H, G.py, lo, hi, c);
-            const float w = (hi == y ? c : 0.f) - (lo == y ? c : 0.f);
-            if (w == 0.f) continue;
-            const int64_t q = static_cast<int64_t>(qy) * G.W + x;
-            const PixelState st = pixel_state(D, G, x, qy);
-            const float g[3] = {__ldg(gI + q * 3), __ldg(gI + q * 3 + 1), __ldg(gI + q * 3 + 2)};
-            float gm[6], gDx, gDy;
-            pixel_backward<kMse>(Ab + q, G.HW, st, g, w2, gm, gDx, gDy);
-            acc = fmaf(w, gDy, acc);
-        }
-        grad_depth[k] = acc;
+        if (s >= 0 && s < S) continue;
+        for (int64_t k = threadIdx.x; k < HW; k += blockDim.x) grad_depth[b * HW + k] = 0.f;
     }
 }
 

@@ -1165,10 +1165,39 @@ int shade_geom(const tacsl_shading* sh, ShadeGeom& G) {
     return TACSL_OK;
 }
 
-// (row segments of 128 pixels, rows, images); images beyond 65535 are looped over
-dim3 pixel_grid(const ShadeGeom& G, int64_t B) {
-    return dim3(static_cast<unsigned>((G.W + 127) / 128), static_cast<unsigned>(G.H),
-                static_cast<unsigned>(std::min<int64_t>(std::max<int64_t>(B, 1), 65535)));
+// Grid of the depth-gradient kernel: (32 x 8 tiles, sensors, image chunks), with enough
+// image chunks that the launch gives every SM a few CTAs even for small images.
+int launch_depth_grad(bool mse, const ShadeGeom& G, int64_t B, const float* coeffs, const int32_t* sensor_id,
+                      const float* depth_map, const float* u, const float* scale, float* grad_depth,
+                      const DevInfo& dev, tacsl_stream_t stream) {
+    const int64_t tiles = (int64_t)((G.W + kDgTx - 1) / kDgTx) * ((G.H + kDgTy - 1) / kDgTy);
+    if (tiles > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "image too large");
+    // image chunks: at least 32 images per CTA (its coefficients are loaded once), and as
+    // many chunks as keep the last wave of 3 CTAs per SM nearly full
+    const int64_t base = tiles * G.S, slots = 3 * (int64_t)dev.sms;
+    const int64_t c_max = std::max<int64_t>(1, std::min<int64_t>((B + 31) / 32, 65535));
+    int64_t chunks = 1;
+    double best = 1e30;
+    for (int64_t c = 1; c <= std::min<int64_t>(c_max, 64); ++c) {
+        const int64_t ctas = base * c;
+        const double t = (double)((ctas + slots - 1) / slots) / (double)c;   // waves x work per CTA
+        if (t < best - 1e-9) {
+            best = t;
+            chunks = c;
+        }
+    }
+    const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(G.S), static_cast<unsigned>(chunks));
+    if (mse)
+        shade_depth_grad_kernel<true><<<grid, 256, 0, stream>>>(G, B, coeffs, sensor_id, depth_map, u, scale,
+                                                                grad_depth);
+    else
+        shade_depth_grad_kernel<false><<<grid, 256, 0, stream>>>(G, B, coeffs, sensor_id, depth_map, u, scale,
+                                                                 grad_depth);
+    int rc = check_launch("depth gradient kernel");
+    if (rc) return rc;
+    zero_bad_sensor_images_kernel<<<static_cast<unsigned>(std::min<int64_t>(B, 4096)), 256, 0, stream>>>(
+        B, G.S, G.HW, sensor_id, grad_depth);
+    return check_launch("depth gradient kernel (bad sensor ids)");
 }
 
 int grid_for(int64_t n, int per_sm, const DevInfo& dev) {
@@ -1263,10 +1292,9 @@ int tacsl_shade_adjoint(const tacsl_shading* shading, int64_t B, const int32_t* 
         if ((rc = check_launch("tacsl_shade_adjoint (coefficients)"))) return rc;
     }
     if (grad_depth != nullptr && B > 0) {
-        shade_depth_grad_kernel<false><<<pixel_grid(G, B), 128, 0, stream>>>(G, B, shading->coeffs, sensor_id,
-                                                                              depth_map, g_intensity, nullptr,
-                                                                              grad_depth);
-        if ((rc = check_launch("tacsl_shade_adjoint (depth)"))) return rc;
+        if ((rc = launch_depth_grad(false, G, B, shading->coeffs, sensor_id, depth_map, g_intensity, nullptr,
+                                    grad_depth, *dev, stream)))
+            return rc;
     }
     return ok();
 }
@@ -1296,9 +1324,9 @@ int tacsl_shade_mse(const tacsl_shading* shading, int64_t B, const int32_t* sens
         if ((rc = check_launch("tacsl_shade_mse (loss map / coefficients)"))) return rc;
     }
     if (grad_depth != nullptr && B > 0) {
-        shade_depth_grad_kernel<true><<<pixel_grid(G, B), 128, 0, stream>>>(G, B, shading->coeffs, sensor_id,
-                                                                             depth_map, target, scale, grad_depth);
-        if ((rc = check_launch("tacsl_shade_mse (depth)"))) return rc;
+        if ((rc = launch_depth_grad(true, G, B, shading->coeffs, sensor_id, depth_map, target, scale, grad_depth,
+                                    *dev, stream)))
+            return rc;
     }
     return ok();
 }

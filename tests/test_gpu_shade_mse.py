@@ -61,7 +61,7 @@ def _close(got, want, rel):
     assert np.abs(got - want).max() <= rel * np.abs(want).max() + 1e-12, np.abs(got - want).max() / np.abs(want).max()
 
 
-@pytest.mark.parametrize("S,B,H,W", [(2, 6, 24, 32), (1, 3, 7, 12), (3, 10, 16, 12)])
+@pytest.mark.parametrize("S,B,H,W", [(2, 6, 24, 32), (1, 3, 7, 12), (3, 10, 16, 12), (1, 2, 1, 8), (2, 5, 9, 36)])
 def test_shade_mse_matches_oracle(S, B, H, W):
     co, dm, sid, tgt, px, py = _case(3 + B, S, B, H, W)
     lm, gc, gd = _mse(co, dm, sid, tgt, px, py)
