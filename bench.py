@@ -1033,7 +1033,7 @@ def run_grad(args, rank, world, local_rank, dist):
             "render_adjoint_kernel": {"algorithmic_bytes": radj_bytes, "hit_columns": n_hit,
                                       "frac": radj_bytes / (k_ms["render_adjoint_kernel"] * 1e-3) / 1e9 / peak},
             "peak_gbs": peak},
-        "gpu_launches_per_step": 4,
+        "gpu_launches_per_step": 3,
         "cpu_baseline": (oracle_grad_rate(sc, args.oracle_seconds, args.seed + 500)
                          if rank == 0 and not args.no_cpu_baseline else None),
     }
