@@ -489,12 +489,29 @@ __global__ void __launch_bounds__(256) flag_bad_sensors_kernel(int64_t B, int S,
     }
 }
 
+// Per-lane asynchronous 4-byte copy global -> shared (completion per thread, by group).
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int kCgStages = 6;     // images in flight per warp
+constexpr int kCgSeg = 128;      // images of a warp's slice listed at a time
+constexpr int kCgVals = 7;       // per lane and image: 4 depth samples, 3 upstream values
+
 // dL/dA[s][k][c][px] = sum over images b of sensor s of g[b][px][c] m_k(b, px) (where the
 // clamp passes).  Grid (pixel tiles, sensors); each warp sums its slice of the images in
 // order and the eight partial sums are added in warp order (deterministic).
 // kMse = false: g is read from u = dL/dI.  kMse = true: u is the target intensity, g =
 // w2 (I - u), and loss_map[s][px] (if not NULL) receives sum_b sum_c (clamp(I) - u)^2 in
 // the same order; grad_coeffs may then be NULL.
+// Each lane's 7 inputs per image (the 4 depth samples of its difference stencils and the
+// 3 upstream values) are fetched kCgStages images ahead by per-lane cp.async copies into
+// a shared-memory ring, so a warp keeps several images' loads in flight without
+// registers; the warp first lists its slice's images of sensor s, kCgSeg at a time.
 template <bool kMse>
 __global__ void __launch_bounds__(256) shade_coeff_grad_kernel(ShadeGeom G, int64_t B, const float* __restrict__ coeffs,
                                                                 const int32_t* __restrict__ sensor_id,
@@ -504,13 +521,24 @@ __global__ void __launch_bounds__(256) shade_coeff_grad_kernel(ShadeGeom G, int6
                                                                 float* __restrict__ grad_coeffs,
                                                                 float* __restrict__ loss_map) {
     constexpr int kTerms = kMse ? 19 : 18;
-    __shared__ float part[kImgWarps][kTerms][kPxTile];
+    __shared__ union {
+        float ring[kImgWarps][kCgStages][kCgVals][kPxTile];
+        float part[kImgWarps][kTerms][kPxTile];
+    } sm;
+    __shared__ int list[kImgWarps][kCgSeg];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s = blockIdx.y;
     const int64_t px = static_cast<int64_t>(blockIdx.x) * kPxTile + lane;
     const bool valid = px < G.HW;
     const int y = valid ? static_cast<int>(px / G.W) : 0, x = valid ? static_cast<int>(px - static_cast<int64_t>(y) * G.W) : 0;
     const float w2 = kMse ? 2.f * (scale != nullptr ? __ldg(scale) : 1.f) : 1.f;
+    // the lane's difference stencils (the same for every image)
+    int xlo, xhi, ylo, yhi;
+    float cx, cy;
+    axis_stencil(x, G.W, G.px, xlo, xhi, cx);
+    axis_stencil(y, G.H, G.py, ylo, yhi, cy);
+    const int64_t o_xh = static_cast<int64_t>(y) * G.W + xhi, o_xl = static_cast<int64_t>(y) * G.W + xlo;
+    const int64_t o_yh = static_cast<int64_t>(yhi) * G.W + x, o_yl = static_cast<int64_t>(ylo) * G.W + x;
     float a[6][3], acc[6][3], lacc = 0.f;
 #pragma unroll
     for (int kk = 0; kk < 6; ++kk)
@@ -521,45 +549,73 @@ __global__ void __launch_bounds__(256) shade_coeff_grad_kernel(ShadeGeom G, int6
         }
     const int64_t per = (B + kImgWarps - 1) / kImgWarps;
     const int64_t w0 = min(warp * per, B), w1 = min(w0 + per, B);
-    for_image_pairs(sensor_id, w0, w1, s, [&](int64_t b0, int64_t b1) {
-        if (!valid) return;
-        const int64_t bb1 = b1 >= 0 ? b1 : b0;
-        const PixelState st0 = pixel_state(depth + b0 * G.HW, G, x, y);
-        const PixelState st1 = pixel_state(depth + bb1 * G.HW, G, x, y);
-        float g0[3], g1[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            g0[c] = __ldg(u_inten + (b0 * G.HW + px) * 3 + c);
-            g1[c] = b1 >= 0 ? __ldg(u_inten + (bb1 * G.HW + px) * 3 + c) : 0.f;
+    const unsigned below = (1u << lane) - 1u;
+    for (int64_t seg = w0; seg < w1; seg += kCgSeg) {
+        const int64_t seg_end = min(seg + kCgSeg, w1);
+        int n = 0;
+        for (int64_t base = seg; base < seg_end; base += 32) {
+            const int sid = base + lane < seg_end ? __ldg(sensor_id + base + lane) : -1;
+            const unsigned mask = __ballot_sync(0xffffffffu, sid == s);
+            if (sid == s) list[warp][n + __popc(mask & below)] = static_cast<int>(base + lane);
+            n += __popc(mask);
         }
+        __syncwarp();
+        auto issue = [&](int i) {
+            if (valid && i < n) {
+                const int64_t b = list[warp][i];
+                float* st = &sm.ring[warp][i % kCgStages][0][lane];
+                const float* D = depth + b * G.HW;
+                const float* U = u_inten + (b * G.HW + px) * 3;
+                cp_async4(st + 0 * kPxTile, D + o_xh);
+                cp_async4(st + 1 * kPxTile, D + o_xl);
+                cp_async4(st + 2 * kPxTile, D + o_yh);
+                cp_async4(st + 3 * kPxTile, D + o_yl);
+                cp_async4(st + 4 * kPxTile, U);
+                cp_async4(st + 5 * kPxTile, U + 1);
+                cp_async4(st + 6 * kPxTile, U + 2);
+            }
+            cp_async_commit();      // one group per image slot, empty or not
+        };
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {          // image b0, then b1: the summation order is the image order
-            if (i == 1 && b1 < 0) break;
-            const PixelState& st = i ? st1 : st0;
-            const float m[6] = {1.f, st.nx, st.ny, st.nx * st.nx, st.ny * st.ny, st.nx * st.ny};
+        for (int i = 0; i < kCgStages - 1; ++i) issue(i);
+        for (int i = 0; i < n; ++i) {
+            issue(i + kCgStages - 1);
+            cp_async_wait<kCgStages - 1>();      // this lane's copies of image i have landed
+            if (!valid) continue;
+            const float* st = &sm.ring[warp][i % kCgStages][0][lane];
+            PixelState ps;
+            ps.dx = (st[0 * kPxTile] - st[1 * kPxTile]) * cx;
+            ps.dy = (st[2 * kPxTile] - st[3 * kPxTile]) * cy;
+            ps.r = rsqrtf(fmaf(ps.dx, ps.dx, fmaf(ps.dy, ps.dy, 1.f)));
+            ps.nx = ps.dx * ps.r;
+            ps.ny = ps.dy * ps.r;
+            const float uu[3] = {st[4 * kPxTile], st[5 * kPxTile], st[6 * kPxTile]};
+            const float m[6] = {1.f, ps.nx, ps.ny, ps.nx * ps.nx, ps.ny * ps.ny, ps.nx * ps.ny};
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float I = 0.f;
 #pragma unroll
                 for (int kk = 0; kk < 6; ++kk) I = fmaf(a[kk][c], m[kk], I);
-                const float uc = i ? g1[c] : g0[c];
                 if (kMse) {
-                    const float e = fminf(fmaxf(I, 0.f), 255.f) - uc;
+                    const float e = fminf(fmaxf(I, 0.f), 255.f) - uu[c];
                     lacc = fmaf(e, e, lacc);
                 }
                 if (I > 0.f && I < 255.f) {
-                    const float gc = kMse ? w2 * (I - uc) : uc;
+                    const float gc = kMse ? w2 * (I - uu[c]) : uu[c];
 #pragma unroll
                     for (int kk = 0; kk < 6; ++kk) acc[kk][c] = fmaf(gc, m[kk], acc[kk][c]);
                 }
             }
         }
-    });
+        cp_async_wait<0>();
+        __syncwarp();               // the list and the ring are reused by the next segment
+    }
+    __syncthreads();                // every warp is done with the ring: it becomes the partial sums
 #pragma unroll
     for (int kk = 0; kk < 6; ++kk)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) part[warp][kk * 3 + c][lane] = acc[kk][c];
-    if (kMse) part[warp][kTerms - 1][lane] = lacc;
+        for (int c = 0; c < 3; ++c) sm.part[warp][kk * 3 + c][lane] = acc[kk][c];
+    if (kMse) sm.part[warp][kTerms - 1][lane] = lacc;
     __syncthreads();
     // kTerms x 32 sums over the 8 warps, in warp order; 256 threads take them in turn
     for (int i = threadIdx.x; i < kTerms * kPxTile; i += blockDim.x) {
@@ -568,7 +624,7 @@ __global__ void __launch_bounds__(256) shade_coeff_grad_kernel(ShadeGeom G, int6
         if (p >= G.HW) continue;
         float sum = 0.f;
 #pragma unroll
-        for (int w = 0; w < kImgWarps; ++w) sum += part[w][term][l];
+        for (int w = 0; w < kImgWarps; ++w) sum += sm.part[w][term][l];
         if (term < 18) {
             if (grad_coeffs != nullptr) grad_coeffs[(static_cast<int64_t>(s) * 18 + term) * G.HW + p] = sum;
         } else if (loss_map != nullptr) {
