@@ -408,86 +408,11 @@ __device__ __forceinline__ PixelState pixel_state(const float* D, const ShadeGeo
     return s;
 }
 
-// Images of one sensor within [c0, c1), found 32 ids at a time and handed over in
-// order, two at a time: f(b0, b1) with b1 = -1 when only one is left.  The pairs let a
-// warp issue the loads of two images before it computes either.
-template <class F>
-__device__ __forceinline__ void for_image_pairs(const int32_t* __restrict__ sensor_id, int64_t c0, int64_t c1, int s,
-                                                F&& f) {
-    const int lane = threadIdx.x & 31;
-    int64_t pending = -1;
-    for (int64_t base = c0; base < c1; base += 32) {
-        const int sid = base + lane < c1 ? __ldg(sensor_id + base + lane) : -1;
-        unsigned mask = __ballot_sync(0xffffffffu, sid == s);
-        while (mask != 0u) {
-            const int j = __ffs(mask) - 1;
-            mask &= mask - 1u;
-            if (pending < 0) {
-                pending = base + j;
-            } else {
-                f(pending, base + j);
-                pending = -1;
-            }
-        }
-    }
-    if (pending >= 0) f(pending, int64_t(-1));
-}
-
 // Work split of the per-pixel image kernels: a CTA of 8 warps owns 32 consecutive pixels
 // of one sensor's image plane (one per lane, so the per-pixel coefficients stay in
 // registers) and a range of images; its warps take equal slices of that range.
 constexpr int kPxTile = 32;
 constexpr int kImgWarps = 8;
-
-// Clamped intensity: grid (pixel tiles, sensors, image chunks).
-__global__ void __launch_bounds__(256) shade_intensity_kernel(ShadeGeom G, int64_t B, int64_t chunk,
-                                                               const float* __restrict__ coeffs,
-                                                               const int32_t* __restrict__ sensor_id,
-                                                               const float* __restrict__ depth,
-                                                               float* __restrict__ inten) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int s = blockIdx.y;
-    const int64_t px = static_cast<int64_t>(blockIdx.x) * kPxTile + lane;
-    const bool valid = px < G.HW;
-    const int y = valid ? static_cast<int>(px / G.W) : 0, x = valid ? static_cast<int>(px - static_cast<int64_t>(y) * G.W) : 0;
-    float a[6][3];
-#pragma unroll
-    for (int kk = 0; kk < 6; ++kk)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            a[kk][c] = valid ? __ldg(coeffs + (static_cast<int64_t>(s) * 18 + kk * 3 + c) * G.HW + px) : 0.f;
-    const int64_t c0 = static_cast<int64_t>(blockIdx.z) * chunk, c1 = min(c0 + chunk, B);
-    const int64_t per = (c1 - c0 + kImgWarps - 1) / kImgWarps;
-    const int64_t w0 = min(c0 + warp * per, c1), w1 = min(w0 + per, c1);
-    for_image_pairs(sensor_id, w0, w1, s, [&](int64_t b0, int64_t b1) {
-        if (!valid) return;
-        const PixelState st0 = pixel_state(depth + b0 * G.HW, G, x, y);
-        const PixelState st1 = pixel_state(depth + (b1 >= 0 ? b1 : b0) * G.HW, G, x, y);
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            if (i == 1 && b1 < 0) break;
-            const PixelState& st = i ? st1 : st0;
-            const float m[6] = {1.f, st.nx, st.ny, st.nx * st.nx, st.ny * st.ny, st.nx * st.ny};
-            float* out = inten + ((i ? b1 : b0) * G.HW + px) * 3;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float I = 0.f;
-#pragma unroll
-                for (int kk = 0; kk < 6; ++kk) I = fmaf(a[kk][c], m[kk], I);
-                out[c] = fminf(fmaxf(I, 0.f), 255.f);
-            }
-        }
-    });
-}
-
-// Bad sensor ids of the intensity forward: flagged once per image.
-__global__ void __launch_bounds__(256) flag_bad_sensors_kernel(int64_t B, int S, const int32_t* __restrict__ sensor_id) {
-    for (int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; b < B;
-         b += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int s = __ldg(sensor_id + b);
-        if (s < 0 || s >= S) raise_dev_error(TACSL_DEVERR_BAD_SENSOR_ID);
-    }
-}
 
 // Per-lane asynchronous 4-byte copy global -> shared (completion per thread, by group).
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
@@ -501,6 +426,109 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 constexpr int kCgStages = 6;     // images in flight per warp
 constexpr int kCgSeg = 128;      // images of a warp's slice listed at a time
 constexpr int kCgVals = 7;       // per lane and image: 4 depth samples, 3 upstream values
+
+// The images of sensor s in [w0, w1), in order, each with this lane's NV input values
+// fetched kCgStages images ahead: the warp lists its images kCgSeg at a time (ballot),
+// issue(b, dst) starts the lane's copies of image b into dst[v * kPxTile] (cp.async; it
+// may issue none), and f(b, src) consumes them once they have landed.  ring: this warp's
+// [kCgStages][NV][kPxTile] floats; list: its kCgSeg ints.  Warp-uniform control flow.
+template <int NV, class Issue, class F>
+__device__ __forceinline__ void for_images_pipelined(const int32_t* __restrict__ sensor_id, int64_t w0, int64_t w1,
+                                                     int s, float* ring, int* list, Issue&& issue, F&& f) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    for (int64_t seg = w0; seg < w1; seg += kCgSeg) {
+        const int64_t seg_end = min(seg + kCgSeg, w1);
+        int n = 0;
+        for (int64_t base = seg; base < seg_end; base += 32) {
+            const int sid = base + lane < seg_end ? __ldg(sensor_id + base + lane) : -1;
+            const unsigned mask = __ballot_sync(0xffffffffu, sid == s);
+            if (sid == s) list[n + __popc(mask & below)] = static_cast<int>(base + lane);
+            n += __popc(mask);
+        }
+        __syncwarp();
+        auto start = [&](int i) {
+            if (i < n) issue(static_cast<int64_t>(list[i]), ring + (i % kCgStages) * NV * kPxTile + lane);
+            cp_async_commit();      // one group per image slot, empty or not
+        };
+#pragma unroll
+        for (int i = 0; i < kCgStages - 1; ++i) start(i);
+        for (int i = 0; i < n; ++i) {
+            start(i + kCgStages - 1);
+            cp_async_wait<kCgStages - 1>();      // this lane's copies of image i have landed
+            f(static_cast<int64_t>(list[i]), ring + (i % kCgStages) * NV * kPxTile + lane);
+        }
+        cp_async_wait<0>();
+        __syncwarp();               // the list and the ring are reused by the next segment
+    }
+}
+
+
+// Clamped intensity: grid (pixel tiles, sensors, image chunks).  Each lane's 4 depth
+// samples per image are fetched kCgStages images ahead (for_images_pipelined).
+__global__ void __launch_bounds__(256) shade_intensity_kernel(ShadeGeom G, int64_t B, int64_t chunk,
+                                                               const float* __restrict__ coeffs,
+                                                               const int32_t* __restrict__ sensor_id,
+                                                               const float* __restrict__ depth,
+                                                               float* __restrict__ inten) {
+    __shared__ float ring[kImgWarps][kCgStages][4][kPxTile];
+    __shared__ int list[kImgWarps][kCgSeg];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = blockIdx.y;
+    const int64_t px = static_cast<int64_t>(blockIdx.x) * kPxTile + lane;
+    const bool valid = px < G.HW;
+    const int y = valid ? static_cast<int>(px / G.W) : 0, x = valid ? static_cast<int>(px - static_cast<int64_t>(y) * G.W) : 0;
+    int xlo, xhi, ylo, yhi;
+    float cx, cy;
+    axis_stencil(x, G.W, G.px, xlo, xhi, cx);
+    axis_stencil(y, G.H, G.py, ylo, yhi, cy);
+    const int64_t o_xh = static_cast<int64_t>(y) * G.W + xhi, o_xl = static_cast<int64_t>(y) * G.W + xlo;
+    const int64_t o_yh = static_cast<int64_t>(yhi) * G.W + x, o_yl = static_cast<int64_t>(ylo) * G.W + x;
+    float a[6][3];
+#pragma unroll
+    for (int kk = 0; kk < 6; ++kk)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            a[kk][c] = valid ? __ldg(coeffs + (static_cast<int64_t>(s) * 18 + kk * 3 + c) * G.HW + px) : 0.f;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.z) * chunk, c1 = min(c0 + chunk, B);
+    const int64_t per = (c1 - c0 + kImgWarps - 1) / kImgWarps;
+    const int64_t w0 = min(c0 + warp * per, c1), w1 = min(w0 + per, c1);
+    for_images_pipelined<4>(
+        sensor_id, w0, w1, s, &ring[warp][0][0][0], list[warp],
+        [&](int64_t b, float* st) {
+            if (!valid) return;
+            const float* D = depth + b * G.HW;
+            cp_async4(st + 0 * kPxTile, D + o_xh);
+            cp_async4(st + 1 * kPxTile, D + o_xl);
+            cp_async4(st + 2 * kPxTile, D + o_yh);
+            cp_async4(st + 3 * kPxTile, D + o_yl);
+        },
+        [&](int64_t b, const float* st) {
+            if (!valid) return;
+            const float dx = (st[0 * kPxTile] - st[1 * kPxTile]) * cx;
+            const float dy = (st[2 * kPxTile] - st[3 * kPxTile]) * cy;
+            const float r = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, 1.f)));
+            const float nx = dx * r, ny = dy * r;
+            const float m[6] = {1.f, nx, ny, nx * nx, ny * ny, nx * ny};
+            float* out = inten + (b * G.HW + px) * 3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float I = 0.f;
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk) I = fmaf(a[kk][c], m[kk], I);
+                out[c] = fminf(fmaxf(I, 0.f), 255.f);
+            }
+        });
+}
+
+// Bad sensor ids of the intensity forward: flagged once per image.
+__global__ void __launch_bounds__(256) flag_bad_sensors_kernel(int64_t B, int S, const int32_t* __restrict__ sensor_id) {
+    for (int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; b < B;
+         b += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int s = __ldg(sensor_id + b);
+        if (s < 0 || s >= S) raise_dev_error(TACSL_DEVERR_BAD_SENSOR_ID);
+    }
+}
 
 // dL/dA[s][k][c][px] = sum over images b of sensor s of g[b][px][c] m_k(b, px) (where the
 // clamp passes).  Grid (pixel tiles, sensors); each warp sums its slice of the images in
@@ -549,40 +577,22 @@ __global__ void __launch_bounds__(256) shade_coeff_grad_kernel(ShadeGeom G, int6
         }
     const int64_t per = (B + kImgWarps - 1) / kImgWarps;
     const int64_t w0 = min(warp * per, B), w1 = min(w0 + per, B);
-    const unsigned below = (1u << lane) - 1u;
-    for (int64_t seg = w0; seg < w1; seg += kCgSeg) {
-        const int64_t seg_end = min(seg + kCgSeg, w1);
-        int n = 0;
-        for (int64_t base = seg; base < seg_end; base += 32) {
-            const int sid = base + lane < seg_end ? __ldg(sensor_id + base + lane) : -1;
-            const unsigned mask = __ballot_sync(0xffffffffu, sid == s);
-            if (sid == s) list[warp][n + __popc(mask & below)] = static_cast<int>(base + lane);
-            n += __popc(mask);
-        }
-        __syncwarp();
-        auto issue = [&](int i) {
-            if (valid && i < n) {
-                const int64_t b = list[warp][i];
-                float* st = &sm.ring[warp][i % kCgStages][0][lane];
-                const float* D = depth + b * G.HW;
-                const float* U = u_inten + (b * G.HW + px) * 3;
-                cp_async4(st + 0 * kPxTile, D + o_xh);
-                cp_async4(st + 1 * kPxTile, D + o_xl);
-                cp_async4(st + 2 * kPxTile, D + o_yh);
-                cp_async4(st + 3 * kPxTile, D + o_yl);
-                cp_async4(st + 4 * kPxTile, U);
-                cp_async4(st + 5 * kPxTile, U + 1);
-                cp_async4(st + 6 * kPxTile, U + 2);
-            }
-            cp_async_commit();      // one group per image slot, empty or not
-        };
-#pragma unroll
-        for (int i = 0; i < kCgStages - 1; ++i) issue(i);
-        for (int i = 0; i < n; ++i) {
-            issue(i + kCgStages - 1);
-            cp_async_wait<kCgStages - 1>();      // this lane's copies of image i have landed
-            if (!valid) continue;
-            const float* st = &sm.ring[warp][i % kCgStages][0][lane];
+    for_images_pipelined<kCgVals>(
+        sensor_id, w0, w1, s, &sm.ring[warp][0][0][0], list[warp],
+        [&](int64_t b, float* st) {
+            if (!valid) return;
+            const float* D = depth + b * G.HW;
+            const float* U = u_inten + (b * G.HW + px) * 3;
+            cp_async4(st + 0 * kPxTile, D + o_xh);
+            cp_async4(st + 1 * kPxTile, D + o_xl);
+            cp_async4(st + 2 * kPxTile, D + o_yh);
+            cp_async4(st + 3 * kPxTile, D + o_yl);
+            cp_async4(st + 4 * kPxTile, U);
+            cp_async4(st + 5 * kPxTile, U + 1);
+            cp_async4(st + 6 * kPxTile, U + 2);
+        },
+        [&](int64_t, const float* st) {
+            if (!valid) return;
             PixelState ps;
             ps.dx = (st[0 * kPxTile] - st[1 * kPxTile]) * cx;
             ps.dy = (st[2 * kPxTile] - st[3 * kPxTile]) * cy;
@@ -606,10 +616,7 @@ __global__ void __launch_bounds__(256) shade_coeff_grad_kernel(ShadeGeom G, int6
                     for (int kk = 0; kk < 6; ++kk) acc[kk][c] = fmaf(gc, m[kk], acc[kk][c]);
                 }
             }
-        }
-        cp_async_wait<0>();
-        __syncwarp();               // the list and the ring are reused by the next segment
-    }
+        });
     __syncthreads();                // every warp is done with the ring: it becomes the partial sums
 #pragma unroll
     for (int kk = 0; kk < 6; ++kk)
