@@ -710,19 +710,27 @@ __device__ __forceinline__ void load_coeffs18(const float* As, int64_t HW, int64
 }
 
 // Grid (tiles, sensors, image chunks), 256 threads.  For each image of sensor s in the
-// chunk (all warps walk the same list, found 32 ids at a time by ballot): every thread
-// evaluates (dL/dD_x, dL/dD_y) at its pixel and threads 0..79 at one halo pixel each,
-// into shared memory; then each pixel sums its four stencil-transpose terms.  The
-// coefficients of a thread's pixel and halo pixel stay in registers across the images.
+// chunk (listed by warp 0, kCgSeg at a time, into shared memory): every thread evaluates
+// (dL/dD_x, dL/dD_y) at its pixel and threads 0..79 at one halo pixel each, into shared
+// memory; then each pixel sums its four stencil-transpose terms.  The coefficients of a
+// thread's pixel and halo pixel stay in registers across the images, and its 14 inputs
+// per image (4 depth samples and 3 upstream values, for each of the two pixels) are
+// fetched kDgStages images ahead by per-thread cp.async copies into a shared ring.
+constexpr int kDgStages = 3;
+constexpr int kDgVals = 14;
+
 template <bool kMse>
 __global__ void __launch_bounds__(256, 3) shade_depth_grad_kernel(ShadeGeom G, int64_t B, const float* __restrict__ coeffs,
-                                                                const int32_t* __restrict__ sensor_id,
-                                                                const float* __restrict__ depth,
-                                                                const float* __restrict__ u_inten,
-                                                                const float* __restrict__ scale,
-                                                                float* __restrict__ grad_depth) {
-    __shared__ float gx_s[2][kDgTy][kDgTx + 2];   // dL/dD_x at columns x0 - 1 .. x0 + 32, two images
-    __shared__ float gy_s[2][kDgTy + 2][kDgTx];   // dL/dD_y at rows y0 - 1 .. y0 + 8
+                                                                   const int32_t* __restrict__ sensor_id,
+                                                                   const float* __restrict__ depth,
+                                                                   const float* __restrict__ u_inten,
+                                                                   const float* __restrict__ scale,
+                                                                   float* __restrict__ grad_depth) {
+    __shared__ float gx_s[kDgTy][kDgTx + 2];   // dL/dD_x at columns x0 - 1 .. x0 + 32
+    __shared__ float gy_s[kDgTy + 2][kDgTx];   // dL/dD_y at rows y0 - 1 .. y0 + 8
+    __shared__ float ring[kDgStages][kDgVals][256];
+    __shared__ int list[kCgSeg];
+    __shared__ int list_n;
     const int t = threadIdx.x, lane = t & 31;
     const int tiles_x = (G.W + kDgTx - 1) / kDgTx;
     const int x0 = (static_cast<int>(blockIdx.x) % tiles_x) * kDgTx, y0 = (static_cast<int>(blockIdx.x) / tiles_x) * kDgTy;
@@ -747,82 +755,104 @@ __global__ void __launch_bounds__(256, 3) shade_depth_grad_kernel(ShadeGeom G, i
     const bool hvalid = haxis >= 0 && hx >= 0 && hx < G.W && hy >= 0 && hy < G.H;
     float ah[6][3];
     load_coeffs18<kMse>(As, G.HW, hvalid ? static_cast<int64_t>(hy) * G.W + hx : 0, hvalid, ah);
-    const int64_t qo = static_cast<int64_t>(y) * G.W + x, qh = static_cast<int64_t>(hy) * G.W + hx;
-    // images two at a time: both images' loads are issued before either is used
-    auto process = [&](int64_t b0, int64_t b1) {
-        const int n = b1 >= 0 ? 2 : 1;
-        if (valid) {
-            PixelState st[2];
-            float u[2][3];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int64_t b = i == 0 || n == 1 ? b0 : b1;
-                st[i] = pixel_state(depth + b * G.HW, G, x, y);
-                const float* U = u_inten + (b * G.HW + qo) * 3;
-                u[i][0] = __ldg(U);
-                u[i][1] = __ldg(U + 1);
-                u[i][2] = __ldg(U + 2);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                float gx, gy;
-                pixel_backward_reg<kMse>(a, st[i], u[i], w2, gx, gy);
-                gx_s[i][ty][tx + 1] = gx;
-                gy_s[i][ty + 1][tx] = gy;
-            }
-        }
-        if (hvalid) {
-            PixelState st[2];
-            float u[2][3];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int64_t b = i == 0 || n == 1 ? b0 : b1;
-                st[i] = pixel_state(depth + b * G.HW, G, hx, hy);
-                const float* U = u_inten + (b * G.HW + qh) * 3;
-                u[i][0] = __ldg(U);
-                u[i][1] = __ldg(U + 1);
-                u[i][2] = __ldg(U + 2);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                float gx, gy;
-                pixel_backward_reg<kMse>(ah, st[i], u[i], w2, gx, gy);
-                if (haxis == 0) gx_s[i][hy - y0][hx - x0 + 1] = gx;
-                else gy_s[i][hy - y0 + 1][hx - x0] = gy;
-            }
-        }
-        __syncthreads();
-        if (valid) {
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                if (i == 1 && n == 1) break;
-                float acc = sl[0].w * gx_s[i][ty][sl[0].qx - x0 + 1];
-                acc = fmaf(sl[1].w, gx_s[i][ty][sl[1].qx - x0 + 1], acc);
-                acc = fmaf(sl[2].w, gy_s[i][sl[2].qy - y0 + 1][tx], acc);
-                acc = fmaf(sl[3].w, gy_s[i][sl[3].qy - y0 + 1][tx], acc);
-                grad_depth[(i ? b1 : b0) * G.HW + qo] = acc;
-            }
-        }
-        __syncthreads();
+    // the difference stencils of both pixels (image-independent offsets and scales)
+    int lo, hi;
+    float cxo, cyo, cxh, cyh;
+    axis_stencil(valid ? x : 0, G.W, G.px, lo, hi, cxo);
+    // (offsets within one image: H * W < 2^28, so 32 bits hold them)
+    const int oxh = y * G.W + hi, oxl = y * G.W + lo;
+    axis_stencil(valid ? y : 0, G.H, G.py, lo, hi, cyo);
+    const int oyh = hi * G.W + x, oyl = lo * G.W + x;
+    axis_stencil(hvalid ? hx : 0, G.W, G.px, lo, hi, cxh);
+    const int hxh = hy * G.W + hi, hxl = hy * G.W + lo;
+    axis_stencil(hvalid ? hy : 0, G.H, G.py, lo, hi, cyh);
+    const int hyh = hi * G.W + hx, hyl = lo * G.W + hx;
+    const int qo = y * G.W + x, qh = hy * G.W + hx;
+    auto state = [](float xh, float xl, float yh, float yl, float cx, float cy) {
+        PixelState st;
+        st.dx = (xh - xl) * cx;
+        st.dy = (yh - yl) * cy;
+        st.r = rsqrtf(fmaf(st.dx, st.dx, fmaf(st.dy, st.dy, 1.f)));
+        st.nx = st.dx * st.r;
+        st.ny = st.dy * st.r;
+        return st;
     };
     const int64_t chunk = (B + gridDim.z - 1) / gridDim.z;
     const int64_t c0 = static_cast<int64_t>(blockIdx.z) * chunk, c1 = min(c0 + chunk, B);
-    int64_t pending = -1;
-    for (int64_t base = c0; base < c1; base += 32) {
-        const int sid = base + lane < c1 ? __ldg(sensor_id + base + lane) : -1;
-        unsigned mask = __ballot_sync(0xffffffffu, sid == s);     // the same in every warp
-        while (mask != 0u) {
-            const int j = __ffs(mask) - 1;
-            mask &= mask - 1u;
-            if (pending < 0) {
-                pending = base + j;
-            } else {
-                process(pending, base + j);
-                pending = -1;
+    for (int64_t seg = c0; seg < c1; seg += kCgSeg) {
+        const int64_t seg_end = min(seg + kCgSeg, c1);
+        if (t < 32) {       // warp 0 lists the segment's images of sensor s
+            int n = 0;
+            for (int64_t base = seg; base < seg_end; base += 32) {
+                const int sid = base + lane < seg_end ? __ldg(sensor_id + base + lane) : -1;
+                const unsigned mask = __ballot_sync(0xffffffffu, sid == s);
+                if (sid == s) list[n + __popc(mask & ((1u << lane) - 1u))] = static_cast<int>(base + lane);
+                n += __popc(mask);
             }
+            if (lane == 0) list_n = n;
         }
+        __syncthreads();
+        const int n = list_n;
+        auto issue = [&](int i) {
+            if (i < n) {
+                const int64_t b = list[i];
+                const float* D = depth + b * G.HW;
+                const float* U = u_inten + b * G.HW * 3;
+                float* st = &ring[i % kDgStages][0][t];
+                if (valid) {
+                    cp_async4(st + 0 * 256, D + oxh);
+                    cp_async4(st + 1 * 256, D + oxl);
+                    cp_async4(st + 2 * 256, D + oyh);
+                    cp_async4(st + 3 * 256, D + oyl);
+                    cp_async4(st + 4 * 256, U + 3 * qo);
+                    cp_async4(st + 5 * 256, U + 3 * qo + 1);
+                    cp_async4(st + 6 * 256, U + 3 * qo + 2);
+                }
+                if (hvalid) {
+                    cp_async4(st + 7 * 256, D + hxh);
+                    cp_async4(st + 8 * 256, D + hxl);
+                    cp_async4(st + 9 * 256, D + hyh);
+                    cp_async4(st + 10 * 256, D + hyl);
+                    cp_async4(st + 11 * 256, U + 3 * qh);
+                    cp_async4(st + 12 * 256, U + 3 * qh + 1);
+                    cp_async4(st + 13 * 256, U + 3 * qh + 2);
+                }
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int i = 0; i < kDgStages - 1; ++i) issue(i);
+        for (int i = 0; i < n; ++i) {
+            issue(i + kDgStages - 1);
+            cp_async_wait<kDgStages - 1>();          // this thread's copies of image i have landed
+            const float* st = &ring[i % kDgStages][0][t];
+            if (valid) {
+                const float u[3] = {st[4 * 256], st[5 * 256], st[6 * 256]};
+                float gx, gy;
+                pixel_backward_reg<kMse>(a, state(st[0], st[256], st[2 * 256], st[3 * 256], cxo, cyo), u, w2, gx, gy);
+                gx_s[ty][tx + 1] = gx;
+                gy_s[ty + 1][tx] = gy;
+            }
+            if (hvalid) {
+                const float u[3] = {st[11 * 256], st[12 * 256], st[13 * 256]};
+                float gx, gy;
+                pixel_backward_reg<kMse>(ah, state(st[7 * 256], st[8 * 256], st[9 * 256], st[10 * 256], cxh, cyh), u,
+                                         w2, gx, gy);
+                if (haxis == 0) gx_s[hy - y0][hx - x0 + 1] = gx;
+                else gy_s[hy - y0 + 1][hx - x0] = gy;
+            }
+            __syncthreads();
+            if (valid) {
+                float acc = sl[0].w * gx_s[ty][sl[0].qx - x0 + 1];
+                acc = fmaf(sl[1].w, gx_s[ty][sl[1].qx - x0 + 1], acc);
+                acc = fmaf(sl[2].w, gy_s[sl[2].qy - y0 + 1][tx], acc);
+                acc = fmaf(sl[3].w, gy_s[sl[3].qy - y0 + 1][tx], acc);
+                grad_depth[static_cast<int64_t>(list[i]) * G.HW + qo] = acc;
+            }
+            __syncthreads();
+        }
+        cp_async_wait<0>();
     }
-    if (pending >= 0) process(pending, int64_t(-1));
 }
 
 // Zeroes the depth gradient of every image whose sensor id is out of range (the
