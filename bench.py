@@ -1127,6 +1127,11 @@ def run_serve(args, rank, world, local_rank, dist):
         srv.wait(rid)
     srv_sat_s = time.perf_counter() - t0
     srv_sat = sum(n_taxel[int(i)] for i in order) / srv_sat_s
+    # host<->device bytes of each request (its pinned inputs in, its outputs back)
+    req_bytes = [sum(t[k].numel() * t[k].element_size() for k in keys) +
+                 sum(v.numel() * v.element_size() for v in outs[i].values()) for i, t in enumerate(tpl)]
+    srv_copy_gbs = sum(req_bytes[int(i)] for i in order) / srv_sat_s / 1e9
+    plain_copy_gbs = sum(req_bytes) / svc.sum() / 1e9
 
     def run_stream(rate, serve_fn):
         gaps = g.exponential(1.0 / rate, size=len(order))
@@ -1170,10 +1175,11 @@ def run_serve(args, rank, world, local_rank, dist):
         "workload": SERVE_WORKLOAD, "templates": len(tpl), "requests_per_run": int(len(order)),
         "template_envs": [t["n_env"] for t in w.templates], "mean_envs_per_request": mean_env,
         "unit": "taxel-points/s", "generation_s": t_gen, "hbm_budget_bytes": budget, "n_streams": args.serve_streams,
-        "plain": {"saturation": plain_sat, "saturation_req_per_s": plain_rate,
+        "mean_bytes_per_request": float(np.mean([req_bytes[int(i)] for i in order])),
+        "plain": {"saturation": plain_sat, "saturation_req_per_s": plain_rate, "copy_gb_per_s": plain_copy_gbs,
                   "service_ms": {"mean": float(1e3 * svc.mean()), "max": float(1e3 * svc.max())},
                   "path": "per request: tacsl_batch_plan/upload, copies in, tacsl_batch_step, copies out, synchronise"},
-        "server": {"saturation": srv_sat, "saturation_speedup": srv_sat / plain_sat,
+        "server": {"saturation": srv_sat, "saturation_speedup": srv_sat / plain_sat, "copy_gb_per_s": srv_copy_gbs,
                    "batches": st["batches"], "max_batch_requests": st["max_batch_requests"],
                    "arena_peak_bytes": st["arena_peak_bytes"]},
         "poisson": streams,
