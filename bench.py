@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--e2e-chunk", type=int, default=256)
+    ap.add_argument("--e2e-chunk", type=int, default=128)
     ap.add_argument("--oracle-seconds", type=float, default=6.0,
                     help="seconds of FP64 oracle time per NEXT-row baseline (render, batch, grad)")
     ap.add_argument("--no-e2e", action="store_true")
