@@ -332,11 +332,13 @@ def _host_t(t, dtype, name):
 
 
 def tactile_step_host(sdfs: SdfSet, params: ContactParams, taxels, obj_id, pad_pose, pad_twist,
-                      shading: Shading | None = None, sensor_id=None, depth_map=None, out=None, chunk_envs=512,
+                      shading: Shading | None = None, sensor_id=None, depth_map=None, out=None, chunk_envs=128,
                       workspace=None, stream=None):
     """tactile_step with the per-step arrays in host memory (pinned for overlap): obj_id,
     pad_pose, pad_twist, sensor_id, depth_map in; (depth, f_n, f_t, wrench, rgb) host
-    tensors out, written when the stream reaches the end of the call."""
+    tensors out, written when the stream reaches the end of the call.  chunk_envs: envs
+    per pipelined chunk (128 measured best for 2-pad envs with 320x240 images: smaller
+    chunks shorten the pipeline's head and tail, where only one direction copies)."""
     _dev(taxels, torch.float32, "taxels")
     for t, n, dt in ((obj_id, "obj_id", torch.int32), (pad_pose, "pad_pose", torch.float32),
                      (pad_twist, "pad_twist", torch.float32)):
