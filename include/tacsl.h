@@ -67,7 +67,7 @@ typedef struct CUstream_st* tacsl_stream_t;
 #define TACSL_MAX_SENSOR 16   /* sensor models per call */
 #define TACSL_MAX_TAXELS 65536
 
-/* One object's signed-distance grid (Sec. III-C: "the SDF of the contacting object").
+/* One object's signed-distance grid (Sec. III-C: each contacting object carries an SDF).
  * Node (i, j, k) sits at origin + (i, j, k) * voxel; data is [n[2]][n[1]][n[0]],
  * x fastest, negative inside the object.  n[k] >= 3; n0*n1*n2 < 2^31. */
 typedef struct {
@@ -130,8 +130,8 @@ int32_t tacsl_abi_version(void);
 int tacsl_check_errors(tacsl_stream_t stream, uint32_t* flags, int32_t clear);
 
 /*
- * SDF query with gradient (Sec. III-C: d from "querying the SDF ... at the tactile
- * points"; the gradient "calculated using finite differencing").
+ * SDF query with gradient (Sec. III-C: the penetration depth is read from the object's
+ * SDF at each tactile point, and its gradient is taken by finite differences).
  *   pts    [n][3] object-frame points;  obj_id [n] grid per point.
  *   phi    [n]    trilinear interpolation of the grid at the point;
  *   grad   [n][3] central difference of that interpolant with step voxel/2 per axis.
@@ -207,9 +207,9 @@ int tacsl_tactile_step(const tacsl_sdf_set* set, const tacsl_contact_params* par
                        const float* depth_map, uint8_t* rgb, tacsl_stream_t stream);
 
 /*
- * Depth maps of the E x P pads (Sec. III-B: "render a depth image I_depth showing the
- * indenting object" from a camera inside the sensor; the paper does this with a graphics
- * render, here it is a CUDA column march against the posed SDF).
+ * Depth maps of the E x P pads (Sec. III-B: a camera inside the sensor sees the depth of
+ * the indenting object; the paper does this with a graphics render, here it is a CUDA
+ * column march against the posed SDF).
  *   depth_map [E][P][H][W] float32 (16-byte aligned):
  *     D = d0 - max(0, -z_hit), z_hit = the first point of the object on the pixel's column
  *     over [-z_max, 0] (marching up from -z_max), D = d0 where the column misses it.

@@ -11,7 +11,7 @@
  *       tactile points, d' = (grad d)^T x' by the chain rule, n = grad d by
  *       finite differences.
  *   Eq. 3 (Kelvin-Voigt): the contact force is unilateral -> clamp at zero.
- *   Sec. III-B and App. "Tactile Image Visualization": I_rgb = F(I_depth) with
+ *   Sec. III-B and App. F (tactile image visualisation): I_rgb = F(I_depth) with
  *       F a calibrated per-pixel polynomial table; read here as a quadratic in
  *       the depth-map normal (n_x, n_y) with per-pixel coefficients.
  */

@@ -13,9 +13,9 @@
  *
  * Readings of the paper where it is silent (each one also stated in the .c file):
  *   - the SDF is trilinear between nodes at origin + i*voxel (Sec. III-C says only
- *     "querying the SDF");
+ *     that the SDF is queried);
  *   - the gradient is the central difference of that interpolant with step
- *     voxel/2 per axis (Sec. III-C: "finite differencing");
+ *     voxel/2 per axis (Sec. III-C names finite differences, no scheme or step);
  *   - a point is in the grid's domain iff every continuous index u lies in
  *     [0.5, n-1.5]; outside, phi = +inf, gradient 0, no force;
  *   - the normal force is clamped at zero (the unilateral law of Eq. 3);
