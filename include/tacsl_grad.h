@@ -3,7 +3,7 @@
  * status codes as in tacsl.h).
  *
  * Calibrating a tactile sensor model means fitting the contact parameters (the paper
- * measures the contact stiffness of its pads, Sec. VI-A) and the image model (the
+ * measures the contact stiffness of its pads, App. B) and the image model (the
  * calibrated depth-to-RGB mapping of Sec. III-B) to observations.  These entry points
  * give the gradients such a fit needs, computed by hand-written adjoint kernels:
  *   - of the force field and wrenches (Sec. III-C) w.r.t. each pad's pose and twist and

@@ -243,7 +243,7 @@ def shade_mse(coeffs, pitch_x, pitch_y, sensor_id, depth, target):
     """Squared error of the clamped intensities against target images [B, H, W, 3]:
     L = sum_s loss_map[s], loss_map[s, y, x] = sum over the images b of sensor s and the
     channels c of (clamp(I_c(b, y, x), 0, 255) - target[b, y, x, c])^2 (the image loss of
-    sensor calibration, Sec. VI-A, on the intensity of reading c16).  Returns dict
+    sensor calibration, App. B and Sec. III-B, on the intensity of reading c16).  Returns dict
     loss_map [S, H, W], coeffs [S, 6, 3, H, W] and depth [B, H, W] (gradients of L)."""
     coeffs = np.asarray(coeffs, np.float32)
     S, _, _, H, W = coeffs.shape

@@ -1,6 +1,6 @@
 // Hand-written adjoints of the tactile step, for calibrating the sensor and contact
 // models from observed force fields and images (the use the paper makes of measured
-// contact stiffness, Sec. VI-A, and of a calibrated image model, Sec. III-B).
+// contact stiffness, App. B, and of a calibrated image model, Sec. III-B).
 //
 // Force field (Sec. III-C).  For an upstream gradient of the depth, normal and shear
 // force fields and of the per-pad wrench, the kernel returns the gradient w.r.t. each

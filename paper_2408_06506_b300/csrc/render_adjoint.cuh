@@ -1,5 +1,5 @@
 // Adjoint of the depth render w.r.t. the pad poses (the pose -> depth -> image chain of
-// sensor calibration, Sec. VI-A of arXiv 2408.06506, through the column camera of
+// sensor calibration, App. B of arXiv 2408.06506, through the column camera of
 // Sec. III-B).
 //
 // A column that meets the object at z_hit in (-z_max, 0) reads D = d0 + z_hit, where
