@@ -239,6 +239,27 @@ def test_render_adjoint_rejects(lib):
     assert f(C.byref(st), 0, 2, FAKE, FAKE, C.byref(cam), FAKE, FAKE, FAKE, None) == 0
 
 
+def test_shade_mse_rejects(lib):
+    from paper_2408_06506_b300 import autograd as ta
+    f = ta._lib().tacsl_shade_mse
+    sh = _shading()
+    ok = dict(sid=FAKE, dm=FAKE, tgt=FAKE, scale=None, lm=FAKE, gc=FAKE, gd=FAKE)
+
+    def call(shading=sh, B=4, **kw):
+        a = dict(ok, **kw)
+        return f(C.byref(shading) if shading is not None else None, B, a["sid"], a["dm"], a["tgt"], a["scale"],
+                 a["lm"], a["gc"], a["gd"], None)
+
+    assert call(shading=None) == INVALID
+    assert call(shading=_shading(W=18)) == INVALID
+    assert call(B=-1) == INVALID
+    assert call(tgt=0) == INVALID                 # the target stands where the image output would
+    assert call(sid=0) == INVALID and call(dm=FAKE + 4) == INVALID
+    for k in ("tgt", "scale", "lm", "gc", "gd"):  # 4-byte alignment of the other arrays
+        assert call(**{k: FAKE + 2}) == INVALID, k
+    assert call(B=0, lm=None, gc=None, gd=None) == 0   # nothing to do
+
+
 def test_render_step_requires_matching_camera(lib):
     st, prm, cam = _set(_sdf()), _params(), _camera(H=8, W=16)
     sh = _shading(H=12, W=16)
