@@ -333,16 +333,15 @@ __global__ void __launch_bounds__(256) sdf_query_kernel(const SdfTable tab, int6
     }
 }
 
-// One warp per pad, eight pads per CTA, grid-stride over pads.
-__global__ void __launch_bounds__(256) penalty_kernel(const SdfTable tab, const Params4 prm, int64_t B, int P, int T,
+// One warp per pad and per CTA, grid-stride over pads.
+__global__ void __launch_bounds__(32) penalty_kernel(const SdfTable tab, const Params4 prm, int64_t B, int P, int T,
                                                       const float* __restrict__ taxels,
                                                       const int32_t* __restrict__ obj_id,
                                                       const float* __restrict__ pad_pose,
                                                       const float* __restrict__ pad_twist, float* __restrict__ depth,
                                                       float* __restrict__ f_n, float* __restrict__ f_t,
                                                       float* __restrict__ wrench) {
-    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * 8;
-    for (int64_t b = static_cast<int64_t>(blockIdx.x) * 8 + (threadIdx.x >> 5); b < B; b += nwarps)
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x)
         pad_by_warp<4>(tab, prm, P, T, taxels, obj_id, pad_pose, pad_twist, depth, f_n, f_t, wrench, b);
 }
 
