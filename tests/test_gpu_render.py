@@ -115,3 +115,70 @@ def test_render_step_equals_render_then_step(orc):
     ref_rgb, ref_I, _ = orc.shade(sc.coeffs, sc.pitch_x, sc.pitch_y, sc.sensor_id, dmap.cpu().numpy(),
                                   with_intensity=True)
     assert_rgb_close(rgb.cpu().numpy(), ref_rgb, ref_I)
+
+
+def _half_space_grid(nrm, n=64, h=0.5e-3):
+    nrm = np.asarray(nrm, np.float64) / np.linalg.norm(nrm)
+    return synth.bake_field(lambda x, y, z: nrm[0] * x + nrm[1] * y + nrm[2] * z, (n, n, n), h,
+                            [-(n - 1) * h / 2] * 3), nrm
+
+
+def _render_one(grid, pose, cam):
+    sdfs = tacsl.SdfSet.from_grids([grid])
+    return tacsl.render_depth(sdfs, tacsl.Camera(**cam), dev(np.zeros(1, np.int32)),
+                              dev(np.asarray(pose, np.float32).reshape(1, 1, 7))).cpu().numpy()[0, 0]
+
+
+def test_render_tilted_half_space_closed_form():
+    """A half-space tilted against the pad: the first point inside on each column is
+    z = -(n . p0) / (n . R e_z), to the march's resolution voxel * 2^-16 plus float32
+    rounding of the grid index (a few 1e-9 m)."""
+    grid, nrm = _half_space_grid([0.3, -0.2, 1.0])
+    q = synth.quat_multiply(synth.quat_multiply([0.0, 1.0, 0.0, 0.0], synth.quat_from_axis_angle([1.0, 0.5, 0.0], 0.1)),
+                            synth.quat_from_axis_angle([0.0, 0.0, 1.0], 0.7))
+    R = synth.quat_to_matrix(np.asarray(q) / np.linalg.norm(q))
+    pose = np.concatenate([-1.5e-3 * nrm + R @ np.array([0.3e-3, -0.2e-3, 0.0]), q]).astype(np.float32)
+    H, W, pitch = 8, 12, 0.5e-3
+    cam = dict(H=H, W=W, pitch_x=pitch, pitch_y=pitch, x0=-(W - 1) / 2 * pitch, y0=-(H - 1) / 2 * pitch,
+               d0=synth.D0, z_max=3e-3)
+    D = _render_one(grid, pose, cam)
+    Rf = synth.quat_to_matrix(pose[3:].astype(np.float64) / np.linalg.norm(pose[3:].astype(np.float64)))
+    f32 = np.float32
+    xs = float(f32(cam["x0"])) + np.arange(W) * float(f32(pitch))
+    ys = float(f32(cam["y0"])) + np.arange(H) * float(f32(pitch))
+    yy, xx = np.meshgrid(ys, xs, indexing="ij")
+    p0 = np.stack([xx, yy, np.zeros_like(xx)], -1) @ Rf.T + pose[:3].astype(np.float64)
+    zc = -(p0 @ nrm) / (nrm @ Rf[:, 2])
+    assert zc.max() < -1e-4 and zc.min() > -3e-3 + 1e-4
+    want = float(f32(synth.D0)) + zc
+    assert np.abs(D - want).max() <= grid.voxel / 65536 + 2e-8
+
+
+def test_render_clamp_and_miss_exact():
+    """An object below the camera's range reads exactly d0 - z_max (float32), a pad with a
+    gap exactly d0, on every column."""
+    grid, nrm = _half_space_grid([0.0, 0.0, 1.0], n=48)
+    H, W, pitch = 8, 12, 0.5e-3
+    cam = dict(H=H, W=W, pitch_x=pitch, pitch_y=pitch, x0=-(W - 1) / 2 * pitch, y0=-(H - 1) / 2 * pitch,
+               d0=synth.D0, z_max=3e-3)
+    flip = [0.0, 1.0, 0.0, 0.0]          # pad +z along -n: the column rises into the half-space
+    deep = _render_one(grid, np.concatenate([[0.0, 0.0, -5e-3], flip]), cam)
+    assert (deep == np.float32(np.float32(synth.D0) - np.float32(3e-3))).all()
+    gap = _render_one(grid, np.concatenate([[0.0, 0.0, 5e-4], flip]), cam)
+    assert (gap == np.float32(synth.D0)).all()
+
+
+def test_render_columns_leaving_the_grid(orc):
+    """A sphere's grid (a 15.5 mm box) under a 48 x 38 mm camera: most columns never enter
+    the grid's domain and many cross its boundary part-way; parity with the oracle."""
+    sc = synth.scene_sphere_pad(seed=15, E=12)
+    d = scene_to_device(sc)
+    W, H = 64, 48
+    cam = dict(H=H, W=W, pitch_x=48e-3 / W, pitch_y=38e-3 / H, x0=-24e-3 + 24e-3 / W, y0=-19e-3 + 19e-3 / H,
+               d0=synth.D0, z_max=3e-3)
+    g = sc.grids[0]
+    span = (np.asarray(g.data.shape) - 2) * g.voxel
+    assert span.max() < 0.5 * 38e-3              # the camera is much wider than the domain
+    D = tacsl.render_depth(d["sdfs"], tacsl.Camera(**cam), d["obj_id"], d["pose"]).cpu().numpy()
+    _check_render(orc, sc, d["sdfs"], D, cam)
+    assert (D < np.float32(synth.D0)).any() and (D == np.float32(synth.D0)).mean() > 0.5
