@@ -47,13 +47,15 @@ struct CellCacheF {
 };
 
 // phi at a continuous grid index u inside the domain: trilinear in the cell
-// min(floor(u), n - 2) (clamped at 0, which also keeps the loads in bounds whatever u
-// rounds to), nodes re-read only when the cell changes.
+// min(floor(u), n - 2), nodes re-read only when the cell changes.  The caller samples
+// only the slab where every u_a lies in [0.5, n_a - 1.5] (up to ~1e-5 of rounding), so
+// floor(u) is already in [0, n - 2]; fmaxf maps a NaN index (a degenerate pose) to cell
+// 0, which keeps the loads in bounds.
 __device__ __forceinline__ float column_phi_in(const DevSdf& S, float ux, float uy, float uz, uint64_t pol,
                                                CellCacheF& cc) {
-    const float cx = fminf(fmaxf(floorf(ux), 0.f), static_cast<float>(S.n0 - 2));
-    const float cy = fminf(fmaxf(floorf(uy), 0.f), static_cast<float>(S.n1 - 2));
-    const float cz = fminf(fmaxf(floorf(uz), 0.f), static_cast<float>(S.n2 - 2));
+    const float cx = fmaxf(floorf(ux), 0.f);
+    const float cy = fmaxf(floorf(uy), 0.f);
+    const float cz = fmaxf(floorf(uz), 0.f);
     if (cx != cc.cx || cy != cc.cy || cz != cc.cz) {
         const int n0 = S.n0, n01 = S.n0 * S.n1;
         const float* b = S.data + (static_cast<int64_t>(static_cast<int>(cz)) * n01 +
