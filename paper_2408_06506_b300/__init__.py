@@ -117,9 +117,18 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+# The current stream's raw handle: torch's accessor returns it without building a Stream
+# object (which costs ~0.1 ms per call); the public call is the fallback.
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+_cur_device = getattr(torch._C, "_cuda_getDevice", None)
+
+
 def _stream(stream):
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return C.c_void_p(s.cuda_stream)
+    if stream is not None:
+        return C.c_void_p(stream.cuda_stream)
+    if _raw_stream is not None and _cur_device is not None:
+        return C.c_void_p(_raw_stream(_cur_device()))
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
 def _dev(t: torch.Tensor, dtype, name: str):
