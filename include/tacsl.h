@@ -23,7 +23,8 @@
  *     call returns a nonzero status, launches nothing and writes no output, and
  *     tacsl_last_error() describes the problem.
  *   - A zero-sized batch (n, E, P, T or B equal to 0) returns TACSL_OK and launches
- *     nothing.
+ *     nothing, except that per-sensor sums over images (the coefficient gradient and
+ *     loss map of tacsl_grad.h) are still written, as zeros.
  *   - Values that only exist on the device (object ids, sensor ids) are checked by the
  *     kernels: a bad one poisons the affected outputs as documented and sets a bit
  *     in the device error word, read with tacsl_check_errors().
