@@ -1,5 +1,7 @@
 """GPU parity of depth-map rendering (the column march of the in-sensor camera,
 Sec. III-B) against the FP64 oracle, and of the render-from-poses step."""
+from types import SimpleNamespace
+
 import numpy as np
 import pytest
 import torch
@@ -182,3 +184,26 @@ def test_render_columns_leaving_the_grid(orc):
     D = tacsl.render_depth(d["sdfs"], tacsl.Camera(**cam), d["obj_id"], d["pose"]).cpu().numpy()
     _check_render(orc, sc, d["sdfs"], D, cam)
     assert (D < np.float32(synth.D0)).any() and (D == np.float32(synth.D0)).mean() > 0.5
+
+
+def test_render_full_workload_sampled(orc):
+    """The 4096-env object scene (8192 maps of 320x240, the benchmark's launch): 12
+    sampled pads against the oracle's march, pad by pad, under the same rules."""
+    sc = synth.scene_objects(seed=2, E=4096, P=2, depth_maps="none")
+    H, W = 240, 320
+    px, py = 24e-3 / W, 19e-3 / H
+    cam = dict(H=H, W=W, pitch_x=px, pitch_y=py, x0=-px * W / 2 + 0.5 * px, y0=-py * H / 2 + 0.5 * py,
+               d0=synth.D0, z_max=3e-3)
+    sdfs = tacsl.SdfSet.from_grids(sc.grids)
+    D = tacsl.render_depth(sdfs, tacsl.Camera(**cam), dev(sc.obj_id), dev(sc.pad_pose))
+    torch.cuda.synchronize()
+    assert tacsl.check_errors() == 0
+    hits = (D < np.float32(synth.D0)).reshape(sc.E * sc.P, -1).sum(1).cpu().numpy()
+    rng = np.random.default_rng(8)
+    picks = np.concatenate([rng.choice(np.flatnonzero(hits > 1000), 8, replace=False),
+                            rng.choice(np.flatnonzero(hits == 0), 4, replace=False)])
+    for b in picks:
+        e, p = divmod(int(b), sc.P)
+        one = SimpleNamespace(grids=sc.grids, P=1, obj_id=sc.obj_id[e:e + 1],
+                              pad_pose=np.ascontiguousarray(sc.pad_pose[e:e + 1, p:p + 1]))
+        _check_render(orc, one, sdfs, D[e:e + 1, p:p + 1].cpu().numpy(), cam)
