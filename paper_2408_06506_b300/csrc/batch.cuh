@@ -254,12 +254,10 @@ __global__ void __launch_bounds__(kShThreads, 1) batch_shade_kernel(const BatchS
         return;
     }
 
-    const uint64_t pol_stream = policy_evict_first();
-    uint8_t* my_staging = smem + kOffStaging + warp * (kShStagingRing * kShWarpStaging);
     TileGeom g;
     TileCoefs c;
     int cur_item = -1;
-    int st = 0, wbuf = 0;
+    int st = 0;
     uint32_t ph = 0, cph = 0;
     for (;;) {
         if (!mbar_wait_bounded(smem_u32(&full[st]), ph)) {
@@ -285,9 +283,7 @@ __global__ void __launch_bounds__(kShThreads, 1) batch_shade_kernel(const BatchS
         const int64_t px0 = __ldg(A.img_px + m.x);
         uint32_t w0, w1, w2;
         shade_four(stages + static_cast<int64_t>(st) * A.stage_floats, g, c, &empty[st], lane, w0, w1, w2);
-        store_warp_vec(A.rgb + (px0 + g.tile_start + warp * kShWarpPx) * 3, my_staging + wbuf * kShWarpStaging, lane,
-                       g.warp_px, w0, w1, w2, pol_stream);
-        wbuf ^= 1;
+        if (g.px_valid) store_words(A.rgb + (px0 + g.tile_start + 4 * tid) * 3, w0, w1, w2);
         if (++st == NS) { st = 0; ph ^= 1u; }
     }
 }

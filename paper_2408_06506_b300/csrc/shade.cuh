@@ -18,13 +18,13 @@
 //   coefficient full/empty barrier pair), so switching items costs a shared-memory
 //   copy into registers, not an L2 round trip.
 // * Arithmetic runs on FP32 pairs (f32x2), quantisation uses two FP instructions and a
-//   saturating byte pack per value, horizontal neighbours come by warp shuffle.
+//   saturating byte pack per value; horizontal neighbours are read from shared memory.
 // * Sparsity of contact: a warp whose 128 pixels all have equal neighbours (the
 //   undeformed gel) writes the item's background bytes, which are exactly what the
 //   full evaluation gives for n = (0, 0, -1).
-// * Each warp transposes its 128 pixels' RGB (384 bytes) through a private staging
-//   buffer and writes them with 16-byte stores; L2 policies mark the depth and RGB
-//   streams evict-first and the coefficients evict-last.
+// * Each thread writes its four pixels' RGB as three 4-byte words straight to global
+//   memory (L2 merges a warp's 384 contiguous bytes into whole sectors); L2 policies
+//   mark the depth stream evict-first and the coefficients evict-last.
 #pragma once
 
 #include "common.cuh"
@@ -37,8 +37,6 @@ constexpr int kShConsumers = kShConsumerWarps * 32;        // 480 compute thread
 constexpr int kShThreads = kShConsumers + 32;              // + one producer warp
 constexpr int kShTile = kShConsumers * 4;                  // pixels per tile, 4 per thread
 constexpr int kShWarpPx = 128;                             // pixels per compute warp
-constexpr int kShWarpStaging = kShWarpPx * 3;              // RGB bytes per warp and tile
-constexpr int kShStagingRing = 2;                          // staging buffers per warp
 constexpr int kShMaxStages = 16;
 constexpr int kShCoefFloats = 18 * kShTile;                // one tile's shading coefficients
 
@@ -48,16 +46,14 @@ constexpr int kOffEmpty = kOffFull + kShMaxStages * 8;             // kShMaxStag
 constexpr int kOffCoefFull = kOffEmpty + kShMaxStages * 8;         // u64
 constexpr int kOffCoefEmpty = kOffCoefFull + 8;                    // u64
 constexpr int kOffMeta = kOffCoefEmpty + 8;                        // kShMaxStages x int2 (image, item)
-constexpr int kOffRed = kOffMeta + kShMaxStages * 8;               // kShConsumerWarps x 6 f32
-constexpr int kOffStaging = ((kOffRed + kShConsumerWarps * 6 * 4) + 127) / 128 * 128;
-constexpr int kOffCoef = kOffStaging + kShConsumerWarps * kShStagingRing * kShWarpStaging;
+constexpr int kOffCoef = ((kOffMeta + kShMaxStages * 8) + 127) / 128 * 128;
 constexpr int kOffStage = kOffCoef + kShCoefFloats * 4;
 
 __host__ __device__ constexpr int shade_smem_bytes(int n_stages, int stage_floats) {
     return kOffStage + n_stages * stage_floats * 4;
 }
 
-enum StoreMode { kStoreVec = 0, kStoreWord = 1, kStoreByte = 2 };
+enum StoreMode { kStoreWord = 0, kStoreByte = 1 };
 
 struct ShadeArgs {
     const float* coeffs;        // [S][6][3][HW], 16-byte aligned
@@ -142,12 +138,6 @@ __device__ __forceinline__ uint32_t pack_u8x4(uint32_t b0, uint32_t b1, uint32_t
     asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, 0;" : "=r"(h) : "r"(b3), "r"(b2));
     asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(w) : "r"(b1), "r"(b0), "r"(h));
     return w;
-}
-
-__device__ __forceinline__ void stg_v4_hint(void* p, uint4 v, uint64_t pol) {
-    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
-                 "r"(v.w), "l"(pol)
-                 : "memory");
 }
 
 // Does block `it` hold an image of sensor it.s?  (Warp-uniform; flags bad sensor ids once
@@ -362,12 +352,9 @@ __device__ __forceinline__ void shade_four(const float* sp, const TileGeom& g, c
     const float4 cv = *reinterpret_cast<const float4*>(sp + g.oc);
     const ulonglong2 up = *reinterpret_cast<const ulonglong2*>(sp + g.ou);
     const ulonglong2 dn = *reinterpret_cast<const ulonglong2*>(sp + g.od);
-    float L = __shfl_up_sync(0xffffffffu, cv.w, 1);
-    float R = __shfl_down_sync(0xffffffffu, cv.x, 1);
-    if (lane == 0) L = sp[g.oL];
-    if (lane == 31) R = sp[g.oR];
-    L = g.hasL ? L : cv.x;
-    R = g.hasR ? R : cv.w;
+    // horizontal neighbours: oL / oR already point at the edge pixel itself on the border
+    const float L = sp[g.oL];
+    const float R = sp[g.oR];
     __syncwarp();
     if (lane == 0) mbar_arrive(smem_u32(empty_bar));   // this warp is done with the stage
 
@@ -416,16 +403,16 @@ __device__ __forceinline__ void shade_four(const float* sp, const TileGeom& g, c
                    __float_as_uint(hi(q[1][2])));
 }
 
-// The warp's 128 pixels (384 bytes) starting at dst, 16-byte aligned: a transpose
-// through the warp's staging buffer, then one 16-byte store per lane.
-__device__ __forceinline__ void store_warp_vec(uint8_t* dst, uint8_t* staging, int lane, int warp_px, uint32_t w0,
-                                               uint32_t w1, uint32_t w2, uint64_t pol) {
-    uint32_t* sg = reinterpret_cast<uint32_t*>(staging);
-    sg[3 * lane] = w0;
-    sg[3 * lane + 1] = w1;
-    sg[3 * lane + 2] = w2;
-    __syncwarp();
-    if (lane * 16 < warp_px * 3) stg_v4_hint(dst + 16 * lane, reinterpret_cast<const uint4*>(sg)[lane], pol);
+// This thread's four pixels' RGB (12 bytes at dst, 4-byte aligned) as three plain word
+// stores.  A warp's stores cover 384 contiguous bytes, which L2 merges into whole
+// sectors.  Measured on 8192 images of 320x240: 0.78 ms, against 0.80 ms with an
+// evict-first hint on each store, 0.87 ms with an 8-byte plus a 4-byte store, and
+// 0.88 ms through a shared-memory transpose to 16-byte stores.
+__device__ __forceinline__ void store_words(uint8_t* dst, uint32_t w0, uint32_t w1, uint32_t w2) {
+    uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
+    d32[0] = w0;
+    d32[1] = w1;
+    d32[2] = w2;
 }
 
 // Barrier set-up shared by both image kernels (thread 0, then a block barrier).
@@ -463,12 +450,10 @@ __global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A)
     }
 
     // ---- compute warps ----
-    const uint64_t pol_stream = policy_evict_first();
-    uint8_t* my_staging = smem + kOffStaging + warp * (kShStagingRing * kShWarpStaging);
     TileGeom g;
     TileCoefs c;
     int cur_item = -1;
-    int st = 0, wbuf = 0;
+    int st = 0;
     uint32_t ph = 0, cph = 0;
     for (;;) {
         if (!mbar_wait_bounded(smem_u32(&full[st]), ph)) {
@@ -494,15 +479,10 @@ __global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A)
         uint32_t w0, w1, w2;
         shade_four(stages + static_cast<int64_t>(st) * A.stage_floats, g, c, &empty[st], lane, w0, w1, w2);
         const int64_t img = m.x;
-        if (A.store_mode == kStoreVec) {
-            store_warp_vec(A.rgb + (img * A.HW + g.tile_start + warp * kShWarpPx) * 3,
-                           my_staging + wbuf * kShWarpStaging, lane, g.warp_px, w0, w1, w2, pol_stream);
-            wbuf ^= 1;
-        } else if (g.px_valid) {
+        if (g.px_valid) {
             uint8_t* dst = A.rgb + (img * A.HW + g.tile_start + 4 * tid) * 3;
             if (A.store_mode == kStoreWord) {
-                uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
-                d32[0] = w0; d32[1] = w1; d32[2] = w2;
+                store_words(dst, w0, w1, w2);
             } else {
                 const uint32_t ws[3] = {w0, w1, w2};
 #pragma unroll

@@ -202,9 +202,7 @@ int plan_shade(const tacsl_shading* sh, int64_t B, const int32_t* sensor_id, con
     if (ns < 2)
         return fail(TACSL_ERR_UNSUPPORTED, "image width %d too large for the shared-memory pipeline", a.W);
     a.n_stages = ns;
-    if (aligned(rgb, 16) && a.HW % 16 == 0)
-        a.store_mode = kStoreVec;
-    else if (aligned(rgb, 4))
+    if (aligned(rgb, 4))
         a.store_mode = kStoreWord;
     else
         a.store_mode = kStoreByte;
