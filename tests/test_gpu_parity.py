@@ -196,7 +196,7 @@ def _shade_case(orc, B, H, W, S, seed, sensor_id=None, rgb_offset=0):
 @pytest.mark.parametrize("B,H,W,S", [
     (1, 120, 160, 1),      # config-1 image
     (64, 240, 320, 2),     # config-2 images, mixed sensors
-    (5, 37, 52, 3),        # single partial tile, HW % 16 != 0 (word stores)
+    (5, 37, 52, 3),        # single partial tile, HW % 16 != 0
     (9, 1, 64, 1),         # one row: no y derivative
     (11, 6, 4, 2),         # minimum width
     (3, 480, 640, 2),      # largest configured image (many tiles, wide halo)
@@ -213,7 +213,8 @@ def test_shade_image_parity(orc, B, H, W, S):
 
 @pytest.mark.parametrize("offset", [1, 4, 16])
 def test_shade_image_unaligned_output(orc, offset):
-    """Byte-, word- and bulk-store paths all give the same bytes."""
+    """An RGB buffer at any byte offset (byte stores at 1, word stores at 4 and 16) gives the
+    same bytes."""
     rgb, ref_rgb, ref_I, _ = _shade_case(orc, 7, 24, 32, 2, seed=offset, rgb_offset=offset)
     assert_rgb_close(rgb, ref_rgb, ref_I)
 
