@@ -7,8 +7,11 @@
 // on the column: D = d0 - max(0, -z_hit), z_hit searched over [-z_max, 0] from below.
 //
 // March: conservative sphere tracing up the column - step kappa*phi inside the grid
-// domain (kappa = 1/sqrt 3: the trilinear interpolant of a 1-Lipschitz field is at most
-// sqrt 3-Lipschitz, so a step cannot pass the surface), never less than voxel/8 - then
+// domain, kappa = 1/|d|_1 for the column's direction d = R e_z (each partial derivative
+// of the trilinear interpolant of a 1-Lipschitz field is at most 1 in magnitude, so along
+// d phi changes by at most |d|_1 per unit height, between 1 and sqrt 3: a step cannot
+// pass the surface; the isotropic bound 1/sqrt 3 took 6.09 against 5.53 ms for 8192
+// maps of 320x240), never less than voxel/8 - then
 // bisection of the first bracket down to voxel * 2^-16; z_hit is the bracket's upper
 // end.  phi is the trilinear interpolant of the force field (same cell rule and FMA
 // order as phi_cell8), so image and force field see the same SDF; outside the grid's
@@ -21,7 +24,11 @@
 // misses without further samples: by the same Lipschitz bound none of them could be
 // inside the object.  Samples are taken in grid-index space (u = (x - origin) / voxel,
 // affine in the column's height), not by posing each point; the current trilinear cell
-// and its 8 nodes stay in registers while samples remain in it.
+// and its 8 nodes stay in registers while samples remain in it.  The step itself is
+// longer than the reference march's isotropic kappa = 1/sqrt 3: both are conservative and
+// share the voxel/8 minimum step, so they can differ only on a column where the object
+// dips below it for less than that minimum step (92 of the 629M columns of the 4096-env
+// workload: a hit on one side, a miss on the other, the hit on the surface).
 //
 // One thread per column: a warp takes 32 neighbouring columns of a row, whose marches
 // take similar paths and whose SDF reads fall on neighbouring nodes.
@@ -88,7 +95,7 @@ __device__ __forceinline__ float column_phi_in(const DevSdf& S, float ux, float 
 struct __align__(16) RenderFrame {
     float u00[3];
     int id;          // object id, -1 when out of range
-    float ui[3], pad0;
+    float ui[3], kappa;   // kappa: march step per unit of phi, 1 / |R e_z|_1
     float uj[3], pad1;
     float du[3], pad2;
     float inv_du[3], pad3;
@@ -116,6 +123,7 @@ __device__ __forceinline__ void render_frame(const SdfTable& tab, const int32_t*
         f.du[a] = r[3 * a + 2] * S.inv_h;
         f.inv_du[a] = 1.f / f.du[a];
     }
+    f.kappa = 1.f / (fabsf(r[2]) + fabsf(r[5]) + fabsf(r[8]));
     f.id = id;
 }
 
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(256) render_kernel(const SdfTable tab, int64_t
             }
             float zhit = 1.f;   // > 0: no hit
             if (zlo <= zhi) {
-                const float dmin = S.h * 0.125f, kappa = 0.57735026918962576f;
+                const float dmin = S.h * 0.125f, kappa = F.kappa;
                 CellCacheF cc;
                 float z = zlo;
                 float phi = column_phi_in(S, fmaf(z, du0, u0), fmaf(z, du1, u1), fmaf(z, du2, u2), pol, cc);
