@@ -225,7 +225,7 @@ __device__ __forceinline__ void pad_taxels_by_warp(const SdfTable& tab, const Pa
     const float* r = Pz.r;
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int t0 = lane; t0 < T; t0 += 32 * NP) {
-        float p[NP][3], vel[NP][3], phi8[NP];
+        float p[NP][3], phi8[NP];
         GridPos gp[NP];
         bool on[NP];
 #pragma unroll
@@ -239,10 +239,6 @@ __device__ __forceinline__ void pad_taxels_by_warp(const SdfTable& tab, const Pa
             const float xo = fmaf(r[0], p[u][0], fmaf(r[1], p[u][1], fmaf(r[2], p[u][2], Pz.t[0])));
             const float yo = fmaf(r[3], p[u][0], fmaf(r[4], p[u][1], fmaf(r[5], p[u][2], Pz.t[1])));
             const float zo = fmaf(r[6], p[u][0], fmaf(r[7], p[u][1], fmaf(r[8], p[u][2], Pz.t[2])));
-            // relative velocity of the point: v + w x x
-            vel[u][0] = Pz.v[0] + (Pz.w[1] * zo - Pz.w[2] * yo);
-            vel[u][1] = Pz.v[1] + (Pz.w[2] * xo - Pz.w[0] * zo);
-            vel[u][2] = Pz.v[2] + (Pz.w[0] * yo - Pz.w[1] * xo);
             gp[u] = grid_pos(S, xo, yo, zo);
             gp[u].inside = gp[u].inside && on[u];
         }
@@ -254,8 +250,16 @@ __device__ __forceinline__ void pad_taxels_by_warp(const SdfTable& tab, const Pa
         for (int u = 0; u < NP; ++u) {
             if (!on[u]) continue;
             const int t = t0 + 32 * u;
-            float phi = phi8[u], g[3] = {0.f, 0.f, 0.f};
+            float phi = phi8[u], g[3] = {0.f, 0.f, 0.f}, vel[3] = {0.f, 0.f, 0.f};
             if (phi8[u] < 0.f) {
+                // relative velocity of the point, v + w x x (needed only in contact; the
+                // posed point is recomputed with the same operations as above)
+                const float xo = fmaf(r[0], p[u][0], fmaf(r[1], p[u][1], fmaf(r[2], p[u][2], Pz.t[0])));
+                const float yo = fmaf(r[3], p[u][0], fmaf(r[4], p[u][1], fmaf(r[5], p[u][2], Pz.t[1])));
+                const float zo = fmaf(r[6], p[u][0], fmaf(r[7], p[u][1], fmaf(r[8], p[u][2], Pz.t[2])));
+                vel[0] = Pz.v[0] + (Pz.w[1] * zo - Pz.w[2] * yo);
+                vel[1] = Pz.v[1] + (Pz.w[2] * xo - Pz.w[0] * zo);
+                vel[2] = Pz.v[2] + (Pz.w[0] * yo - Pz.w[1] * xo);
                 // penetrating: the 27-node window gives the gradient (and the same phi)
                 Stencil q;
                 q.inside = true;
@@ -269,7 +273,7 @@ __device__ __forceinline__ void pad_taxels_by_warp(const SdfTable& tab, const Pa
                 stencil_fold(q, v, S.inv_h, phi, g);
             }
             float dep, fn[3], ft[3];
-            contact_force(r, phi, g, vel[u][0], vel[u][1], vel[u][2], kn, kd, kt, mu, dep, fn, ft);
+            contact_force(r, phi, g, vel[0], vel[1], vel[2], kn, kd, kt, mu, dep, fn, ft);
             depth[t] = dep;
 #pragma unroll
             for (int a = 0; a < 3; ++a) { f_n[t * 3 + a] = fn[a]; f_t[t * 3 + a] = ft[a]; }
