@@ -135,15 +135,18 @@ def touched_sdf_bytes_batch(sc):
     return _touched_sectors(sc.grids, pts_by_obj)
 
 
-def profiled_traffic(name):
+def profiled_traffic(name, algorithmic_bytes):
     """DRAM bytes per launch from profiles/<name>_traffic.txt, if taken on the current
-    sources of the files it lists (else None: the counters are stale)."""
+    sources of the files it lists and on a launch of the same algorithmic bytes (else None:
+    the counters are stale, or belong to another workload size)."""
     tfile = os.path.join(ROOT, "profiles", f"{name}_traffic.txt")
     if not os.path.exists(tfile):
         return None
     kv = dict(ln.strip().split("=", 1) for ln in open(tfile) if "=" in ln and not ln.startswith("#"))
     files = kv.get("source_files", "").split(",")
     if not files[0] or kv.get("source_hash") != _source_hash(files):
+        return None
+    if int(kv.get("algorithmic_bytes_per_launch", -1)) != int(algorithmic_bytes):
         return None
     return int(kv["dram_bytes_per_launch"])
 
@@ -587,7 +590,7 @@ def run_ours(args, rank, world, local_rank, dist):
     # dominant kernel: the image kernel; its compulsory bytes over its own event-timed launches
     img_bytes = parts["depth_map_read"] + parts["rgb_write"] + parts["shading_coeffs"]
     achieved = img_bytes / (breakdown["shade_image_ms"] * 1e-3) / 1e9
-    traffic = profiled_traffic("shade_kernel")   # ncu DRAM bytes per launch, if taken on these sources
+    traffic = profiled_traffic("shade_kernel", img_bytes)   # ncu DRAM bytes per launch, if taken on these sources
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -784,7 +787,7 @@ def run_batch(args, rank, world, local_rank, dist):
         "roofline": {"bound": "hbm", "kernel": "tacsl::batch_shade_kernel", "algorithmic_bytes": img_bytes,
                      "achieved": img_bytes / (shade_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": img_bytes / (shade_ms * 1e-3) / 1e9 / peak,
-                     "traffic": profiled_traffic("batch_shade_kernel")},
+                     "traffic": profiled_traffic("batch_shade_kernel", img_bytes)},
         "roofline_force": {"bound": "hbm", "kernel": "tacsl::batch_force_kernel", "algorithmic_bytes": force_bytes,
                            "sdf_sectors_touched": sdf_bytes, "achieved": force_bytes / (forces_ms * 1e-3) / 1e9,
                            "frac": force_bytes / (forces_ms * 1e-3) / 1e9 / peak},
