@@ -814,7 +814,7 @@ def run_grad(args, rank, world, local_rank, dist):
 
     import paper_2408_06506_b300 as tacsl
     from paper_2408_06506_b300 import autograd as ta
-    from paper_2408_06506_b300.dist import max_over_ranks
+    from paper_2408_06506_b300.dist import max_over_ranks, sum_shared_grads
 
     sc = make_scene(args.grad_envs, args.seed + 200 + rank)
 
@@ -843,7 +843,12 @@ def run_grad(args, rank, world, local_rank, dist):
 
     n_img = E * P * HW * 3
 
-    def step():
+    def exchange():
+        # data-parallel calibration: every rank's shard shares the shading coefficients, so
+        # their gradient is summed over the ranks (one all-reduce; nothing with one rank)
+        sum_shared_grads([coeffs.grad], dist)
+
+    def step(with_exchange=True):
         # the image term through the fused squared-error kernel (no intensity tensor)
         for t in leaves:
             t.grad = None
@@ -851,6 +856,8 @@ def run_grad(args, rank, world, local_rank, dist):
         L_img = ta.shade_mse(coeffs, depth_map, sid, sc.pitch_x, sc.pitch_y, tI)
         loss = ((fn - tgt[1]) ** 2).mean() + ((ft - tgt[2]) ** 2).mean() + 1e-4 * L_img / n_img
         loss.backward()
+        if with_exchange:
+            exchange()
 
     def step_unfused():
         # the same loss with the intensities materialised and the error taken in PyTorch
@@ -860,6 +867,7 @@ def run_grad(args, rank, world, local_rank, dist):
         I = ta.shade_intensity(coeffs, depth_map, sid, sc.pitch_x, sc.pitch_y)
         loss = ((fn - tgt[1]) ** 2).mean() + ((ft - tgt[2]) ** 2).mean() + 1e-4 * ((I - tI) ** 2).mean()
         loss.backward()
+        exchange()
 
     def timed(fn, n, warm=3):
         for _ in range(warm):
@@ -898,8 +906,9 @@ def run_grad(args, rank, world, local_rank, dist):
             fn()
         return graph
 
-    g_step = captured(step)
-    ms_graph = max_over_ranks(timed(g_step.replay, K), dist, device="cuda")
+    # the graph holds the rank's own forward and backward; the exchange follows each replay
+    g_step = captured(lambda: step(with_exchange=False))
+    ms_graph = max_over_ranks(timed(lambda: (g_step.replay(), exchange()), K), dist, device="cuda")
     assert tacsl.check_errors() == 0
     # the pose -> image chain: the images rendered from the poses (column camera) instead
     # of given depth maps, against the images of poses perturbed by 0.2 mm / 0.01 rad
@@ -913,7 +922,7 @@ def run_grad(args, rank, world, local_rank, dist):
         tI_pose = ta.shade_intensity(tco, tacsl.render_depth(sdfs, cam, obj, dev(tpose.astype(np.float32))),
                                      sid, sc.pitch_x, sc.pitch_y)
 
-    def pose_step():
+    def pose_step(with_exchange=True):
         for t in leaves:
             t.grad = None
         _, fn, ft, _ = ta.force_field(sdfs, taxels, obj, pose, twist, *ks)
@@ -921,6 +930,8 @@ def run_grad(args, rank, world, local_rank, dist):
         L_img = ta.shade_mse(coeffs, D.reshape(-1, sc.H, sc.W), sid, sc.pitch_x, sc.pitch_y, tI_pose)
         loss = ((fn - tgt[1]) ** 2).mean() + ((ft - tgt[2]) ** 2).mean() + 1e-4 * L_img / n_img
         loss.backward()
+        if with_exchange:
+            exchange()
 
     def pose_step_unfused():
         for t in leaves:
@@ -930,6 +941,7 @@ def run_grad(args, rank, world, local_rank, dist):
         I = ta.shade_intensity(coeffs, D.reshape(-1, sc.H, sc.W), sid, sc.pitch_x, sc.pitch_y)
         loss = ((fn - tgt[1]) ** 2).mean() + ((ft - tgt[2]) ** 2).mean() + 1e-4 * ((I - tI_pose) ** 2).mean()
         loss.backward()
+        exchange()
 
     for _ in range(3):
         pose_step()
@@ -939,8 +951,8 @@ def run_grad(args, rank, world, local_rank, dist):
         dist.barrier()
     ms_pose = max_over_ranks(timed(pose_step, K, warm=0), dist, device="cuda")
     ms_pose_unfused = max_over_ranks(timed(pose_step_unfused, K), dist, device="cuda")
-    g_pose = captured(pose_step)
-    ms_pose_graph = max_over_ranks(timed(g_pose.replay, K), dist, device="cuda")
+    g_pose = captured(lambda: pose_step(with_exchange=False))
+    ms_pose_graph = max_over_ranks(timed(lambda: (g_pose.replay(), exchange()), K), dist, device="cuda")
     assert tacsl.check_errors() == 0 and torch.isfinite(pose.grad).all()
     del g_step, g_pose
     # the kernels alone: forward force field and intensity, and their adjoints for fixed
@@ -1037,6 +1049,8 @@ def run_grad(args, rank, world, local_rank, dist):
                                       "frac": radj_bytes / (k_ms["render_adjoint_kernel"] * 1e-3) / 1e9 / peak},
             "peak_gbs": peak},
         "gpu_launches_per_step": 3,
+        "exchange": ("all-reduce (sum) of the shading-coefficient gradient, %d bytes, once per step"
+                     % int(coeffs.numel() * 4) if world > 1 else "none (one rank)"),
         "cpu_baseline": (oracle_grad_rate(sc, args.oracle_seconds, args.seed + 500)
                          if rank == 0 and not args.no_cpu_baseline else None),
     }

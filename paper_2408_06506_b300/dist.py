@@ -2,9 +2,13 @@
 
 Environments are independent (no exchange step), so N ranks split the envs into
 contiguous shards and run the step on their own shard with no collective on the data
-path.  The only cross-rank operations are the barriers around a timed region and the
-max-over-ranks reduction of its duration.  These helpers work with any
-torch.distributed backend (nccl on GPUs, gloo on CPU for tests).
+path.  The only cross-rank operations of the step are the barriers around a timed region
+and the max-over-ranks reduction of its duration.  The calibration workload (gradient
+descent on the contact and shading parameters) has one real exchange: the gradient of a
+parameter that every shard shares (the per-pixel shading coefficients, or contact
+parameters given once for all envs) is the sum of the shards' gradients, one all-reduce
+per step.  These helpers work with any torch.distributed backend (nccl on GPUs, gloo on
+CPU for tests).
 """
 from __future__ import annotations
 
@@ -26,3 +30,25 @@ def max_over_ranks(value: float, dist=None, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def sum_shared_grads(tensors, dist=None) -> None:
+    """Sum, in place and over all ranks, the gradients of parameters every rank's shard
+    shares (identity without a process group or with one rank).  The tensors are
+    flattened into one buffer per dtype and device so that a step makes one collective
+    per buffer; None entries are skipped."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return
+    import torch
+    groups = {}
+    for t in tensors:
+        if t is not None:
+            groups.setdefault((t.dtype, t.device), []).append(t)
+    for ts in groups.values():
+        flat = torch.cat([t.reshape(-1) for t in ts])
+        dist.all_reduce(flat, op=dist.ReduceOp.SUM)
+        o = 0
+        for t in ts:
+            n = t.numel()
+            t.copy_(flat[o:o + n].view_as(t))
+            o += n

@@ -71,3 +71,50 @@ def test_two_gloo_ranks_shard_without_exchange(tmp_path, orc):
         np.testing.assert_array_equal(np.concatenate([p[k] for p in parts]), full[k])
     np.testing.assert_array_equal(np.concatenate([p["rgb"] for p in parts]), rgb_full)
     assert all(float(p["tmax"]) == 1.5 for p in parts)
+
+
+def _grad_worker(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+
+    from oracle import grad as G
+    from paper_2408_06506_b300 import synth
+    from paper_2408_06506_b300.dist import env_shard, sum_shared_grads
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sc = synth.scene_objects(seed=21, E=5, P=2, n=32, depth_maps="exact", H=8, W=12)
+    target = np.random.default_rng(22).uniform(0, 255, size=(sc.E * sc.P, sc.H, sc.W, 3))
+    lo, hi = env_shard(sc.E, rank, world)
+    r = G.shade_mse(sc.coeffs, sc.pitch_x, sc.pitch_y, sc.sensor_id[2 * lo:2 * hi],
+                    sc.depth_map[lo:hi].reshape(-1, sc.H, sc.W), target[2 * lo:2 * hi])
+    own = r["coeffs"].copy()
+    gc = torch.from_numpy(r["coeffs"].copy())
+    gl = torch.from_numpy(r["loss_map"].copy())
+    sum_shared_grads([gc, None, gl], dist)
+    np.savez(os.path.join(out_dir, f"grad{rank}.npz"), own=own, summed=gc.numpy(), loss=gl.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_sum_the_shared_coefficient_gradient(tmp_path):
+    """The calibration's one exchange: each rank differentiates the image loss of its own
+    shard (the oracle's float64 gradient standing in for the GPU adjoint); summing the
+    shading-coefficient gradients over the ranks gives the gradient of the whole batch."""
+    from oracle import grad as G
+    from paper_2408_06506_b300 import synth
+    world = 2
+    mp.start_processes(_grad_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       start_method="spawn", join=True)
+    sc = synth.scene_objects(seed=21, E=5, P=2, n=32, depth_maps="exact", H=8, W=12)
+    target = np.random.default_rng(22).uniform(0, 255, size=(sc.E * sc.P, sc.H, sc.W, 3))
+    full = G.shade_mse(sc.coeffs, sc.pitch_x, sc.pitch_y, sc.sensor_id, sc.depth_map.reshape(-1, sc.H, sc.W),
+                       target)
+    parts = [np.load(tmp_path / f"grad{r}.npz") for r in range(world)]
+    scale = np.abs(full["coeffs"]).max()
+    for p in parts:
+        # each shard alone is not the whole gradient; the sum is, to float64 rounding
+        assert np.abs(p["own"] - full["coeffs"]).max() > 1e-3 * scale
+        np.testing.assert_allclose(p["summed"], full["coeffs"], rtol=0, atol=1e-12 * scale)
+        np.testing.assert_allclose(p["loss"], full["loss_map"], rtol=1e-12, atol=0)
+    np.testing.assert_array_equal(parts[0]["summed"], parts[1]["summed"])
