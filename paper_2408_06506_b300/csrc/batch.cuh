@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kShThreads, 1) batch_shade_kernel(const BatchS
             cur_item = m.y;
             const BatchItem it = batch_item(A, m.y);
             const BatchModel& md = A.mdl[it.m];
-            tile_geometry(md.H, md.W, md.HW, it.tile, md.cx_c, md.cx_e, md.cy_c, md.cy_e, A.stage_floats, tid, warp, g);
+            tile_geometry(md.H, md.W, md.HW, it.tile, md.cx_c, md.cx_e, md.cy_c, md.cy_e, A.stage_floats, tid, g);
             if (!mbar_wait_bounded(smem_u32(cfull), cph)) {
                 if (lane == 0) raise_dev_error(TACSL_DEVERR_TIMEOUT);
                 break;

@@ -36,7 +36,6 @@ constexpr int kShConsumerWarps = 15;                       // compute warps (+1 
 constexpr int kShConsumers = kShConsumerWarps * 32;        // 480 compute threads
 constexpr int kShThreads = kShConsumers + 32;              // + one producer warp
 constexpr int kShTile = kShConsumers * 4;                  // pixels per tile, 4 per thread
-constexpr int kShWarpPx = 128;                             // pixels per compute warp
 constexpr int kShMaxStages = 16;
 constexpr int kShCoefFloats = 18 * kShTile;                // one tile's shading coefficients
 
@@ -270,39 +269,35 @@ __device__ __forceinline__ void shade_producer(const ShadeArgs& A, unsigned char
 // buffer (the tile plus one halo row above and below), and the derivative scales at
 // those pixels: central differences inside, one-sided ones on the image border.
 struct TileGeom {
-    int tile_start, warp_px;
+    int tile_start;
     int oc, ou, od, oL, oR;
     f2 cxp0, cxp1, cyy;
-    bool px_valid, hasL, hasR;
+    bool px_valid;
 };
 
 __device__ __forceinline__ void tile_geometry(int H, int W, int HW, int tile, float cx_c, float cx_e, float cy_c,
-                                              float cy_e, int stage_floats, int tid, int warp, TileGeom& g) {
+                                              float cy_e, int stage_floats, int tid, TileGeom& g) {
     g.tile_start = tile * kShTile;
     const int tile_px = min(kShTile, HW - g.tile_start);
     const int lo_px = max(g.tile_start - W, 0);
-    g.warp_px = min(max(tile_px - warp * kShWarpPx, 0), kShWarpPx);
     g.px_valid = 4 * tid < tile_px;
     const int p = g.tile_start + 4 * tid;
     if (g.px_valid) {
         const int y = p / W, x0 = p - y * W;
-        g.hasL = x0 > 0;
-        g.hasR = x0 + 4 < W;
+        const bool hasL = x0 > 0, hasR = x0 + 4 < W;
         g.oc = p - lo_px;
         g.ou = ((y > 0) ? p - W : p) - lo_px;
         g.od = ((y < H - 1) ? p + W : p) - lo_px;
-        g.oL = (g.hasL ? p - 1 : p) - lo_px;
-        g.oR = (g.hasR ? p + 4 : p + 3) - lo_px;
+        g.oL = (hasL ? p - 1 : p) - lo_px;
+        g.oR = (hasR ? p + 4 : p + 3) - lo_px;
         const float cyv = (y > 0 && y < H - 1) ? cy_c : cy_e;
-        g.cxp0 = pk(g.hasL ? cx_c : cx_e, cx_c);
-        g.cxp1 = pk(cx_c, g.hasR ? cx_c : cx_e);
+        g.cxp0 = pk(hasL ? cx_c : cx_e, cx_c);
+        g.cxp1 = pk(cx_c, hasR ? cx_c : cx_e);
         g.cyy = pk(cyv, cyv);
     } else {
-        // past the tile's end: read in-bounds stage words (the lane's natural position,
-        // which its left neighbour uses as the pixel after the tile) and store nothing
+        // past the tile's end: read in-bounds stage words and store nothing
         g.oc = min(p - lo_px, stage_floats - 4);
         g.ou = g.od = g.oL = g.oR = g.oc;
-        g.hasL = g.hasR = true;
         g.cxp0 = g.cxp1 = g.cyy = 0;
     }
 }
@@ -466,7 +461,7 @@ __global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A)
             // new item: geometry, then the tile's coefficients from shared memory
             cur_item = m.y;
             const Item it = decode_item(A, m.y);
-            tile_geometry(A.H, A.W, A.HW, it.tile, A.cx_c, A.cx_e, A.cy_c, A.cy_e, A.stage_floats, tid, warp, g);
+            tile_geometry(A.H, A.W, A.HW, it.tile, A.cx_c, A.cx_e, A.cy_c, A.cy_e, A.stage_floats, tid, g);
             if (!mbar_wait_bounded(smem_u32(cfull), cph)) {
                 if (lane == 0) raise_dev_error(TACSL_DEVERR_TIMEOUT);
                 break;
