@@ -57,6 +57,7 @@ struct DevInfo {
     int max_smem_optin = 0;
     bool shade_attr_set = false;
     bool batch_shade_attr_set = false;
+    bool cg_attr_set = false;                   // shade_coeff_grad_kernel: dynamic shared memory
     int batch_force_ctas[4] = {0, 0, 0, 0};   // resident CTAs per SM: [np == 4][dynamic]
     int render_adj_ctas = 0;                    // resident render-adjoint CTAs per SM
     // streams and events of tacsl_tactile_step_host, created on its first call here
@@ -1164,6 +1165,40 @@ int shade_geom(const tacsl_shading* sh, ShadeGeom& G) {
     return TACSL_OK;
 }
 
+// Coefficient gradient (and, for the image loss, the loss map): the two-pixels-per-lane
+// kernel, with 8-byte copies of the upstream values where that array allows them.
+template <bool kMse>
+int launch_coeff_grad(const ShadeGeom& G, int64_t B, const float* coeffs, const int32_t* sensor_id,
+                      const float* depth, const float* u, const float* scale, float* grad_coeffs, float* loss_map,
+                      DevInfo& dev, tacsl_stream_t stream) {
+    const int64_t tiles = (G.HW + kCgPx - 1) / kCgPx;
+    if (tiles > INT32_MAX || G.HW > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "image too large");
+    if (!dev.cg_attr_set) {
+        const int bytes = static_cast<int>(kCgSmemBytes);
+        cudaError_t e = cudaFuncSetAttribute(shade_coeff_grad_kernel<false, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(shade_coeff_grad_kernel<false, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(shade_coeff_grad_kernel<true, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(shade_coeff_grad_kernel<true, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        dev.cg_attr_set = true;
+    }
+    const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(G.S));
+    if (aligned(u, 8))
+        shade_coeff_grad_kernel<kMse, true><<<grid, 256, kCgSmemBytes, stream>>>(
+            G, B, coeffs, sensor_id, depth, u, scale, grad_coeffs, loss_map);
+    else
+        shade_coeff_grad_kernel<kMse, false><<<grid, 256, kCgSmemBytes, stream>>>(
+            G, B, coeffs, sensor_id, depth, u, scale, grad_coeffs, loss_map);
+    return check_launch(kMse ? "tacsl_shade_mse (loss map / coefficients)" : "tacsl_shade_adjoint (coefficients)");
+}
+
 // Grid of the depth-gradient kernel: (32 x 8 tiles, sensors, image chunks), with enough
 // image chunks that the launch gives every SM a few CTAs even for small images.
 int launch_depth_grad(bool mse, const ShadeGeom& G, int64_t B, const float* coeffs, const int32_t* sensor_id,
@@ -1283,12 +1318,9 @@ int tacsl_shade_adjoint(const tacsl_shading* shading, int64_t B, const int32_t* 
     ShadeGeom G;
     shade_geom(shading, G);
     if (grad_coeffs != nullptr) {
-        const int64_t tiles = (G.HW + kPxTile - 1) / kPxTile;
-        if (tiles > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "image too large");
-        shade_coeff_grad_kernel<false><<<dim3(static_cast<unsigned>(tiles), static_cast<unsigned>(G.S)), 256, 0,
-                                         stream>>>(G, B, shading->coeffs, sensor_id, depth_map, g_intensity, nullptr,
-                                                   grad_coeffs, nullptr);
-        if ((rc = check_launch("tacsl_shade_adjoint (coefficients)"))) return rc;
+        if ((rc = launch_coeff_grad<false>(G, B, shading->coeffs, sensor_id, depth_map, g_intensity, nullptr,
+                                           grad_coeffs, nullptr, *dev, stream)))
+            return rc;
     }
     if (grad_depth != nullptr && B > 0) {
         if ((rc = launch_depth_grad(false, G, B, shading->coeffs, sensor_id, depth_map, g_intensity, nullptr,
@@ -1315,12 +1347,9 @@ int tacsl_shade_mse(const tacsl_shading* shading, int64_t B, const int32_t* sens
     ShadeGeom G;
     shade_geom(shading, G);
     if (per_sensor) {
-        const int64_t tiles = (G.HW + kPxTile - 1) / kPxTile;
-        if (tiles > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "image too large");
-        shade_coeff_grad_kernel<true><<<dim3(static_cast<unsigned>(tiles), static_cast<unsigned>(G.S)), 256, 0,
-                                        stream>>>(G, B, shading->coeffs, sensor_id, depth_map, target, scale,
-                                                  grad_coeffs, loss_map);
-        if ((rc = check_launch("tacsl_shade_mse (loss map / coefficients)"))) return rc;
+        if ((rc = launch_coeff_grad<true>(G, B, shading->coeffs, sensor_id, depth_map, target, scale, grad_coeffs,
+                                          loss_map, *dev, stream)))
+            return rc;
     }
     if (grad_depth != nullptr && B > 0) {
         if ((rc = launch_depth_grad(true, G, B, shading->coeffs, sensor_id, depth_map, target, scale, grad_depth,
