@@ -54,7 +54,7 @@ typedef struct CUstream_st* tacsl_stream_t;
 /* Status codes. */
 #define TACSL_OK 0
 #define TACSL_ERR_INVALID_ARG 1 /* a host-checkable argument is wrong; nothing launched */
-#define TACSL_ERR_UNSUPPORTED 2 /* valid but beyond this build's limits; nothing launched */
+#define TACSL_ERR_UNSUPPORTED 2 /* valid but beyond the library's limits; nothing launched */
 #define TACSL_ERR_CUDA 3        /* the CUDA runtime reported an error (launch or query) */
 #define TACSL_ERR_TIMEOUT 4     /* a bounded device wait gave up (see the error word) */
 
