@@ -409,10 +409,10 @@ __device__ __forceinline__ PixelState pixel_state(const float* D, const ShadeGeo
     return s;
 }
 
-// Work split of the per-pixel image kernels: a CTA of 8 warps owns 32 consecutive pixels
-// of one sensor's image plane (one per lane, so the per-pixel coefficients stay in
-// registers) and a range of images; its warps take equal slices of that range.
-constexpr int kPxTile = 32;
+// Work split of the per-pixel image kernels (intensity and coefficient gradient): a CTA of
+// 8 warps owns 64 consecutive pixels of one sensor's image plane (two per lane, so the
+// per-pixel coefficients stay in registers) and a range of images; its warps take equal
+// slices of that range.
 constexpr int kImgWarps = 8;
 
 // Per-lane asynchronous 4-byte copy global -> shared (completion per thread, by group).
@@ -426,100 +426,6 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 constexpr int kCgStages = 6;     // images in flight per warp
 constexpr int kCgSeg = 128;      // images of a warp's slice listed at a time
-
-// The images of sensor s in [w0, w1), in order, each with this lane's NV input values
-// fetched kCgStages images ahead: the warp lists its images kCgSeg at a time (ballot),
-// issue(b, dst) starts the lane's copies of image b into dst[v * kPxTile] (cp.async; it
-// may issue none), and f(b, src) consumes them once they have landed.  ring: this warp's
-// [kCgStages][NV][kPxTile] floats; list: its kCgSeg ints.  Warp-uniform control flow.
-template <int NV, class Issue, class F>
-__device__ __forceinline__ void for_images_pipelined(const int32_t* __restrict__ sensor_id, int64_t w0, int64_t w1,
-                                                     int s, float* ring, int* list, Issue&& issue, F&& f) {
-    const int lane = threadIdx.x & 31;
-    const unsigned below = (1u << lane) - 1u;
-    for (int64_t seg = w0; seg < w1; seg += kCgSeg) {
-        const int64_t seg_end = min(seg + kCgSeg, w1);
-        int n = 0;
-        for (int64_t base = seg; base < seg_end; base += 32) {
-            const int sid = base + lane < seg_end ? __ldg(sensor_id + base + lane) : -1;
-            const unsigned mask = __ballot_sync(0xffffffffu, sid == s);
-            if (sid == s) list[n + __popc(mask & below)] = static_cast<int>(base + lane);
-            n += __popc(mask);
-        }
-        __syncwarp();
-        auto start = [&](int i) {
-            if (i < n) issue(static_cast<int64_t>(list[i]), ring + (i % kCgStages) * NV * kPxTile + lane);
-            cp_async_commit();      // one group per image slot, empty or not
-        };
-#pragma unroll
-        for (int i = 0; i < kCgStages - 1; ++i) start(i);
-        for (int i = 0; i < n; ++i) {
-            start(i + kCgStages - 1);
-            cp_async_wait<kCgStages - 1>();      // this lane's copies of image i have landed
-            f(static_cast<int64_t>(list[i]), ring + (i % kCgStages) * NV * kPxTile + lane);
-        }
-        cp_async_wait<0>();
-        __syncwarp();               // the list and the ring are reused by the next segment
-    }
-}
-
-
-// Clamped intensity: grid (pixel tiles, sensors, image chunks).  Each lane's 4 depth
-// samples per image are fetched kCgStages images ahead (for_images_pipelined).
-__global__ void __launch_bounds__(256) shade_intensity_kernel(ShadeGeom G, int64_t B, int64_t chunk,
-                                                               const float* __restrict__ coeffs,
-                                                               const int32_t* __restrict__ sensor_id,
-                                                               const float* __restrict__ depth,
-                                                               float* __restrict__ inten) {
-    __shared__ float ring[kImgWarps][kCgStages][4][kPxTile];
-    __shared__ int list[kImgWarps][kCgSeg];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int s = blockIdx.y;
-    const int64_t px = static_cast<int64_t>(blockIdx.x) * kPxTile + lane;
-    const bool valid = px < G.HW;
-    const int y = valid ? static_cast<int>(px / G.W) : 0, x = valid ? static_cast<int>(px - static_cast<int64_t>(y) * G.W) : 0;
-    int xlo, xhi, ylo, yhi;
-    float cx, cy;
-    axis_stencil(x, G.W, G.px, xlo, xhi, cx);
-    axis_stencil(y, G.H, G.py, ylo, yhi, cy);
-    const int64_t o_xh = static_cast<int64_t>(y) * G.W + xhi, o_xl = static_cast<int64_t>(y) * G.W + xlo;
-    const int64_t o_yh = static_cast<int64_t>(yhi) * G.W + x, o_yl = static_cast<int64_t>(ylo) * G.W + x;
-    float a[6][3];
-#pragma unroll
-    for (int kk = 0; kk < 6; ++kk)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            a[kk][c] = valid ? __ldg(coeffs + (static_cast<int64_t>(s) * 18 + kk * 3 + c) * G.HW + px) : 0.f;
-    const int64_t c0 = static_cast<int64_t>(blockIdx.z) * chunk, c1 = min(c0 + chunk, B);
-    const int64_t per = (c1 - c0 + kImgWarps - 1) / kImgWarps;
-    const int64_t w0 = min(c0 + warp * per, c1), w1 = min(w0 + per, c1);
-    for_images_pipelined<4>(
-        sensor_id, w0, w1, s, &ring[warp][0][0][0], list[warp],
-        [&](int64_t b, float* st) {
-            if (!valid) return;
-            const float* D = depth + b * G.HW;
-            cp_async4(st + 0 * kPxTile, D + o_xh);
-            cp_async4(st + 1 * kPxTile, D + o_xl);
-            cp_async4(st + 2 * kPxTile, D + o_yh);
-            cp_async4(st + 3 * kPxTile, D + o_yl);
-        },
-        [&](int64_t b, const float* st) {
-            if (!valid) return;
-            const float dx = (st[0 * kPxTile] - st[1 * kPxTile]) * cx;
-            const float dy = (st[2 * kPxTile] - st[3 * kPxTile]) * cy;
-            const float r = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, 1.f)));
-            const float nx = dx * r, ny = dy * r;
-            const float m[6] = {1.f, nx, ny, nx * nx, ny * ny, nx * ny};
-            float* out = inten + (b * G.HW + px) * 3;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float I = 0.f;
-#pragma unroll
-                for (int kk = 0; kk < 6; ++kk) I = fmaf(a[kk][c], m[kk], I);
-                out[c] = fminf(fmaxf(I, 0.f), 255.f);
-            }
-        });
-}
 
 // Bad sensor ids of the intensity forward: flagged once per image.
 __global__ void __launch_bounds__(256) flag_bad_sensors_kernel(int64_t B, int S, const int32_t* __restrict__ sensor_id) {
@@ -710,6 +616,117 @@ __global__ void __launch_bounds__(256, 2) shade_coeff_grad_kernel(ShadeGeom G, i
         } else if (loss_map != nullptr) {
             loss_map[static_cast<int64_t>(s) * G.HW + p] = sum;
         }
+    }
+}
+
+// Clamped intensity with two horizontally adjacent pixels per lane: grid (64-pixel tiles,
+// sensors, image chunks), a CTA of 8 warps taking equal slices of its chunk.  Per lane and
+// image the centre depth pair and the pairs above and below arrive as 8-byte cp.async
+// copies kCgStages images ahead (lanes 0 and 31 also fetch the pixel beyond the warp's
+// row segment; the other lanes' horizontal neighbours come by shuffle); the arithmetic
+// runs on FP32 pairs in the operations and order of the single-pixel definition, and the
+// six output floats leave as three 8-byte stores when the output is 8-byte aligned (kO8),
+// else as six 4-byte ones.
+constexpr int kInSlots = 4;       // 8-byte slots per lane and image
+constexpr size_t kInSmemBytes =
+    size_t(kImgWarps) * kCgStages * kInSlots * 32 * sizeof(float2) + size_t(kImgWarps) * kCgSeg * sizeof(int);
+
+template <bool kO8>
+__global__ void __launch_bounds__(256) shade_intensity_kernel(ShadeGeom G, int64_t B, int64_t chunk,
+                                                               const float* __restrict__ coeffs,
+                                                               const int32_t* __restrict__ sensor_id,
+                                                               const float* __restrict__ depth,
+                                                               float* __restrict__ inten) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2* ring = reinterpret_cast<float2*>(dsm) + warp * (kCgStages * kInSlots * 32);
+    int* list = reinterpret_cast<int*>(dsm + size_t(kImgWarps) * kCgStages * kInSlots * 32 * sizeof(float2)) +
+                warp * kCgSeg;
+    const int s = blockIdx.y;
+    const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kCgPx + 2 * lane;   // HW is even: p0 + 1 < HW too
+    const bool valid = p0 < G.HW;
+    const int y = valid ? static_cast<int>(p0 / G.W) : 0, x = valid ? static_cast<int>(p0 - static_cast<int64_t>(y) * G.W) : 0;
+    const bool hasL = x > 0, hasR = x + 2 < G.W;
+    const float c_in = 1.f / (2.f * G.px), c_edge = 1.f / G.px;
+    const float cx0 = hasL ? c_in : c_edge, cx1 = hasR ? c_in : c_edge;
+    int ylo, yhi;
+    float cy;
+    axis_stencil(y, G.H, G.py, ylo, yhi, cy);
+    const int o_c = y * G.W + x, o_u = ylo * G.W + x, o_d = yhi * G.W + x;
+    const int o_e = lane == 0 ? (hasL ? o_c - 1 : -1) : lane == 31 ? (hasR ? o_c + 2 : -1) : -1;
+    const f2 one2 = pk(1.f, 1.f), cyy = pk(cy, cy);
+    f2 a[6][3];
+#pragma unroll
+    for (int kk = 0; kk < 6; ++kk)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float2 v = make_float2(0.f, 0.f);
+            if (valid) v = __ldg(reinterpret_cast<const float2*>(coeffs + (static_cast<int64_t>(s) * 18 + kk * 3 + c) * G.HW + p0));
+            a[kk][c] = pk(v.x, v.y);
+        }
+    const int64_t c0 = static_cast<int64_t>(blockIdx.z) * chunk, c1 = min(c0 + chunk, B);
+    const int64_t per = (c1 - c0 + kImgWarps - 1) / kImgWarps;
+    const int64_t w0 = min(c0 + warp * per, c1), w1 = min(w0 + per, c1);
+    const unsigned below = (1u << lane) - 1u;
+    for (int64_t seg = w0; seg < w1; seg += kCgSeg) {
+        const int64_t seg_end = min(seg + kCgSeg, w1);
+        int n = 0;
+        for (int64_t base = seg; base < seg_end; base += 32) {
+            const int sid = base + lane < seg_end ? __ldg(sensor_id + base + lane) : -1;
+            const unsigned mask = __ballot_sync(0xffffffffu, sid == s);
+            if (sid == s) list[n + __popc(mask & below)] = static_cast<int>(base + lane);
+            n += __popc(mask);
+        }
+        __syncwarp();
+        auto start = [&](int i) {
+            if (i < n && valid) {
+                float2* sl = ring + (i % kCgStages) * (kInSlots * 32) + lane;
+                const float* D = depth + static_cast<int64_t>(list[i]) * G.HW;
+                cp_async8(sl, D + o_c);
+                cp_async8(sl + 32, D + o_u);
+                cp_async8(sl + 64, D + o_d);
+                if (o_e >= 0) cp_async4(&sl[96].x, D + o_e);
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int i = 0; i < kCgStages - 1; ++i) start(i);
+        for (int i = 0; i < n; ++i) {
+            start(i + kCgStages - 1);
+            cp_async_wait<kCgStages - 1>();
+            const float2* sl = ring + (i % kCgStages) * (kInSlots * 32) + lane;
+            const float2 ce = sl[0], up = sl[32], dn = sl[64];
+            float L = __shfl_up_sync(0xffffffffu, ce.y, 1);
+            float R = __shfl_down_sync(0xffffffffu, ce.x, 1);
+            if (lane == 0) L = sl[96].x;
+            if (lane == 31) R = sl[96].x;
+            if (!valid) continue;
+            const f2 dxp = pk((ce.y - (hasL ? L : ce.x)) * cx0, ((hasR ? R : ce.y) - ce.x) * cx1);
+            const f2 dyp = mul2(sub2(pk(dn.x, dn.y), pk(up.x, up.y)), cyy);
+            const f2 s2 = fma2(dxp, dxp, fma2(dyp, dyp, one2));
+            const f2 r = pk(rsqrtf(lo(s2)), rsqrtf(hi(s2)));
+            const f2 nx = mul2(dxp, r), ny = mul2(dyp, r);
+            const f2 m[6] = {one2, nx, ny, mul2(nx, nx), mul2(ny, ny), mul2(nx, ny)};
+            float o[6];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                f2 I = pk(0.f, 0.f);
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk) I = fma2(a[kk][c], m[kk], I);
+                o[c] = fminf(fmaxf(lo(I), 0.f), 255.f);
+                o[3 + c] = fminf(fmaxf(hi(I), 0.f), 255.f);
+            }
+            float* out = inten + (static_cast<int64_t>(list[i]) * G.HW + p0) * 3;
+            if (kO8) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) reinterpret_cast<float2*>(out)[q] = make_float2(o[2 * q], o[2 * q + 1]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) out[q] = o[q];
+            }
+        }
+        cp_async_wait<0>();
+        __syncwarp();
     }
 }
 

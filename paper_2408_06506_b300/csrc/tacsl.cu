@@ -58,6 +58,7 @@ struct DevInfo {
     bool shade_attr_set = false;
     bool batch_shade_attr_set = false;
     bool cg_attr_set = false;                   // shade_coeff_grad_kernel: dynamic shared memory
+    bool in_attr_set = false;                   // shade_intensity_kernel: dynamic shared memory
     int batch_force_ctas[4] = {0, 0, 0, 0};   // resident CTAs per SM: [np == 4][dynamic]
     int render_adj_ctas = 0;                    // resident render-adjoint CTAs per SM
     // streams and events of tacsl_tactile_step_host, created on its first call here
@@ -1292,15 +1293,29 @@ int tacsl_shade_intensity(const tacsl_shading* shading, int64_t B, const int32_t
     if ((rc = device_info(&dev))) return rc;
     ShadeGeom G;
     shade_geom(shading, G);
+    if (G.HW > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "image too large");
+    if (!dev->in_attr_set) {
+        const int bytes = static_cast<int>(kInSmemBytes);
+        cudaError_t e =
+            cudaFuncSetAttribute(shade_intensity_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(shade_intensity_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        dev->in_attr_set = true;
+    }
     // images per CTA: enough chunks to give every SM several CTAs
-    const int64_t tiles = (G.HW + kPxTile - 1) / kPxTile;
+    const int64_t tiles = (G.HW + kCgPx - 1) / kCgPx;
     int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(65535, (int64_t)dev->sms * 8 / std::max<int64_t>(1, tiles * G.S) + 1));
     chunks = std::min<int64_t>(chunks, B);
     const int64_t chunk = (B + chunks - 1) / chunks;
     flag_bad_sensors_kernel<<<grid_for(B, 4, *dev), 256, 0, stream>>>(B, G.S, sensor_id);
-    shade_intensity_kernel<<<dim3(static_cast<unsigned>(tiles), static_cast<unsigned>(G.S),
-                                  static_cast<unsigned>((B + chunk - 1) / chunk)), 256, 0, stream>>>(
-        G, B, chunk, shading->coeffs, sensor_id, depth_map, intensity);
+    const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(G.S), static_cast<unsigned>((B + chunk - 1) / chunk));
+    if (aligned(intensity, 8))
+        shade_intensity_kernel<true><<<grid, 256, kInSmemBytes, stream>>>(G, B, chunk, shading->coeffs, sensor_id,
+                                                                          depth_map, intensity);
+    else
+        shade_intensity_kernel<false><<<grid, 256, kInSmemBytes, stream>>>(G, B, chunk, shading->coeffs, sensor_id,
+                                                                           depth_map, intensity);
     return check_launch("tacsl_shade_intensity");
 }
 
