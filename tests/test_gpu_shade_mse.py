@@ -173,3 +173,47 @@ def test_full_size_sampled_windows():
         assert np.abs(gdb - wd).max() <= 1e-3 * np.abs(wd).max() + 1e-6
         checked += 1
     assert checked >= 3
+
+
+def _at_word_offset(a):
+    """A device copy of float32 array a starting one word past an 8-byte boundary."""
+    flat = torch.empty(a.size + 1, dtype=torch.float32, device="cuda")
+    v = flat[1:].view(a.shape)
+    v.copy_(torch.as_tensor(np.ascontiguousarray(a)))
+    assert v.data_ptr() % 8 == 4
+    return v
+
+
+@pytest.mark.parametrize("S,B,H,W", [(2, 6, 24, 32), (1, 3, 7, 12)])
+def test_word_aligned_arrays_take_the_4_byte_paths(S, B, H, W):
+    """The image kernels copy upstream values and store intensities 8 bytes at a time when
+    the arrays allow it; at a 4-byte-aligned address they fall back to 4-byte accesses with
+    the same results, bit for bit."""
+    co, dm, sid, tgt, px, py = _case(40 + B, S, B, H, W)
+    sh = tacsl.Shading(dev(co), px, py)
+    lib, P = ta._lib(), tacsl._ptr
+    d_sid, d_dm = dev(sid), dev(dm)
+
+    def run(t, g):
+        lm = torch.empty(S, H, W, device="cuda")
+        gc = torch.empty(S, 6, 3, H, W, device="cuda")
+        gd = torch.empty(B, H, W, device="cuda")
+        gc2 = torch.empty_like(gc)
+        gd2 = torch.empty_like(gd)
+        assert lib.tacsl_shade_mse(C.byref(sh.c), B, P(d_sid), P(d_dm), P(t), None, P(lm), P(gc), P(gd), None) == 0
+        assert lib.tacsl_shade_adjoint(C.byref(sh.c), B, P(d_sid), P(d_dm), P(g), P(gc2), P(gd2), None) == 0
+        return [x.cpu().numpy() for x in (lm, gc, gd, gc2, gd2)]
+
+    g = np.random.default_rng(41).normal(size=(B, H, W, 3)).astype(np.float32)
+    aligned = run(dev(tgt), dev(g))
+    shifted = run(_at_word_offset(tgt), _at_word_offset(g))
+    for a, b in zip(aligned, shifted):
+        assert np.array_equal(a, b)
+    inten = torch.empty(B, H, W, 3, device="cuda")
+    inten_w = _at_word_offset(np.zeros((B, H, W, 3), np.float32))
+    for out in (inten, inten_w):
+        assert lib.tacsl_shade_intensity(C.byref(sh.c), B, P(d_sid), P(d_dm), P(out), None) == 0
+    assert torch.equal(inten, inten_w)
+    _, ref, _ = oracle.shade(co, px, py, sid, dm, with_intensity=True)
+    assert np.abs(inten.cpu().numpy() - ref).max() <= 1e-3
+    assert tacsl.check_errors() == 0
