@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--min-timed-s", type=float, default=1.5,
+                    help="the K-step timed region is repeated until about this many seconds have passed")
+    ap.add_argument("--config1-steps", type=int, default=2000)
+    ap.add_argument("--config1-host-calls", type=int, default=500)
+    ap.add_argument("--no-config1", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-templates", type=int, default=16)
     ap.add_argument("--serve-streams", type=int, default=4)
@@ -189,6 +194,9 @@ class ClockSampler:
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.perf_counter()      # the timed region starts once samples flow
+            while not self.lines and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.02)
         except OSError:
             self.proc = None
         return self
@@ -418,21 +426,34 @@ def run_ours(args, rank, world, local_rank, dist):
     torch.cuda.synchronize()
     assert tacsl.check_errors() == 0
 
-    # ---- device-timed region: K fused steps, inputs resident in HBM (4.4 GB > L2) ----
+    # ---- device-timed region: K fused steps, inputs resident in HBM (4.4 GB > L2).  The
+    # K-step region (barrier + synchronise on both sides, max over ranks) is repeated until
+    # about --min-timed-s seconds have passed, so that the clock sampler around all repeats
+    # sees the load; ms_per_step is the median repeat / K ----
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(_smi_id(local_rank)) as clk:
+
+    def timed_region():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
             step()
         ev1.record(stream)
         torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    ms_total = max_over_ranks(ev0.elapsed_time(ev1), dist, device="cuda")
-    ms_step = ms_total / args.steps
+        if dist is not None:
+            dist.barrier()
+        return max_over_ranks(ev0.elapsed_time(ev1), dist, device="cuda")
+
+    with ClockSampler(_smi_id(local_rank)) as clk:
+        t_clock = time.perf_counter()
+        reps = [timed_region()]
+        n_rep = int(max_over_ranks(min(100000, max(3, int(np.ceil(args.min_timed_s * 1e3 / max(reps[0], 1e-3))))),
+                                   dist, device="cuda"))
+        for _ in range(n_rep - 1):
+            reps.append(timed_region())
+        timed_s = time.perf_counter() - t_clock
+    ms_step = float(np.median(reps)) / args.steps
     taxel_pts = world * E * P * T
     images = world * E * P
     value = taxel_pts / (ms_step * 1e-3)
@@ -570,6 +591,7 @@ def run_ours(args, rank, world, local_rank, dist):
                "frac_of_copy_only": ceil_s / (el / args.e2e_steps),
                "path": "pinned host -> tacsl_tactile_step_host (chunks pipelined over 3 streams) -> pinned host"}
 
+    config1 = None if args.no_config1 else run_config1(args, rank, world, local_rank, dist)
     batch = None if args.no_batch else run_batch(args, rank, world, local_rank, dist)
     grad = None if args.no_grad else run_grad(args, rank, world, local_rank, dist)
     serve = None if args.no_serve else run_serve(args, rank, world, local_rank, dist)
@@ -616,16 +638,162 @@ def run_ours(args, rank, world, local_rank, dist):
                           "frac": step_achieved / peak, "algorithmic_bytes": alg, "bytes": parts,
                           "kernels": ["tacsl::shade_kernel", "tacsl::penalty_kernel"]},
         "clocks": clk.summary(),
+        "timed_region": {"repeats": len(reps), "steps_per_repeat": args.steps, "seconds": timed_s,
+                         "ms_per_step": {"median": ms_step, "min": min(reps) / args.steps,
+                                         "max": max(reps) / args.steps}},
         "breakdown": breakdown,
+        "config1": config1,
         "render_step": render,
         "batch": batch,
         "grad": grad,
         "serve": serve,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 2 * args.steps * len(reps),
         "cpu_baseline": cpu,
         "e2e": e2e,
     }
     print(json.dumps(line), flush=True)
+
+
+CONFIG1_WORKLOAD = ("1 env: one 16x20 pad at 1 mm pitch against a sphere of radius 5 mm (64^3 f32 SDF, 0.25 mm "
+                    "voxels), indentation U(0, 1 mm), offset U(+-3 mm), v ~ N(0, 0.02 m/s); one 160x120 f32 depth map "
+                    "-> uint8 RGB")
+
+
+def run_config1(args, rank, world, local_rank, dist):
+    """Latency of one tactile step of a single environment (latency-bound: reported in
+    microseconds, not against a roofline), measured five ways, with the FP64 oracle's
+    single-env time beside it.  Every rank measures its own GPU; rank 0 reports."""
+    import torch
+
+    import paper_2408_06506_b300 as tacsl
+    from paper_2408_06506_b300 import synth
+
+    sc = synth.scene_sphere_pad(seed=1)
+
+    def dev(a):
+        return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+    sdfs = tacsl.SdfSet.from_grids(sc.grids)
+    params = tacsl.ContactParams(dev(sc.k_n), dev(sc.k_d), dev(sc.k_t), dev(sc.mu))
+    shading = tacsl.Shading(dev(sc.coeffs), sc.pitch_x, sc.pitch_y)
+    taxels, obj_id, pose, twist = dev(sc.taxels), dev(sc.obj_id), dev(sc.pad_pose), dev(sc.pad_twist)
+    sensor_id, depth_map = dev(sc.sensor_id), dev(sc.depth_map)
+    E, P, T = sc.E, sc.P, sc.T
+    outs = dict(depth=torch.empty(E, P, T, device="cuda"), f_n=torch.empty(E, P, T, 3, device="cuda"),
+                f_t=torch.empty(E, P, T, 3, device="cuda"), wrench=torch.empty(E, P, 6, device="cuda"),
+                rgb=torch.empty(E * P, sc.H, sc.W, 3, dtype=torch.uint8, device="cuda"))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        tacsl.tactile_step(sdfs, params, taxels, obj_id, pose, twist, shading, sensor_id, depth_map, **outs)
+
+    n = max(1000, args.config1_steps)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def device_us(fn, count):
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(count):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return 1e3 * ev0.elapsed_time(ev1) / count
+
+    for _ in range(50):
+        step()
+    torch.cuda.synchronize()
+    assert tacsl.check_errors() == 0
+    # (1) back-to-back calls through the binding, device-timed
+    back_to_back = device_us(step, n)
+    # (2) one step per CUDA-graph replay; (3) 100 steps per replay (launch cost amortised)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    g1, g100 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g1):
+        step()
+    with torch.cuda.graph(g100):
+        for _ in range(100):
+            step()
+    for _ in range(10):
+        g1.replay()
+    graph1 = device_us(g1.replay, n)
+    g100.replay()
+    graph100 = device_us(g100.replay, max(10, n // 100)) / 100
+    # (4) wall clock of one call that waits for its result (launch + run + synchronise)
+    wall = []
+    for _ in range(args.config1_host_calls):
+        t0 = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        wall.append(time.perf_counter() - t0)
+    # (5) through tacsl_tactile_step_host with pinned host buffers: inputs in, results out,
+    # the call waited for, every call
+    h_in = {"obj_id": torch.as_tensor(sc.obj_id).pin_memory(), "pose": torch.as_tensor(sc.pad_pose).pin_memory(),
+            "twist": torch.as_tensor(sc.pad_twist).pin_memory(),
+            "sensor_id": torch.as_tensor(sc.sensor_id).pin_memory(),
+            "depth_map": torch.as_tensor(np.ascontiguousarray(sc.depth_map).reshape(-1, sc.H, sc.W)).pin_memory()}
+    h_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs.items()}
+    ws = torch.empty(tacsl.load().tacsl_tactile_step_host_workspace(1, P, T, sc.H, sc.W), dtype=torch.uint8,
+                     device="cuda")
+
+    def host_step():
+        tacsl.tactile_step_host(sdfs, params, taxels, h_in["obj_id"], h_in["pose"], h_in["twist"], shading,
+                                h_in["sensor_id"], h_in["depth_map"], out=h_out, chunk_envs=1, workspace=ws)
+
+    for _ in range(20):
+        host_step()
+    torch.cuda.synchronize()
+    step()
+    torch.cuda.synchronize()
+    for k in ("depth", "f_n", "f_t", "wrench", "rgb"):
+        assert torch.equal(h_out[k], outs[k].cpu()), k
+    host = []
+    for _ in range(args.config1_host_calls):
+        t0 = time.perf_counter()
+        host_step()
+        torch.cuda.synchronize()
+        host.append(time.perf_counter() - t0)
+    assert tacsl.check_errors() == 0
+    h2d = sum(t.numel() * t.element_size() for t in h_in.values())
+    d2h = sum(t.numel() * t.element_size() for t in h_out.values())
+    pct = lambda v, q: 1e6 * float(np.percentile(v, q))   # noqa: E731
+    res = {
+        "workload": CONFIG1_WORKLOAD, "taxel_points": E * P * T, "images": E * P, "unit": "us",
+        "device_us_back_to_back": back_to_back,
+        "graph_us_per_replay": graph1,
+        "graph_us_per_step_100_per_replay": graph100,
+        "wall_us_device_step_synchronised": {"p50": pct(wall, 50), "p99": pct(wall, 99), "calls": len(wall)},
+        "host_buffers_us": {"p50": pct(host, 50), "p99": pct(host, 99), "calls": len(host),
+                            "h2d_bytes": h2d, "d2h_bytes": d2h,
+                            "path": "pinned host -> tacsl_tactile_step_host -> pinned host, synchronised per call"},
+        "launches_per_step": 2, "steps_timed": n,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+
+        def one(_k):
+            oracle.penalty_forces(sc.grids, sc.taxels, sc.obj_id, sc.pad_pose, sc.pad_twist, sc.k_n, sc.k_d, sc.k_t,
+                                  sc.mu, nthreads=1)
+            oracle.shade(sc.coeffs, sc.pitch_x, sc.pitch_y, sc.sensor_id, sc.depth_map, nthreads=1)
+
+        one(0)
+        ts = []
+        t_end = time.perf_counter() + min(3.0, args.oracle_seconds)
+        while time.perf_counter() < t_end or len(ts) < 10:
+            t0 = time.perf_counter()
+            one(len(ts))
+            ts.append(time.perf_counter() - t0)
+        res["cpu_baseline"] = {"value": pct(ts, 50), "unit": "us per step (median)", "p99_us": pct(ts, 99),
+                               "cores": 1, "kind": "oracle",
+                               "sample": f"the same single-env step, {len(ts)} calls, FP64, one thread "
+                                         "(one env is one work unit)"}
+    return res
 
 
 BATCH_WORKLOAD = ("16384 envs x 2 pads; pad resolution 10x12..40x50, SDF from a pool of 32 grids 32^3..256^3, "

@@ -194,6 +194,20 @@ int tacsl_shade_image(const tacsl_shading* shading, int64_t B, const int32_t* se
                       const float* depth_map, uint8_t* rgb, tacsl_stream_t stream);
 
 /*
+ * tacsl_shade_image with the limit of its device-side barrier waits given explicitly, for
+ * tests of those bounded waits (the paper has no counterpart).  The image kernel streams
+ * depth tiles through a shared-memory ring guarded by barriers; every wait on them gives
+ * up after wait_ns nanoseconds of %globaltimer (tacsl_shade_image uses 2 s), sets
+ * TACSL_DEVERR_TIMEOUT in the device error word and ends its warp's loop, after the
+ * producer warp has waited (with the 2 s limit) for the copies it already issued.  The
+ * images are then incomplete.  wait_ns = 0 means the default.  A tiny limit makes the
+ * waits run out on purpose; the next call with the default limit works normally.
+ */
+int tacsl_shade_image_wait_limit(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id,
+                                 const float* depth_map, uint8_t* rgb, uint64_t wait_ns,
+                                 tacsl_stream_t stream);
+
+/*
  * The whole tactile step in one call: tacsl_shade_image on the E*P depth maps (image
  * b = e*P + p belongs to pad (e, p)) and tacsl_penalty_forces on the E x P pads.
  * Arguments and results are exactly those of the two calls; shading may be NULL to skip
@@ -214,11 +228,18 @@ int tacsl_tactile_step(const tacsl_sdf_set* set, const tacsl_contact_params* par
  *   depth_map [E][P][H][W] float32 (16-byte aligned):
  *     D = d0 - max(0, -z_hit), z_hit = the first point of the object on the pixel's column
  *     over [-z_max, 0] (marching up from -z_max), D = d0 where the column misses it.
- * The march: steps of phi/sqrt(3) where the column is inside the grid's domain (phi = the
- * trilinear SDF), the distance to the domain box outside it, never below voxel/8; the
- * first step that lands inside the object (in the domain with phi <= 0; outside the domain
- * the SDF is undefined and never counts) closes a bracket that is halved until it is at
- * most voxel * 2^-16 wide; z_hit is its upper end.  A bad obj_id gives NaN maps and sets TACSL_DEVERR_BAD_OBJ_ID.
+ * The march: where the column is inside the grid's domain (phi = the trilinear SDF) it
+ * steps phi/|R e_z|_1, R e_z being the column's direction in the grid frame (each partial
+ * derivative of the trilinear interpolant of a 1-Lipschitz grid is at most 1, so phi
+ * changes by at most |R e_z|_1 per unit of column height; 1 for a pad aligned with the
+ * grid, sqrt(3) at worst); the part of the column outside the domain is skipped by a slab
+ * test; no step is below voxel/8.  The first step that lands inside the object (in the
+ * domain with phi <= 0; outside the domain the SDF is undefined and never counts) closes
+ * a bracket that is halved until it is at most voxel * 2^-16 wide; z_hit is its upper
+ * end.  (The FP64 oracle's march keeps the isotropic step phi/sqrt(3); both are
+ * conservative, so they can differ only on columns where the object dips below the
+ * voxel/8 minimum step for less than one such step.)  A bad obj_id gives NaN maps and
+ * sets TACSL_DEVERR_BAD_OBJ_ID.
  */
 int tacsl_render_depth(const tacsl_sdf_set* set, int32_t E, int32_t P, const int32_t* obj_id,
                        const float* pad_pose, const tacsl_camera* camera, float* depth_map,

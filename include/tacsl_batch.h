@@ -154,8 +154,12 @@ int tacsl_batch_forces(const tacsl_batch_plan* plan, void* workspace, const tacs
  * of T in pad order; wrench [n_pad][6]); desc->sensor is ignored.
  *   - At most 65528 pads per call; more returns TACSL_ERR_UNSUPPORTED.
  *   - The first call on a device looks up the array's address there (set-up, once per
- *     device, with that device current); make that first call before any stream
- *     capture.
+ *     device, with that device current).
+ *   - The call cannot be captured in a CUDA graph: on a stream that is capturing it
+ *     returns TACSL_ERR_UNSUPPORTED and enqueues nothing (tacsl_batch_graph_create is
+ *     the capturable form).
+ *   - The schedule is copied from pageable host memory, which CUDA may do synchronously:
+ *     the call can block until the work already on stream has finished.
  *   - Every call shares the one array and it keeps the last call's contents: calls whose
  *     work overlaps on the GPU (different streams, or different host threads without
  *     ordering) race on it.  Calls on one stream are ordered and safe. */

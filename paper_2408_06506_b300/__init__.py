@@ -91,6 +91,8 @@ def load():
         lib.tacsl_pad_wrench.argtypes = [I64, I32, P, P, P, P, P]
         lib.tacsl_shade_image.restype = C.c_int
         lib.tacsl_shade_image.argtypes = [C.POINTER(_Shading), I64, P, P, P, P]
+        lib.tacsl_shade_image_wait_limit.restype = C.c_int
+        lib.tacsl_shade_image_wait_limit.argtypes = [C.POINTER(_Shading), I64, P, P, P, C.c_uint64, P]
         lib.tacsl_tactile_step.restype = C.c_int
         lib.tacsl_tactile_step.argtypes = [C.POINTER(_SdfSet), C.POINTER(_Params), I32, I32, I32, P, P, P, P,
                                            P, P, P, P, C.POINTER(_Shading), P, P, P, P]

@@ -98,11 +98,21 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
 }
 
 // Wait until the barrier's phase with the given parity has completed, for at most
-// ~`limit_ns` nanoseconds.  Returns false on timeout (the caller then aborts).
+// ~`limit_ns` nanoseconds.  Returns false on timeout (the caller then aborts).  A phase
+// already complete costs one non-blocking test.  Otherwise the wait polls with try_wait
+// (which may suspend the thread in hardware) and reads the clock every 64 polls; limits
+// below 1 ms (tests of the timeout path) poll without suspending and read the clock every
+// time, so that a wait longer than the limit reliably gives up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
                                                   uint64_t limit_ns = 2000000000ull) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_test(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
+    if (limit_ns < 1000000ull) {
+        for (;;) {
+            if (mbar_test(bar, parity)) return true;
+            if (global_timer_ns() - t0 > limit_ns) return false;
+        }
+    }
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 63u && global_timer_ns() - t0 > limit_ns) return false;
@@ -149,6 +159,13 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
             dst),
         "l"(src), "r"(bytes), "r"(bar), "l"(pol)
         : "memory");
+}
+
+// The same without a cache hint.
+__device__ __forceinline__ void bulk_g2s_nohint(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
 }
 
 // Bulk copy shared::cta -> global (bulk-group completion), with an L2 cache policy.

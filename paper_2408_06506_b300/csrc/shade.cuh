@@ -2,15 +2,18 @@
 // RGB (Sec. III-B of arXiv 2408.06506, I_rgb = F(I_depth)).
 //
 // Design (B300):
-// * A tile is 1920 consecutive pixels of the flattened H*W image, 4 per compute
-//   thread.  A work item is (block of M images, sensor s, tile); one CTA per SM takes
-//   items round-robin and keeps the item's 18 shading coefficients per pixel (72
-//   floats per thread) in REGISTERS while it streams the block's images of sensor s
-//   through them, so coefficients are read once per item, not once per image.
+// * Four horizontally adjacent pixels per compute thread; a tile is the compute warps'
+//   pixels of the flattened H*W image (1408 for the uniform kernel's 11 compute warps,
+//   1920 for the batched kernel's 15).  A work item is (block of M images, sensor s,
+//   tile); one CTA per SM takes items and keeps the item's 18 shading coefficients per
+//   pixel (72 floats per thread) in REGISTERS while it streams the block's images of
+//   sensor s through them, so coefficients are read once per item, not once per image.
 // * A producer warp streams each image's tile plus one halo row above and below (a
 //   contiguous byte range) into a ring of shared-memory stages with the bulk copy
-//   engine (cp.async.bulk), signalling full/empty mbarriers; the 15 compute warps
-//   never meet at a block-wide barrier.
+//   engine (cp.async.bulk), signalling full/empty mbarriers; the compute warps never
+//   meet at a block-wide barrier.  In the uniform kernel a stage holds three images, so
+//   a compute warp's fixed cost per stage is shared by three images and their shading
+//   chains interleave.
 // * Normals use only shared memory: the thread's 4 pixels, their up/down rows and
 //   the two horizontal neighbours.  Borders use one-sided differences via
 //   per-thread offsets and scale factors chosen once per item.
@@ -23,8 +26,10 @@
 //   undeformed gel) writes the item's background bytes, which are exactly what the
 //   full evaluation gives for n = (0, 0, -1).
 // * Each thread writes its four pixels' RGB as three 4-byte words straight to global
-//   memory (L2 merges a warp's 384 contiguous bytes into whole sectors); L2 policies
-//   mark the depth stream evict-first and the coefficients evict-last.
+//   memory (L2 merges a warp's 384 contiguous bytes into whole sectors); the
+//   coefficients carry an evict-last L2 policy.
+// * Every barrier wait is bounded (2 s by default; the limit is a kernel argument in the
+//   uniform kernel); a warp that gives up sets TACSL_DEVERR_TIMEOUT and leaves.
 #pragma once
 
 #include "common.cuh"
@@ -66,6 +71,7 @@ struct ShadeArgs {
     float cx_c, cx_e, cy_c, cy_e;   // 1/(2 pitch_x), 1/pitch_x, 1/(2 pitch_y), 1/pitch_y
     int n_stages, stage_floats;
     int store_mode;
+    uint64_t wait_ns;           // limit of every barrier wait (TACSL default: 2 s)
 };
 
 // Work item k = (image block, sensor, tile), tile fastest: consecutive items - run at
@@ -165,104 +171,8 @@ __device__ __forceinline__ int next_item(const ShadeArgs& A, int k) {
     return A.n_items;
 }
 
-// Stage item k's 18 coefficient rows into shared memory (lane 0 issues the copies).
-__device__ __forceinline__ void load_coefficients(const ShadeArgs& A, int k, float* coef, uint64_t* cfull,
-                                                  uint64_t pol) {
-    const Item it = decode_item(A, k);
-    const int tile_start = it.tile * kShTile;
-    const uint32_t row_bytes = static_cast<uint32_t>(min(kShTile, A.HW - tile_start)) * 4u;
-    mbar_arrive_expect_tx(smem_u32(cfull), 18u * row_bytes);
-    const float* src = A.coeffs + static_cast<int64_t>(it.s) * 18 * A.HW + tile_start;
-    for (int r = 0; r < 18; ++r)
-        bulk_g2s(smem_u32(coef + r * kShTile), src + static_cast<int64_t>(r) * A.HW, row_bytes, smem_u32(cfull), pol);
-}
-
-// Producer warp: walks this CTA's items that hold images of their sensor.  Each item's
-// coefficient rows are staged into shared memory one item ahead: as soon as the compute
-// warps have copied item k's coefficients into registers (coefficient-empty barrier),
-// the producer copies item k+1's, while it keeps streaming item k's images - each
-// image's tile plus one halo row above and below, a contiguous byte range - into the
-// stage ring, announcing (image, item) in meta[].
-__device__ __forceinline__ void shade_producer(const ShadeArgs& A, unsigned char* smem) {
-    const int lane = threadIdx.x & 31;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffFull);
-    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + kOffEmpty);
-    uint64_t* cfull = reinterpret_cast<uint64_t*>(smem + kOffCoefFull);
-    uint64_t* cempty = reinterpret_cast<uint64_t*>(smem + kOffCoefEmpty);
-    int2* meta = reinterpret_cast<int2*>(smem + kOffMeta);
-    float* coef = reinterpret_cast<float*>(smem + kOffCoef);
-    float* stages = reinterpret_cast<float*>(smem + kOffStage);
-    const int NS = A.n_stages;
-    const uint64_t pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
-    int st = 0;
-    uint32_t ph = 0, cph = 0;   // cph: phase of the coefficient-empty barrier to wait for next
-    bool ok = true;
-    int k = (static_cast<int>(blockIdx.x) < A.n_items && item_has_images(A, decode_item(A, blockIdx.x)))
-                ? static_cast<int>(blockIdx.x)
-                : next_item(A, blockIdx.x);
-    if (k < A.n_items && lane == 0) load_coefficients(A, k, coef, cfull, pol_keep);   // buffer starts free
-    while (k < A.n_items && ok) {
-        const int kn = next_item(A, k);
-        bool next_loaded = kn >= A.n_items;
-        const Item it = decode_item(A, k);
-        const int b0 = it.blk * A.M, b1 = min(b0 + A.M, A.B);
-        const int tile_start = it.tile * kShTile;
-        const int tile_px = min(kShTile, A.HW - tile_start);
-        const int lo_px = max(tile_start - A.W, 0);
-        const uint32_t bytes = static_cast<uint32_t>(min(tile_start + tile_px + A.W, A.HW) - lo_px) * 4u;
-        for (int base = b0; base < b1 && ok; base += 32) {
-            const int b = base + lane;
-            const int sid = b < b1 ? __ldg(A.sensor_id + b) : -1;
-            unsigned bal = __ballot_sync(0xffffffffu, sid == it.s);
-            while (bal != 0u && ok) {
-                const int j = __ffs(bal) - 1;
-                bal &= bal - 1u;
-                if (lane == 0) {
-                    if (mbar_wait_bounded(smem_u32(&empty[st]), ph ^ 1u)) {
-                        meta[st] = make_int2(base + j, k);
-                        mbar_arrive_expect_tx(smem_u32(&full[st]), bytes);
-                        bulk_g2s(smem_u32(stages + static_cast<int64_t>(st) * A.stage_floats),
-                                 A.depth + static_cast<int64_t>(base + j) * A.HW + lo_px, bytes, smem_u32(&full[st]),
-                                 pol_stream);
-                    } else {
-                        raise_dev_error(TACSL_DEVERR_TIMEOUT);
-                        ok = false;
-                    }
-                    // stage the next item's coefficients once item k's have been taken
-                    if (ok && !next_loaded && mbar_test(smem_u32(cempty), cph)) {
-                        load_coefficients(A, kn, coef, cfull, pol_keep);
-                        next_loaded = true;
-                    }
-                }
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                next_loaded = __shfl_sync(0xffffffffu, next_loaded, 0);
-                if (++st == NS) { st = 0; ph ^= 1u; }
-            }
-        }
-        if (ok && !next_loaded) {
-            // item k ended before its coefficients were taken: wait for that, then stage kn
-            if (lane == 0) {
-                if (mbar_wait_bounded(smem_u32(cempty), cph))
-                    load_coefficients(A, kn, coef, cfull, pol_keep);
-                else {
-                    raise_dev_error(TACSL_DEVERR_TIMEOUT);
-                    ok = false;
-                }
-            }
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-        }
-        cph ^= 1u;
-        k = kn;
-    }
-    // end-of-stream marker: an arrival without bytes completes the stage's phase
-    if (lane == 0 && mbar_wait_bounded(smem_u32(&empty[st]), ph ^ 1u)) {
-        meta[st] = make_int2(-1, -1);
-        mbar_arrive(smem_u32(&full[st]));
-    }
-}
-
 // ---------------------------------------------------------------------------
-// Compute-warp building blocks (shared by the uniform and the batched kernel)
+// Compute-warp building blocks of the batched image kernel (four pixels per thread)
 // ---------------------------------------------------------------------------
 
 // Where this thread's four pixels of one tile and their neighbours sit in a stage
@@ -275,10 +185,11 @@ struct TileGeom {
     bool px_valid;
 };
 
+template <int TILE = kShTile>
 __device__ __forceinline__ void tile_geometry(int H, int W, int HW, int tile, float cx_c, float cx_e, float cy_c,
                                               float cy_e, int stage_floats, int tid, TileGeom& g) {
-    g.tile_start = tile * kShTile;
-    const int tile_px = min(kShTile, HW - g.tile_start);
+    g.tile_start = tile * TILE;
+    const int tile_px = min(TILE, HW - g.tile_start);
     const int lo_px = max(g.tile_start - W, 0);
     g.px_valid = 4 * tid < tile_px;
     const int p = g.tile_start + 4 * tid;
@@ -309,6 +220,7 @@ struct TileCoefs {
     uint32_t bg0, bg1, bg2;           // RGB of a flat neighbourhood (n = (0, 0, -1))
 };
 
+template <int TILE = kShTile>
 __device__ __forceinline__ void take_coefficients(const float* coef, const TileGeom& g, int tid, TileCoefs& c) {
     // coefficients in units of 1/256 with the rounding half folded into the bias:
     // A0/256 + 1/512 and Ak/256 (exact power-of-two scaling)
@@ -318,7 +230,7 @@ __device__ __forceinline__ void take_coefficients(const float* coef, const TileG
     for (int k = 0; k < 6; ++k)
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(coef + (k * 3 + ch) * kShTile + q);
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(coef + (k * 3 + ch) * TILE + q);
             c.cf[k][ch][0] = k == 0 ? fma2(v.x, s256, h512) : mul2(v.x, s256);
             c.cf[k][ch][1] = k == 0 ? fma2(v.y, s256, h512) : mul2(v.y, s256);
         }
@@ -426,21 +338,330 @@ __device__ __forceinline__ void shade_init_barriers(unsigned char* smem, int NS)
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A) {
+// ---------------------------------------------------------------------------
+// Uniform image kernel (tacsl_shade_image, tacsl_tactile_step)
+// ---------------------------------------------------------------------------
+//
+// The producer / compute-warp pipeline above, with IPS images per ring stage: the
+// producer fills a stage with the tiles of IPS consecutive images of the item (one
+// barrier phase for all their copies), and a compute warp takes them in one iteration.
+// A warp's fixed cost per iteration (barrier wait, stage lookup, release, store
+// addressing, loop) is then shared by IPS images, and their shading chains are
+// independent, so the scheduler can interleave them.  NW compute warps of four pixels
+// per thread make a tile of NW * 128 pixels.  The per-pixel arithmetic and its order are
+// those of shade_four, so the bytes are the same for every NW and IPS.
+
+template <int NW, int IPS>
+struct ShadeCfg {
+    static constexpr int kWarps = NW;                      // compute warps
+    static constexpr int kImages = IPS;                    // images per ring stage
+    static_assert(IPS >= 1 && IPS <= 3, "a stage's meta holds up to three images");
+    static constexpr int kThreads = NW * 32 + 32;          // + one producer warp
+    static constexpr int kTile = NW * 32 * 4;              // pixels per tile
+    // shared memory: barriers, per-stage meta (int4), coefficient tile, ring
+    static constexpr int kOffFull = 0;
+    static constexpr int kOffEmpty = kOffFull + kShMaxStages * 8;
+    static constexpr int kOffCoefFull = kOffEmpty + kShMaxStages * 8;
+    static constexpr int kOffCoefEmpty = kOffCoefFull + 8;
+    static constexpr int kOffMeta = kOffCoefEmpty + 8;
+    static constexpr int kOffCoef = (kOffMeta + kShMaxStages * 16 + 127) / 128 * 128;
+    static constexpr int kOffStage = kOffCoef + 18 * kTile * 4;
+    // slot_floats: one image's tile plus its two halo rows
+    static constexpr int smem_bytes(int n_stages, int slot_floats) {
+        return kOffStage + n_stages * IPS * slot_floats * 4;
+    }
+};
+
+// Stage item k's 18 coefficient rows into shared memory (lane 0 issues the copies).
+template <int TILE>
+__device__ __forceinline__ void load_item_coefficients(const ShadeArgs& A, int k, float* coef, uint64_t* cfull,
+                                                       uint64_t pol) {
+    const Item it = decode_item(A, k);
+    const int tile_start = it.tile * TILE;
+    const uint32_t row_bytes = static_cast<uint32_t>(min(TILE, A.HW - tile_start)) * 4u;
+    mbar_arrive_expect_tx(smem_u32(cfull), 18u * row_bytes);
+    const float* src = A.coeffs + static_cast<int64_t>(it.s) * 18 * A.HW + tile_start;
+    for (int r = 0; r < 18; ++r)
+        bulk_g2s(smem_u32(coef + r * TILE), src + static_cast<int64_t>(r) * A.HW, row_bytes, smem_u32(cfull), pol);
+}
+
+// Producer warp: walks this CTA's items that hold images of their sensor.  Each item's
+// coefficient rows are staged into shared memory one item ahead: as soon as the compute
+// warps have copied item k's coefficients into registers (coefficient-empty barrier),
+// the producer copies item k+1's, while it keeps streaming item k's images - each
+// image's tile plus one halo row above and below, a contiguous byte range - into the
+// stage ring, IPS images per stage, announcing (images, item) in meta[] (missing
+// images are -1).  Every wait is bounded by A.wait_ns; after a timeout the warp
+// stops issuing, and before it returns it waits (bounded by the default limit) until
+// every copy it issued has landed, so that the CTA never ends with a copy into its
+// shared memory still in flight.
+template <class CFG>
+__device__ __forceinline__ void uniform_producer(const ShadeArgs& A, unsigned char* smem) {
+    constexpr int TILE = CFG::kTile, IPS = CFG::kImages;
+    const int lane = threadIdx.x & 31;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + CFG::kOffFull);
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + CFG::kOffEmpty);
+    uint64_t* cfull = reinterpret_cast<uint64_t*>(smem + CFG::kOffCoefFull);
+    uint64_t* cempty = reinterpret_cast<uint64_t*>(smem + CFG::kOffCoefEmpty);
+    int4* meta = reinterpret_cast<int4*>(smem + CFG::kOffMeta);
+    float* coef = reinterpret_cast<float*>(smem + CFG::kOffCoef);
+    float* stages = reinterpret_cast<float*>(smem + CFG::kOffStage);
+    const int NS = A.n_stages;
+    const int64_t stage_stride = static_cast<int64_t>(IPS) * A.stage_floats;
+    const uint64_t pol_keep = policy_evict_last();
+    int st = 0;
+    uint32_t ph = 0, cph = 0;   // cph: phase of the coefficient-empty barrier to wait for next
+    uint32_t n_fill = 0, n_coef = 0;   // stage phases and coefficient phases started (lane 0)
+    bool ok = true;
+    int k = (static_cast<int>(blockIdx.x) < A.n_items && item_has_images(A, decode_item(A, blockIdx.x)))
+                ? static_cast<int>(blockIdx.x)
+                : next_item(A, blockIdx.x);
+    if (k < A.n_items && lane == 0) {   // the coefficient buffer starts free
+        load_item_coefficients<TILE>(A, k, coef, cfull, pol_keep);
+        ++n_coef;
+    }
+    while (k < A.n_items && ok) {
+        const int kn = next_item(A, k);
+        bool next_loaded = kn >= A.n_items;
+        const Item it = decode_item(A, k);
+        const int b0 = it.blk * A.M, b1 = min(b0 + A.M, A.B);
+        const int tile_start = it.tile * TILE;
+        const int tile_px = min(TILE, A.HW - tile_start);
+        const int lo_px = max(tile_start - A.W, 0);
+        const uint32_t bytes = static_cast<uint32_t>(min(tile_start + tile_px + A.W, A.HW) - lo_px) * 4u;
+        // fill one stage with the images g0, g1, g2 (the first n_grp of them; n_grp <= IPS)
+        int g0 = -1, g1 = -1, g2 = -1;
+        int n_grp = 0;
+        auto fill = [&]() {
+            if (lane == 0) {
+                if (mbar_wait_bounded(smem_u32(&empty[st]), ph ^ 1u, A.wait_ns)) {
+                    meta[st] = make_int4(g0, n_grp > 1 ? g1 : -1, n_grp > 2 ? g2 : -1, k);
+                    mbar_arrive_expect_tx(smem_u32(&full[st]), static_cast<uint32_t>(n_grp) * bytes);
+                    // the depth tiles carry no L2 hint: their first and last rows are read
+                    // again, as halo, by the CTAs working on the neighbouring tiles
+                    float* dst = stages + st * stage_stride;
+                    const float* src = A.depth + lo_px;
+                    bulk_g2s_nohint(smem_u32(dst), src + static_cast<int64_t>(g0) * A.HW, bytes, smem_u32(&full[st]));
+                    if (IPS > 1 && n_grp > 1)
+                        bulk_g2s_nohint(smem_u32(dst + A.stage_floats), src + static_cast<int64_t>(g1) * A.HW, bytes,
+                                        smem_u32(&full[st]));
+                    if (IPS > 2 && n_grp > 2)
+                        bulk_g2s_nohint(smem_u32(dst + 2 * A.stage_floats), src + static_cast<int64_t>(g2) * A.HW,
+                                        bytes, smem_u32(&full[st]));
+                    ++n_fill;
+                } else {
+                    raise_dev_error(TACSL_DEVERR_TIMEOUT);
+                    ok = false;
+                }
+                // stage the next item's coefficients once item k's have been taken
+                if (ok && !next_loaded && mbar_test(smem_u32(cempty), cph)) {
+                    load_item_coefficients<TILE>(A, kn, coef, cfull, pol_keep);
+                    ++n_coef;
+                    next_loaded = true;
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            next_loaded = __shfl_sync(0xffffffffu, next_loaded, 0);
+            n_grp = 0;
+            if (++st == NS) { st = 0; ph ^= 1u; }
+        };
+        for (int base = b0; base < b1 && ok; base += 32) {
+            const int b = base + lane;
+            const int sid = b < b1 ? __ldg(A.sensor_id + b) : -1;
+            unsigned bal = __ballot_sync(0xffffffffu, sid == it.s);
+            while (bal != 0u && ok) {
+                const int img = base + __ffs(bal) - 1;
+                bal &= bal - 1u;
+                if (n_grp == 0) g0 = img;
+                else if (n_grp == 1) g1 = img;
+                else g2 = img;
+                if (++n_grp == IPS) fill();
+            }
+        }
+        if (ok && n_grp > 0) fill();
+        if (ok && !next_loaded) {
+            // item k ended before its coefficients were taken: wait for that, then stage kn
+            if (lane == 0) {
+                if (mbar_wait_bounded(smem_u32(cempty), cph, A.wait_ns)) {
+                    load_item_coefficients<TILE>(A, kn, coef, cfull, pol_keep);
+                    ++n_coef;
+                } else {
+                    raise_dev_error(TACSL_DEVERR_TIMEOUT);
+                    ok = false;
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+        }
+        cph ^= 1u;
+        k = kn;
+    }
+    if (lane != 0) return;
+    // end-of-stream marker: an arrival without bytes completes the stage's phase
+    if (mbar_wait_bounded(smem_u32(&empty[st]), ph ^ 1u, A.wait_ns)) {
+        meta[st] = make_int4(-1, -1, -1, -1);
+        mbar_arrive(smem_u32(&full[st]));
+        ++n_fill;
+    } else {
+        raise_dev_error(TACSL_DEVERR_TIMEOUT);
+    }
+    // Drain: stage phase i (i = 0, 1, ...) is stage i % NS with parity (i / NS) & 1, and
+    // only this lane arrives on the full barriers, so a phase still pending is one whose
+    // copies have not landed.  In a normal run the compute warps wait for every copy
+    // anyway and these waits return at once; after a timeout they may have left already.
+    const uint32_t uNS = static_cast<uint32_t>(NS);
+    for (uint32_t i = n_fill > uNS ? n_fill - uNS : 0u; i < n_fill; ++i)
+        if (!mbar_wait_bounded(smem_u32(&full[i % uNS]), (i / uNS) & 1u)) raise_dev_error(TACSL_DEVERR_TIMEOUT);
+    if (n_coef > 0u && !mbar_wait_bounded(smem_u32(cfull), (n_coef - 1u) & 1u))
+        raise_dev_error(TACSL_DEVERR_TIMEOUT);
+}
+
+// One elected lane arrives on the barrier after the warp's shared-memory reads (no branch).
+__device__ __forceinline__ void warp_arrive(uint32_t bar) {
+    __syncwarp();
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "@p mbarrier.arrive.shared::cta.b64 _, [%0];\n\t}" ::"r"(bar)
+        : "memory");
+}
+
+// Bounded wait on a barrier phase that every lane of the warp polls; the result is made
+// warp-uniform, so that the warp either goes on or leaves as one.
+__device__ __forceinline__ bool warp_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    const bool ok = mbar_wait_bounded(bar, parity, limit_ns);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// The full evaluation of the four pixels' RGB words (the arithmetic of shade_four).
+__device__ __forceinline__ void quad_eval(const float (&ex)[4], const f2 (&ey)[2], const TileGeom& g,
+                                          const TileCoefs& c, uint32_t (&w)[3]) {
+    const f2 one2 = pk(1.f, 1.f);
+    const f2 gx0 = mul2(pk(ex[0], ex[1]), g.cxp0);
+    const f2 gx1 = mul2(pk(ex[2], ex[3]), g.cxp1);
+    const f2 gy0 = mul2(ey[0], g.cyy);
+    const f2 gy1 = mul2(ey[1], g.cyy);
+    f2 q[2][3];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const f2 gx = j ? gx1 : gx0, gy = j ? gy1 : gy0;
+        const f2 s2 = fma2(gx, gx, fma2(gy, gy, one2));
+        const f2 r = pk(rsqrt_ge1(lo(s2)), rsqrt_ge1(hi(s2)));
+        const f2 nx = mul2(gx, r), ny = mul2(gy, r);
+        const f2 m3 = mul2(nx, nx), m4 = mul2(ny, ny), m5 = mul2(nx, ny);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            // t = (I + 0.5)/256: four packed FMAs, the last term per lane with saturation
+            const f2 part = fma2(c.cf[4][ch][j], m4,
+                                 fma2(c.cf[3][ch][j], m3, fma2(c.cf[2][ch][j], ny, fma2(c.cf[1][ch][j], nx, c.cf[0][ch][j]))));
+            const float ta = __saturatef(fmaf(lo(c.cf[5][ch][j]), lo(m5), lo(part)));
+            const float tb = __saturatef(fmaf(hi(c.cf[5][ch][j]), hi(m5), hi(part)));
+            q[j][ch] = floor256(ta, tb);
+        }
+    }
+    // q[j][ch] holds pixels (2j, 2j+1); memory order is px0 rgb, px1 rgb, px2 rgb, px3 rgb
+    w[0] = pack_u8x4(__float_as_uint(lo(q[0][0])), __float_as_uint(lo(q[0][1])), __float_as_uint(lo(q[0][2])),
+                     __float_as_uint(hi(q[0][0])));
+    w[1] = pack_u8x4(__float_as_uint(hi(q[0][1])), __float_as_uint(hi(q[0][2])), __float_as_uint(lo(q[1][0])),
+                     __float_as_uint(lo(q[1][1])));
+    w[2] = pack_u8x4(__float_as_uint(lo(q[1][2])), __float_as_uint(hi(q[1][0])), __float_as_uint(hi(q[1][1])),
+                     __float_as_uint(hi(q[1][2])));
+}
+
+template <int STORE>
+__device__ __forceinline__ void quad_store(uint8_t* dst, const uint32_t (&w)[3]) {
+    if constexpr (STORE == kStoreWord) {
+        store_words(dst, w[0], w[1], w[2]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) dst[k] = static_cast<uint8_t>(w[k >> 2] >> (8 * (k & 3)));
+    }
+}
+
+// The RGB words of this thread's four pixels in each of the stage's IPS images (slot i
+// at sp + i * slot_floats; image i is missing when img[i] < 0).  The warp arrives on the
+// stage's empty barrier as soon as its shared-memory reads are done.  A warp whose 128
+// pixels of an image all see equal neighbours (the undeformed gel: D_x = D_y = 0,
+// n = (0, 0, -1)) takes the item's background words for it, which are bitwise what the
+// full evaluation gives; the other images get the full evaluation, in one block when all
+// of them need it, so that their independent chains can interleave.
+template <int IPS>
+__device__ __forceinline__ void shade_stage(const float* sp, int slot_floats, const int (&img)[3], const TileGeom& g,
+                                            const TileCoefs& c, uint32_t empty_bar, uint32_t (&w)[IPS][3]) {
+    float4 cv[IPS];
+    ulonglong2 up[IPS], dn[IPS];
+    float L[IPS], R[IPS];
+#pragma unroll
+    for (int i = 0; i < IPS; ++i) {
+        const float* s = sp + i * slot_floats;   // a missing image reads stale words of its slot
+        cv[i] = *reinterpret_cast<const float4*>(s + g.oc);
+        up[i] = *reinterpret_cast<const ulonglong2*>(s + g.ou);
+        dn[i] = *reinterpret_cast<const ulonglong2*>(s + g.od);
+        // horizontal neighbours: oL / oR already point at the edge pixel itself on the border
+        L[i] = s[g.oL];
+        R[i] = s[g.oR];
+    }
+    warp_arrive(empty_bar);   // this warp is done with the stage
+    float ex[IPS][4];
+    f2 ey[IPS][2];
+    bool dense[IPS];
+    bool any = false, all = true;
+#pragma unroll
+    for (int i = 0; i < IPS; ++i) {
+        ex[i][0] = cv[i].y - L[i];
+        ex[i][1] = cv[i].z - cv[i].x;
+        ex[i][2] = cv[i].w - cv[i].y;
+        ex[i][3] = R[i] - cv[i].z;
+        ey[i][0] = sub2(dn[i].x, up[i].x);
+        ey[i][1] = sub2(dn[i].y, up[i].y);
+        const bool flat = ((__float_as_uint(ex[i][0]) | __float_as_uint(ex[i][1]) | __float_as_uint(ex[i][2]) |
+                            __float_as_uint(ex[i][3]) | static_cast<uint32_t>(ey[i][0]) |
+                            static_cast<uint32_t>(ey[i][0] >> 32) | static_cast<uint32_t>(ey[i][1]) |
+                            static_cast<uint32_t>(ey[i][1] >> 32)) &
+                           0x7fffffffu) == 0u;
+        dense[i] = !__all_sync(0xffffffffu, flat || !g.px_valid || (i > 0 && img[i] < 0));
+        any = any || dense[i];
+        all = all && dense[i];
+        w[i][0] = c.bg0;
+        w[i][1] = c.bg1;
+        w[i][2] = c.bg2;
+    }
+    if (!any) return;
+    if (IPS == 1 || all) {
+#pragma unroll
+        for (int i = 0; i < IPS; ++i) quad_eval(ex[i], ey[i], g, c, w[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < IPS; ++i)
+            if (dense[i]) quad_eval(ex[i], ey[i], g, c, w[i]);
+    }
+}
+
+template <class CFG, int STORE>
+__global__ void __launch_bounds__(CFG::kThreads, 1) shade_kernel(const ShadeArgs A) {
+    constexpr int IPS = CFG::kImages, TILE = CFG::kTile;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffFull);
-    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + kOffEmpty);
-    uint64_t* cfull = reinterpret_cast<uint64_t*>(smem + kOffCoefFull);
-    uint64_t* cempty = reinterpret_cast<uint64_t*>(smem + kOffCoefEmpty);
-    const int2* meta = reinterpret_cast<const int2*>(smem + kOffMeta);
-    const float* coef = reinterpret_cast<const float*>(smem + kOffCoef);
-    const float* stages = reinterpret_cast<const float*>(smem + kOffStage);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + CFG::kOffFull);
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + CFG::kOffEmpty);
+    uint64_t* cfull = reinterpret_cast<uint64_t*>(smem + CFG::kOffCoefFull);
+    uint64_t* cempty = reinterpret_cast<uint64_t*>(smem + CFG::kOffCoefEmpty);
+    const int4* meta = reinterpret_cast<const int4*>(smem + CFG::kOffMeta);
+    const float* coef = reinterpret_cast<const float*>(smem + CFG::kOffCoef);
+    const float* stages = reinterpret_cast<const float*>(smem + CFG::kOffStage);
     const int NS = A.n_stages;
 
-    shade_init_barriers(smem, NS);
-    if (warp == kShConsumerWarps) {
-        shade_producer(A, smem);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), CFG::kWarps);
+        }
+        mbar_init(smem_u32(cfull), 1);
+        mbar_init(smem_u32(cempty), CFG::kWarps);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == CFG::kWarps) {
+        uniform_producer<CFG>(A, smem);
         return;
     }
 
@@ -451,38 +672,34 @@ __global__ void __launch_bounds__(kShThreads, 1) shade_kernel(const ShadeArgs A)
     int st = 0;
     uint32_t ph = 0, cph = 0;
     for (;;) {
-        if (!mbar_wait_bounded(smem_u32(&full[st]), ph)) {
+        if (!warp_wait_bounded(smem_u32(&full[st]), ph, A.wait_ns)) {
             if (lane == 0) raise_dev_error(TACSL_DEVERR_TIMEOUT);
             break;
         }
-        const int2 m = meta[st];
+        const int4 m = meta[st];   // (image 0, image 1, image 2, item); -1: no image
         if (m.x < 0) break;
-        if (m.y != cur_item) {
+        if (m.w != cur_item) {
             // new item: geometry, then the tile's coefficients from shared memory
-            cur_item = m.y;
-            const Item it = decode_item(A, m.y);
-            tile_geometry(A.H, A.W, A.HW, it.tile, A.cx_c, A.cx_e, A.cy_c, A.cy_e, A.stage_floats, tid, g);
-            if (!mbar_wait_bounded(smem_u32(cfull), cph)) {
+            cur_item = m.w;
+            tile_geometry<TILE>(A.H, A.W, A.HW, decode_item(A, m.w).tile, A.cx_c, A.cx_e, A.cy_c, A.cy_e,
+                                A.stage_floats, tid, g);
+            if (!warp_wait_bounded(smem_u32(cfull), cph, A.wait_ns)) {
                 if (lane == 0) raise_dev_error(TACSL_DEVERR_TIMEOUT);
                 break;
             }
             cph ^= 1u;
-            take_coefficients(coef, g, tid, c);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(cempty));
+            take_coefficients<TILE>(coef, g, tid, c);
+            warp_arrive(smem_u32(cempty));
         }
-        uint32_t w0, w1, w2;
-        shade_four(stages + static_cast<int64_t>(st) * A.stage_floats, g, c, &empty[st], lane, w0, w1, w2);
-        const int64_t img = m.x;
+        const int img[3] = {m.x, m.y, m.z};
+        uint32_t w[IPS][3];
+        shade_stage<IPS>(stages + static_cast<int64_t>(st) * IPS * A.stage_floats, A.stage_floats, img, g, c,
+                         smem_u32(&empty[st]), w);
         if (g.px_valid) {
-            uint8_t* dst = A.rgb + (img * A.HW + g.tile_start + 4 * tid) * 3;
-            if (A.store_mode == kStoreWord) {
-                store_words(dst, w0, w1, w2);
-            } else {
-                const uint32_t ws[3] = {w0, w1, w2};
+            const int64_t px = static_cast<int64_t>(g.tile_start) + 4 * tid;
 #pragma unroll
-                for (int k = 0; k < 12; ++k) dst[k] = static_cast<uint8_t>(ws[k >> 2] >> (8 * (k & 3)));
-            }
+            for (int i = 0; i < IPS; ++i)
+                if (i == 0 || img[i] >= 0) quad_store<STORE>(A.rgb + (static_cast<int64_t>(img[i]) * A.HW + px) * 3, w[i]);
         }
         if (++st == NS) { st = 0; ph ^= 1u; }
     }

@@ -8,7 +8,7 @@ import torch
 import paper_2408_06506_b300 as tacsl
 from paper_2408_06506_b300 import synth
 
-from gpu_common import (DEPTH_ATOL, assert_forces_close, assert_rgb_close, assert_wrench_close, dev,
+from gpu_common import (DEPTH_ATOL, RGB_TIE_BAND, assert_forces_close, assert_rgb_close, assert_wrench_close, dev,
                         force_abs_floor, scene_to_device, wrench_scale)
 
 pytestmark = pytest.mark.gpu
@@ -270,20 +270,36 @@ def test_tactile_step_matches_separate_calls(orc, E, ny, nx, H, W):
 
 def test_tactile_step_full_workload(orc):
     """4096 envs x 2 pads x 20x25 taxels, eight 128^3 objects, 8192 images of 320x240, in
-    the launch configuration the benchmark times.  Every taxel is checked; images are
-    checked on a sample of 48 plus a self-consistency check of all of them."""
+    the launch configuration the benchmark times.  Every taxel is checked, and every one
+    of the 8192 images: the oracle shades each distinct (depth map, sensor) pair of the
+    launch once, and each image slot is compared byte by byte with the oracle image of
+    its own pair (within 1 LSB, and only at rounding ties)."""
     sc = synth.scene_objects(seed=2, E=4096, P=2, depth_maps="cycled", n_distinct_maps=256)
     d = scene_to_device(sc)
     depth, fn, ft, wr, rgb = _step(d)
     torch.cuda.synchronize()
     _check_forces(sc, _oracle_forces(orc, sc), depth, fn, ft, wr)
-    sample = np.random.default_rng(0).choice(sc.E * sc.P, size=48, replace=False)
-    dm = sc.depth_map.reshape(-1, sc.H, sc.W)
-    ref_rgb, ref_I, _ = orc.shade(sc.coeffs, sc.pitch_x, sc.pitch_y, sc.sensor_id[sample], dm[sample],
-                                  with_intensity=True)
-    assert_rgb_close(rgb[torch.as_tensor(sample, device="cuda")].cpu().numpy(), ref_rgb, ref_I)
-    # images that share a depth map and a sensor must be identical
-    r = rgb.view(sc.E * sc.P, -1)
+    B = sc.E * sc.P
     nd = sc.meta["distinct_depth_maps"]
-    assert torch.equal(r[nd:2 * nd], r[:nd]) if nd % 2 == 0 else True
+    dm = sc.depth_map.reshape(B, sc.H, sc.W)
+    # slot b holds depth map b % nd (the generator cycles through the distinct maps)
+    src_map = np.arange(B) % nd
+    assert all(np.array_equal(dm[b], dm[src_map[b]]) for b in range(0, B, 97))
+    pairs, slot_pair = np.unique(np.stack([src_map, sc.sensor_id]), axis=1, return_inverse=True)
+    ref_rgb, ref_I, bad = orc.shade(sc.coeffs, sc.pitch_x, sc.pitch_y, pairs[1].astype(np.int32),
+                                    dm[pairs[0]], with_intensity=True)
+    assert bad == 0
+    ref_rgb_d = torch.as_tensor(ref_rgb).cuda()
+    # the intensity's distance from a rounding tie, where a 1-LSB difference is allowed
+    Ic = np.clip(ref_I, 0, 255)
+    near_tie = torch.as_tensor(np.abs(Ic - np.floor(Ic) - 0.5) < RGB_TIE_BAND).cuda()
+    slot_pair_d = torch.as_tensor(slot_pair.reshape(-1)).cuda()
+    n_diff = 0
+    for b0 in range(0, B, 1024):
+        idx = slot_pair_d[b0:b0 + 1024]
+        diff = (rgb[b0:b0 + 1024].to(torch.int16) - ref_rgb_d[idx].to(torch.int16)).abs()
+        assert int(diff.max()) <= 1
+        off = diff > 0
+        assert bool(near_tie[idx][off].all()), "1-LSB differences away from a rounding tie"
+        n_diff += int(off.sum())
     assert tacsl.check_errors() == 0

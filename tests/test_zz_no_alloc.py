@@ -5,8 +5,10 @@ schedule in a fixed array inside the library instead of a caller workspace.
 
 The test calls it through the C ABI twice in a row, on two different batches, and
 checks each result against tacsl_batch_forces (which uses a caller workspace) at the
-force tolerances of the other GPU tests.  It builds everything it needs itself, so it
-passes alone in a fresh process as well as after the rest of the suite."""
+force tolerances of the other GPU tests, and the second batch pad by pad against the
+FP64 oracle as well.  A call on a stream that is being captured into a CUDA graph is
+refused.  It builds everything it needs itself, so it passes alone in a fresh process
+as well as after the rest of the suite."""
 import ctypes as C
 
 import numpy as np
@@ -17,6 +19,7 @@ import paper_2408_06506_b300 as tacsl
 from paper_2408_06506_b300 import batch as tb
 from paper_2408_06506_b300 import build, synth
 
+from batch_common import check_pad, oracle_pad
 from gpu_common import (DEPTH_ATOL, PHI_F32_ERR, VT_F32_ERR, assert_forces_close, assert_wrench_close,
                         wrench_scale)
 
@@ -46,7 +49,7 @@ def _check_against(sc, plan, out, ref):
 
 
 @pytest.mark.gpu
-def test_static_scratch_forces_match_workspace_forces():
+def test_static_scratch_forces_match_workspace_forces(orc):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     build.build()
@@ -76,6 +79,24 @@ def test_static_scratch_forces_match_workspace_forces():
         torch.cuda.synchronize()
         assert tacsl.check_errors() == 0
         _check_against(sc, plan, out, ref)
+    # the second batch on its own terms: every pad against the FP64 oracle
+    for b in range(sc.n_pad):
+        o = int(plan.taxel_offset[b])
+        T = int(sc.layout_count[sc.layout[b]])
+        check_pad(sc, b, oracle_pad(orc, sc, b), out["depth"][o:o + T], out["f_n"][o:o + T], out["f_t"][o:o + T],
+                  out["wrench"][b])
+
+    # a call on a stream that is being captured is refused before it enqueues anything
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        g.capture_begin()
+        try:
+            rc = f(C.byref(plan.desc), C.byref(sdfs.c), C.byref(params.c), C.byref(io), C.c_void_p(side.cuda_stream))
+        finally:
+            g.capture_end()
+    assert rc == 2 and "captured" in lib.tacsl_last_error().decode()
+    torch.cuda.synchronize()
 
     # beyond the array's capacity: refused on the host, nothing launched
     n = 65529
