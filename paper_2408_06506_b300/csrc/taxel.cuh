@@ -13,10 +13,13 @@
 // and the gradient are gathered only for penetrating taxels.
 //
 // Work split: ONE WARP PER PAD.  Lanes take taxels lane, lane+32, ..., NP at a time so
-// that NP 27-node gathers are in flight per lane, and the warp folds the pad's wrench
-// with shuffles - no block-wide barrier, so many pads progress at once and the gathers'
-// latency overlaps.  SDF reads carry an L2 evict-last policy (the grids are re-read
-// every step).
+// that NP 8-node gathers are in flight per lane.  Taxels that do not penetrate get their
+// outputs (depth 0, zero forces) at once; the penetrating ones of each round are then
+// compacted over the warp's lanes, so the 27-node window and the force law run with as
+// many lanes busy as there are such taxels instead of once per slot with a few lanes
+// busy.  The warp folds the pad's wrench with shuffles - no block-wide barrier, so many
+// pads progress at once and the gathers' latency overlaps.  SDF reads carry an L2
+// evict-last policy (the grids are re-read every step).
 #pragma once
 
 #include "common.cuh"
@@ -98,6 +101,21 @@ __device__ __forceinline__ void stencil_fold(const Stencil& q, const float (&v)[
     g[0] = fmaf(q.cz[2], xd[2], fmaf(q.cz[1], xd[1], q.cz[0] * xd[0])) * inv_h;
     g[1] = fmaf(q.cz[2], cd[2], fmaf(q.cz[1], cd[1], q.cz[0] * cd[0])) * inv_h;
     g[2] = fmaf(q.dz[2], cc[2], fmaf(q.dz[1], cc[1], q.dz[0] * cc[0])) * inv_h;
+}
+
+// Position of the set bit of rank `rank` (0-based, from bit 0 up) of mask; rank must be
+// below popc(mask).  Binary search on the position with population counts.
+__device__ __forceinline__ int nth_set_bit(unsigned mask, int rank) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int c = __popc((mask >> pos) & ((1u << w) - 1u));
+        if (rank >= c) {
+            rank -= c;
+            pos += w;
+        }
+    }
+    return pos;
 }
 
 // Continuous grid index of an object-frame point and its domain test.
@@ -223,16 +241,36 @@ __device__ __forceinline__ void pad_taxels_by_warp(const SdfTable& tab, const Pa
     const uint64_t pol = policy_evict_last();
     const int n0 = S.n0, n01 = S.n0 * S.n1;
     const float* r = Pz.r;
+    // A taxel that does not penetrate (phi >= 0, out of the domain, or NaN) has depth 0
+    // and zero forces, whose pad-frame image R^T (0, 0, 0) carries the signs of R: the
+    // same words contact_force writes for it.  It adds nothing to the wrench.
+    float z[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) z[a] = fmaf(r[a], 0.f, fmaf(r[3 + a], 0.f, r[6 + a] * 0.f));
+    // lane l < 24 writes floats 4l .. 4l+3 of a slot's 96 force floats: components (4l + i) % 3
+    const int m0 = (4 * lane) % 3;   // component of this lane's first float; then m0+1, m0+2, m0 (mod 3)
+    const float za = m0 == 0 ? z[0] : (m0 == 1 ? z[1] : z[2]);
+    const float zb = m0 == 0 ? z[1] : (m0 == 1 ? z[2] : z[0]);
+    const float zc = m0 == 0 ? z[2] : (m0 == 1 ? z[0] : z[1]);
+    const float4 zq = make_float4(za, zb, zc, za);
+    // whole-chunk stores where the pad's three output rows start 16-byte aligned (a slot
+    // is 32 taxels, so the slots keep that alignment)
+    const bool out16 = ((reinterpret_cast<uintptr_t>(depth) | reinterpret_cast<uintptr_t>(f_n) |
+                         reinterpret_cast<uintptr_t>(f_t)) & 15u) == 0u;
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int t0 = lane; t0 < T; t0 += 32 * NP) {
+    // the round loop runs the same number of times on every lane (its body votes)
+    for (int round = 0; round < T; round += 32 * NP) {
+        const int t0 = round + lane;
+        // pass 1, every lane: NP posed taxels and phi from their 8-node cells (all NP
+        // gathers in flight together); the outputs of the taxels that do not penetrate
         float p[NP][3], phi8[NP];
         GridPos gp[NP];
-        bool on[NP];
+        unsigned pen[NP];   // per slot u: the lanes whose taxel t0 - lane + 32u + (that lane) penetrates
 #pragma unroll
         for (int u = 0; u < NP; ++u) {
             const int t = t0 + 32 * u;
-            on[u] = t < T;
-            const int tt = on[u] ? t : t0;
+            const bool on = t < T;
+            const int tt = on ? t : 0;
             p[u][0] = __ldg(taxels + 3 * tt);
             p[u][1] = __ldg(taxels + 3 * tt + 1);
             p[u][2] = __ldg(taxels + 3 * tt + 2);
@@ -240,48 +278,102 @@ __device__ __forceinline__ void pad_taxels_by_warp(const SdfTable& tab, const Pa
             const float yo = fmaf(r[3], p[u][0], fmaf(r[4], p[u][1], fmaf(r[5], p[u][2], Pz.t[1])));
             const float zo = fmaf(r[6], p[u][0], fmaf(r[7], p[u][1], fmaf(r[8], p[u][2], Pz.t[2])));
             gp[u] = grid_pos(S, xo, yo, zo);
-            gp[u].inside = gp[u].inside && on[u];
+            gp[u].inside = gp[u].inside && on;
         }
-        // phi from the 8-node cells (all NP gathers in flight together)
 #pragma unroll
         for (int u = 0; u < NP; ++u)
             phi8[u] = gp[u].inside ? phi_cell8(S, gp[u], pol) : __int_as_float(0x7f800000);
 #pragma unroll
         for (int u = 0; u < NP; ++u) {
-            if (!on[u]) continue;
             const int t = t0 + 32 * u;
-            float phi = phi8[u], g[3] = {0.f, 0.f, 0.f}, vel[3] = {0.f, 0.f, 0.f};
-            if (phi8[u] < 0.f) {
-                // relative velocity of the point, v + w x x (needed only in contact; the
-                // posed point is recomputed with the same operations as above)
-                const float xo = fmaf(r[0], p[u][0], fmaf(r[1], p[u][1], fmaf(r[2], p[u][2], Pz.t[0])));
-                const float yo = fmaf(r[3], p[u][0], fmaf(r[4], p[u][1], fmaf(r[5], p[u][2], Pz.t[1])));
-                const float zo = fmaf(r[6], p[u][0], fmaf(r[7], p[u][1], fmaf(r[8], p[u][2], Pz.t[2])));
-                vel[0] = Pz.v[0] + (Pz.w[1] * zo - Pz.w[2] * yo);
-                vel[1] = Pz.v[1] + (Pz.w[2] * xo - Pz.w[0] * zo);
-                vel[2] = Pz.v[2] + (Pz.w[0] * yo - Pz.w[1] * xo);
-                // penetrating: the 27-node window gives the gradient (and the same phi)
+            const bool in_contact = gp[u].inside && phi8[u] < 0.f;
+            const int slot = round + 32 * u;
+            if (out16 && slot + 32 <= T) {
+                // the slot's 32 taxels as whole 16-byte chunks, all with the no-contact
+                // words; pass 2 then rewrites the penetrating ones (after a warp barrier)
+                if (lane < 8) *reinterpret_cast<float4*>(depth + slot + 4 * lane) = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (lane < 24) {
+                    *reinterpret_cast<float4*>(f_n + 3 * slot + 4 * lane) = zq;
+                    *reinterpret_cast<float4*>(f_t + 3 * slot + 4 * lane) = zq;
+                }
+            } else if (t < T && !in_contact) {
+                depth[t] = 0.f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) { f_n[t * 3 + a] = z[a]; f_t[t * 3 + a] = z[a]; }
+            }
+            pen[u] = __ballot_sync(0xffffffffu, in_contact);
+        }
+        __syncwarp();   // the chunk stores above come before pass 2's stores to the same words
+        // pass 2: the penetrating taxels of this round, compacted over the lanes (slot-major,
+        // lane-minor, so the work is deterministic): the 27-node window gives the gradient
+        // and the same phi, then the force law
+        int first[NP];   // index of slot u's first job
+        int n_pen = 0;
+#pragma unroll
+        for (int u = 0; u < NP; ++u) {
+            first[u] = n_pen;
+            n_pen += __popc(pen[u]);
+        }
+        for (int j0 = 0; j0 < n_pen; j0 += 32) {
+            const int j = j0 + lane;
+            float c6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // this lane's job: its wrench terms
+            if (j < n_pen) {
+                int u = 0, rank = j;
+#pragma unroll
+                for (int v = 0; v + 1 < NP; ++v)
+                    if (u == v && rank >= __popc(pen[v])) { rank -= __popc(pen[v]); u = v + 1; }
+                unsigned mk = pen[0];
+#pragma unroll
+                for (int v = 1; v < NP; ++v) mk = (u == v) ? pen[v] : mk;
+                const int t = round + 32 * u + nth_set_bit(mk, rank);
+                float q3[3];
+                q3[0] = __ldg(taxels + 3 * t);
+                q3[1] = __ldg(taxels + 3 * t + 1);
+                q3[2] = __ldg(taxels + 3 * t + 2);
+                // the posed point, with the same operations as pass 1, and its relative velocity
+                const float xo = fmaf(r[0], q3[0], fmaf(r[1], q3[1], fmaf(r[2], q3[2], Pz.t[0])));
+                const float yo = fmaf(r[3], q3[0], fmaf(r[4], q3[1], fmaf(r[5], q3[2], Pz.t[1])));
+                const float zo = fmaf(r[6], q3[0], fmaf(r[7], q3[1], fmaf(r[8], q3[2], Pz.t[2])));
+                const GridPos g3 = grid_pos(S, xo, yo, zo);
+                const float vx = Pz.v[0] + (Pz.w[1] * zo - Pz.w[2] * yo);
+                const float vy = Pz.v[1] + (Pz.w[2] * xo - Pz.w[0] * zo);
+                const float vz = Pz.v[2] + (Pz.w[0] * yo - Pz.w[1] * xo);
                 Stencil q;
                 q.inside = true;
                 int bx, by, bz;
-                axis_weights(gp[u].ux, S.n0, bx, q.cx, q.dx);
-                axis_weights(gp[u].uy, S.n1, by, q.cy, q.dy);
-                axis_weights(gp[u].uz, S.n2, bz, q.cz, q.dz);
+                axis_weights(g3.ux, S.n0, bx, q.cx, q.dx);
+                axis_weights(g3.uy, S.n1, by, q.cy, q.dy);
+                axis_weights(g3.uz, S.n2, bz, q.cz, q.dz);
                 q.base = S.data + (static_cast<int64_t>(bz) * n01 + static_cast<int64_t>(by) * n0 + bx);
                 float v[3][3][3];
                 stencil_load(q, n0, n01, pol, v);
+                float phi, g[3];
                 stencil_fold(q, v, S.inv_h, phi, g);
-            }
-            float dep, fn[3], ft[3];
-            contact_force(r, phi, g, vel[0], vel[1], vel[2], kn, kd, kt, mu, dep, fn, ft);
-            depth[t] = dep;
+                float dep, fn[3], ft[3];
+                contact_force(r, phi, g, vx, vy, vz, kn, kd, kt, mu, dep, fn, ft);
+                depth[t] = dep;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) { f_n[t * 3 + a] = fn[a]; f_t[t * 3 + a] = ft[a]; }
-            const float fx = fn[0] + ft[0], fy = fn[1] + ft[1], fz = fn[2] + ft[2];
-            acc[0] += fx; acc[1] += fy; acc[2] += fz;
-            acc[3] += p[u][1] * fz - p[u][2] * fy;
-            acc[4] += p[u][2] * fx - p[u][0] * fz;
-            acc[5] += p[u][0] * fy - p[u][1] * fx;
+                for (int a = 0; a < 3; ++a) { f_n[t * 3 + a] = fn[a]; f_t[t * 3 + a] = ft[a]; }
+                const float fx = fn[0] + ft[0], fy = fn[1] + ft[1], fz = fn[2] + ft[2];
+                c6[0] = fx; c6[1] = fy; c6[2] = fz;
+                c6[3] = q3[1] * fz - q3[2] * fy;
+                c6[4] = q3[2] * fx - q3[0] * fz;
+                c6[5] = q3[0] * fy - q3[1] * fx;
+            }
+            // Each taxel's terms go back to the lane that owns it (taxel index mod 32), which
+            // adds them in increasing taxel order: the wrench's summation order does not
+            // depend on NP or on how the jobs were dealt.
+#pragma unroll
+            for (int u = 0; u < NP; ++u) {
+                const int job = first[u] + __popc(pen[u] & ((1u << lane) - 1u));
+                const bool here = ((pen[u] >> lane) & 1u) && job >= j0 && job < j0 + 32;
+                const int from = here ? job - j0 : lane;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const float x = __shfl_sync(0xffffffffu, c6[k], from);
+                    if (here) acc[k] += x;
+                }
+            }
         }
     }
     if (wrench != nullptr) {
