@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--serve-templates", type=int, default=16)
     ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-serve-poses", action="store_true")
     ap.add_argument("--only-serve", action="store_true",
                     help="run only the serving section and print it as the JSON line")
     ap.add_argument("--grad-envs", type=int, default=1024)
@@ -1355,6 +1356,8 @@ def run_serve(args, rank, world, local_rank, dist):
     st = srv.stats()
     srv.close()
     assert tacsl.check_errors() == 0
+    poses = None if args.no_serve_poses else run_serve_poses(args, w, sdfs, sensors, taxels, tpl, n_taxel, max_pads,
+                                                               budget, g, order)
     mean_env = float(np.mean([t["n_env"] for t in w.templates]))
     return {
         "workload": SERVE_WORKLOAD, "templates": len(tpl), "requests_per_run": int(len(order)),
@@ -1369,7 +1372,137 @@ def run_serve(args, rank, world, local_rank, dist):
                    "arena_peak_bytes": st["arena_peak_bytes"]},
         "poisson": streams,
         "latency": "from submission (arrival) to all outputs in pinned host memory",
+        "poses": poses,
     }
+
+
+def run_serve_poses(args, w, sdfs, sensors, taxels, tpl, n_taxel, max_pads, budget, g, order):
+    """The same request stream as pose requests: each request carries its pads' poses,
+    twists and contact parameters only, and the server renders the depth maps on the
+    device (tacsl_batch_render), shades them and computes the force field.  Two variants:
+    'forces' returns the wrench and force fields (no image is asked for, so none is
+    rendered); 'images' returns the wrench, force fields and RGB images.  Plain: one
+    request at a time through the batch entry points (plan, upload, render + step or the
+    force field alone, copies out, synchronise).  Poisson arrivals at 80 % of the plain
+    path's saturation rate."""
+    import threading
+
+    import torch
+
+    import paper_2408_06506_b300 as tacsl
+    from paper_2408_06506_b300 import batch as tb
+    from paper_2408_06506_b300 import serve as sv
+    from paper_2408_06506_b300 import synth
+
+    cams = []
+    for co, px, py in w.models:
+        H, W = co.shape[2], co.shape[3]
+        cams.append(tacsl.Camera(H, W, px, py, -px * W / 2 + 0.5 * px, -py * H / 2 + 0.5 * py, synth.D0, 3e-3))
+    keys = ("obj_id", "layout", "sensor", "pad_pose", "pad_twist", "k_n", "k_d", "k_t", "mu")
+    res = {"cameras": "orthographic per sensor model, centred on the pad, d0 = 20 mm, z_max = 3 mm"}
+    for variant, want in (("forces", ("wrench", "f_n", "f_t")), ("images", ("wrench", "f_n", "f_t", "rgb"))):
+        plain_out = {}
+
+        def plain_serve(i):
+            t = tpl[i]
+            plan = tb.BatchPlan(t["obj_id"].numpy(), t["layout"].numpy(), t["sensor"].numpy(), w.layout_first,
+                                w.layout_count, sensors, n_points=w.taxels.shape[0])
+            d = {k: t[k].cuda(non_blocking=True) for k in ("pad_pose", "pad_twist", "k_n", "k_d", "k_t", "mu")}
+            params = tacsl.ContactParams(d["k_n"], d["k_d"], d["k_t"], d["mu"])
+            if "rgb" in want:
+                maps = plan.render(sdfs, cams, d["pad_pose"])
+                o = plan.step(sdfs, params, taxels, d["pad_pose"], d["pad_twist"], maps)
+            else:
+                o = plan.forces(sdfs, params, taxels, d["pad_pose"], d["pad_twist"])
+            if i not in plain_out:
+                plain_out[i] = {k: torch.empty(o[k].shape, dtype=o[k].dtype).pin_memory() for k in want}
+            for k, v in plain_out[i].items():
+                v.copy_(o[k], non_blocking=True)
+            torch.cuda.synchronize()
+
+        for i in range(len(tpl)):
+            plain_serve(i)
+        assert tacsl.check_errors() == 0
+        svc = []
+        for i in range(len(tpl)):
+            t0 = time.perf_counter()
+            plain_serve(i)
+            svc.append(time.perf_counter() - t0)
+        svc = np.array(svc)
+        plain_rate = len(tpl) / svc.sum()
+        plain_sat = sum(n_taxel) / svc.sum()
+
+        srv = sv.Server(sdfs, sensors, taxels, w.layout_first, w.layout_count, hbm_budget_bytes=budget,
+                        max_pads=max_pads, n_streams=args.serve_streams, batch_timeout_ms=60000)
+        srv.set_cameras(cams)
+        outs = [srv.pose_outputs_for(t["layout"].numpy(), t["sensor"].numpy(), want=want) for t in tpl]
+
+        def submit(i):
+            return srv.submit_poses(out=outs[i], **{k: tpl[i][k] for k in keys})
+
+        for i in range(len(tpl)):                       # warm-up, and a check against plain
+            st_, _ = srv.wait(submit(i))
+            assert st_ == 0
+            for k in want:
+                n = plain_out[i][k].shape[0]
+                assert torch.equal(outs[i][k][:n], plain_out[i][k]), (variant, k)
+        t0 = time.perf_counter()
+        ids = [submit(int(i)) for i in order]
+        for rid in ids:
+            srv.wait(rid)
+        sat_s = time.perf_counter() - t0
+        srv_sat = sum(n_taxel[int(i)] for i in order) / sat_s
+        out_bytes = [sum(v.numel() * v.element_size() for v in o.values() if v is not None) for o in outs]
+        in_bytes = [sum(t[k].numel() * t[k].element_size() for k in keys) for t in tpl]
+
+        def run_stream(rate, mode):
+            gaps = g.exponential(1.0 / rate, size=len(order))
+            arrive = np.cumsum(gaps) - gaps[0]
+            lat = np.zeros(len(order))
+            start = time.perf_counter()
+            if mode == "server":
+                rids = [None] * len(order)
+
+                def producer():
+                    for k, i in enumerate(order):
+                        dt = start + arrive[k] - time.perf_counter()
+                        if dt > 0:
+                            time.sleep(dt)
+                        rids[k] = submit(int(i))
+                th = threading.Thread(target=producer)
+                th.start()
+                th.join()
+                for k in range(len(order)):
+                    lat[k] = srv.wait(rids[k])[1]
+            else:
+                for k, i in enumerate(order):
+                    dt = start + arrive[k] - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    plain_serve(int(i))
+                    lat[k] = 1e3 * (time.perf_counter() - (start + arrive[k]))
+            span = time.perf_counter() - start
+            return {"rate_req_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                    "throughput": sum(n_taxel[int(i)] for i in order) / span}
+
+        rate = 0.8 * plain_rate
+        st = srv.stats()
+        res[variant] = {
+            "returned": list(want),
+            "mean_bytes_in_per_request": float(np.mean([in_bytes[int(i)] for i in order])),
+            "mean_bytes_out_per_request": float(np.mean([out_bytes[int(i)] for i in order])),
+            "plain": {"saturation": plain_sat, "saturation_req_per_s": plain_rate,
+                      "path": "per request: plan/upload, copies in, " +
+                              ("tacsl_batch_render + tacsl_batch_step" if "rgb" in want else "tacsl_batch_forces") +
+                              ", copies out, synchronise"},
+            "server": {"saturation": srv_sat, "saturation_speedup": srv_sat / plain_sat,
+                       "max_batch_requests": st["max_batch_requests"]},
+            "poisson_80%": {"server": run_stream(rate, "server"), "plain": run_stream(rate, "plain")},
+        }
+        srv.close()
+        assert tacsl.check_errors() == 0
+    return res
 
 
 def _smi_id(ordinal):

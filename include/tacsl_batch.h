@@ -172,6 +172,17 @@ int tacsl_batch_forces_static(const tacsl_batch_desc* desc, const tacsl_sdf_set*
 int tacsl_batch_shade(const tacsl_batch_plan* plan, const void* workspace, const tacsl_sensor_set* sensors,
                       const tacsl_batch_io* io, tacsl_stream_t stream);
 
+/* The depth map of every pad that has an image, rendered from its pose (Sec. III-B: the
+ * camera inside the sensor sees the depth of the indenting object; per image exactly
+ * tacsl_render_depth with that model's camera), into depth_map [n_pixel_out] (device,
+ * 16-byte aligned; the packed layout the image kernel reads).  cameras: host array of
+ * n_model cameras, camera m with the H and W of sensor model m (only models that have
+ * images are read).  pad_pose [n_pad][7] device.  A pad whose obj_id is >= set->n_sdf
+ * gets a NaN map and TACSL_DEVERR_BAD_OBJ_ID.  One launch per model with images. */
+int tacsl_batch_render(const tacsl_batch_plan* plan, const void* workspace, const tacsl_sdf_set* set,
+                       const tacsl_camera* cameras, const float* pad_pose, float* depth_map,
+                       tacsl_stream_t stream);
+
 /* Both: the image kernel, then the force-field kernel, on stream. */
 int tacsl_batch_step(const tacsl_batch_plan* plan, void* workspace, const tacsl_sdf_set* set,
                      const tacsl_contact_params* params, const tacsl_sensor_set* sensors,

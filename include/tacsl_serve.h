@@ -57,6 +57,30 @@ typedef struct {
     uint8_t* rgb;
 } tacsl_request;
 
+/* A request that carries poses only (the RL loop's per-step inputs): the server renders
+ * each image's depth map on the device from the pad's pose with the camera of its sensor
+ * model (tacsl_batch_render; cameras set with tacsl_server_set_cameras), then shades it
+ * and computes the force field.  Every output pointer may be NULL: only the outputs the
+ * caller asks for travel back.  Host arrays; n_pad entries unless stated. */
+typedef struct {
+    int32_t n_pad;
+    const int32_t* obj_id;   /* object of each pad (index into the server's SDF set) */
+    const int32_t* layout;   /* taxel layout of each pad */
+    const int32_t* sensor;   /* sensor model of each pad's image, or -1 */
+    const float* pad_pose;   /* [n_pad][7] */
+    const float* pad_twist;  /* [n_pad][6] */
+    const float* k_n;        /* [n_pad] contact parameters per pad */
+    const float* k_d;
+    const float* k_t;
+    const float* mu;
+    float* wrench;           /* [n_pad][6], or NULL */
+    float* depth;            /* taxel outputs laid out as a batch of this request alone, or NULL */
+    float* f_n;
+    float* f_t;
+    uint8_t* rgb;            /* packed RGB of the pads with an image, pad order, or NULL */
+    float* depth_map;        /* the rendered depth maps, same packing, or NULL */
+} tacsl_pose_request;
+
 typedef struct {
     int64_t submitted, completed, batches, pads_served;
     int64_t arena_bytes, arena_peak_bytes, arena_used_bytes;
@@ -90,6 +114,18 @@ int tacsl_server_submit(tacsl_server_t server, const tacsl_request* request, int
  * batch ends: keep them valid until tacsl_server_destroy returns. */
 int tacsl_server_wait(tacsl_server_t server, int64_t request_id, int32_t timeout_ms, int32_t* status,
                       double* latency_ms);
+
+/* The tactile camera of each sensor model, for pose requests: n_camera must equal the
+ * number of sensor models given at creation and camera m must have model m's H and W.
+ * May be called again to change them; requests already submitted use the cameras set
+ * when their batch is formed. */
+int tacsl_server_set_cameras(tacsl_server_t server, const tacsl_camera* cameras, int32_t n_camera);
+
+/* Queue a pose request (checks as tacsl_server_submit; a request with images needs the
+ * cameras).  A batch holds requests of one kind: pose requests, or requests that bring
+ * their depth maps; the worker takes the oldest pending requests of the kind of the
+ * oldest one.  A pad's result depends only on that pad, as for tacsl_server_submit. */
+int tacsl_server_submit_poses(tacsl_server_t server, const tacsl_pose_request* request, int64_t* request_id);
 
 int tacsl_server_get_stats(tacsl_server_t server, tacsl_server_stats* stats);
 

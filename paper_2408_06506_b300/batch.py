@@ -13,7 +13,7 @@ import ctypes as C
 import numpy as np
 import torch
 
-from . import _Params, _SdfSet, _check, _dev, _ptr, _stream, load
+from . import _Camera, _Params, _SdfSet, _check, _dev, _ptr, _stream, load
 
 MAX_MODEL = 64
 
@@ -63,6 +63,7 @@ def _lib():
             "tacsl_batch_forces": [PP, _P, PSdf, PPrm, PI, _P],
             "tacsl_batch_shade": [PP, _P, PS, PI, _P],
             "tacsl_batch_step": [PP, _P, PSdf, PPrm, PS, PI, _P],
+            "tacsl_batch_render": [PP, _P, PSdf, C.POINTER(_Camera), _P, _P, _P],
             "tacsl_batch_autotune": [PP, _P, PSdf, PPrm, PS, PI, _I32, C.POINTER(C.c_double), _P],
             "tacsl_batch_graph_create": [PP, _P, PSdf, PPrm, PS, PI, C.POINTER(_P)],
             "tacsl_graph_launch": [_P, _P],
@@ -74,6 +75,16 @@ def _lib():
             f.argtypes = args
         _bound = True
     return lib
+
+
+def cameras_array(cameras):
+    """A ctypes array of tacsl_camera from a list of tacsl.Camera (None for an empty list)."""
+    if not cameras:
+        return None
+    arr = (_Camera * len(cameras))()
+    for m, c in enumerate(cameras):
+        arr[m] = c.c
+    return arr
 
 
 class SensorSet:
@@ -210,6 +221,17 @@ class BatchPlan:
         _check(_lib().tacsl_batch_shade(C.byref(self.plan), _ptr(self.workspace), C.byref(self.sensors.c),
                                         C.byref(io), _stream(stream)))
         return rgb
+
+    def render(self, sdfs, cameras, pose, depth_map=None, stream=None):
+        """Packed depth maps [n_pixel_out] of every pad with an image, rendered from its pose
+        (cameras: one tacsl.Camera per sensor model of the plan)."""
+        _dev(pose, torch.float32, "pad_pose")
+        if depth_map is None:
+            depth_map = torch.empty(max(self.plan.n_pixel_out, 4), dtype=torch.float32, device=pose.device)
+        cams = cameras_array(cameras)
+        _check(_lib().tacsl_batch_render(C.byref(self.plan), _ptr(self.workspace), C.byref(sdfs.c), cams,
+                                         _ptr(pose), _ptr(depth_map), _stream(stream)))
+        return depth_map
 
     def step(self, sdfs, params, taxels, pose, twist, depth_map, out=None, stream=None) -> dict:
         out = out or self.outputs(pose.device)

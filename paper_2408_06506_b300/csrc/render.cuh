@@ -102,9 +102,9 @@ struct __align__(16) RenderFrame {
 };
 constexpr int kRenderFrames = 256;   // frames a block keeps in shared memory at a time
 
-__device__ __forceinline__ void render_frame(const SdfTable& tab, const int32_t* obj_id, const float* pad_pose,
-                                             int64_t b, int P, const CameraArgs& cam, RenderFrame& f) {
-    const int id = __ldg(obj_id + static_cast<int>(b / P));
+// Frame of the image of pad b (pose row b) against object id.
+__device__ __forceinline__ void render_frame(const SdfTable& tab, int id, const float* pad_pose, int64_t b,
+                                             const CameraArgs& cam, RenderFrame& f) {
     if (id < 0 || id >= tab.count) {
         f.id = -1;
         return;
@@ -133,10 +133,14 @@ __device__ __forceinline__ void render_frame(const SdfTable& tab, const int32_t*
 // column: the part of [-z_max, 0] inside the grid's domain (slab test on the affine
 // u(z)); outside it the SDF is undefined and no point counts as inside the object, so
 // the march runs over that part alone, 3 FMAs per sample.
+// Image b is pad b of E x P pads (object obj_id[b / P], pixels at b * H * W) when img_po
+// is NULL; otherwise the entry img_po[b] = (pad, object) of an image list, with its first
+// pixel at img_px[b] (the batched render over one camera model).
 __global__ void __launch_bounds__(256) render_kernel(const SdfTable tab, int64_t B, int P,
                                                      const int32_t* __restrict__ obj_id,
                                                      const float* __restrict__ pad_pose, const CameraArgs cam,
-                                                     float* __restrict__ depth) {
+                                                     float* __restrict__ depth, const int2* __restrict__ img_po,
+                                                     const int64_t* __restrict__ img_px) {
     __shared__ RenderFrame frames[kRenderFrames];
     const int tiles_x = (cam.W + 31) / 32;
     const int tile_y = static_cast<int>(blockIdx.x) / tiles_x, tile_x = static_cast<int>(blockIdx.x) - tile_y * tiles_x;
@@ -150,14 +154,20 @@ __global__ void __launch_bounds__(256) render_kernel(const SdfTable tab, int64_t
     for (int64_t base = 0; base < n_img; base += kRenderFrames) {
         const int n_here = static_cast<int>(n_img - base < kRenderFrames ? n_img - base : kRenderFrames);
         __syncthreads();       // the previous frames are no longer read
-        if (static_cast<int>(threadIdx.x) < n_here)
-            render_frame(tab, obj_id, pad_pose, static_cast<int64_t>(blockIdx.y) + (base + threadIdx.x) * gridDim.y,
-                         P, cam, frames[threadIdx.x]);
+        if (static_cast<int>(threadIdx.x) < n_here) {
+            const int64_t b = static_cast<int64_t>(blockIdx.y) + (base + threadIdx.x) * gridDim.y;
+            if (img_po == nullptr) {
+                render_frame(tab, __ldg(obj_id + static_cast<int>(b / P)), pad_pose, b, cam, frames[threadIdx.x]);
+            } else {
+                const int2 po = __ldg(img_po + b);
+                render_frame(tab, po.y, pad_pose, po.x, cam, frames[threadIdx.x]);
+            }
+        }
         __syncthreads();
         if (!live) continue;
         for (int m = 0; m < n_here; ++m) {
             const int64_t b = static_cast<int64_t>(blockIdx.y) + (base + m) * gridDim.y;
-            const int64_t k = b * HW + pix;
+            const int64_t k = (img_px == nullptr ? b * HW : __ldg(img_px + b)) + pix;
             const RenderFrame& F = frames[m];
             if (F.id < 0) {
                 depth[k] = __int_as_float(0x7fc00000);

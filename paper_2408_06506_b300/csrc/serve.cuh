@@ -10,9 +10,10 @@
 //      running after batch_timeout_ms fails its requests with TACSL_ERR_TIMEOUT but keeps
 //      its block until the GPU is done with it;
 //   2. while a stream is free and requests wait, forms a batch of the oldest pending
-//      requests whose memory fits in the largest free arena block (and within max_pads),
-//      then - outside the lock - plans and packs it, copies every request's inputs into
-//      the batch's arrays, launches the image and force kernels, copies every request's
+//      requests of one kind whose memory fits in the largest free arena block (and
+//      within max_pads), then - outside the lock - plans and packs it, copies every
+//      request's inputs into the batch's arrays, renders the depth maps of a batch of
+//      pose requests, launches the image and force kernels, copies every request's
 //      outputs back to its host buffers and records an event, all on that stream;
 //   3. sleeps until a request arrives or, while batches run, for a few microseconds.
 // Each batch's arrays are one contiguous arena block: per request the pads, taxels
@@ -93,6 +94,8 @@ class Arena {
 struct Req {
     int64_t id = 0;
     tacsl_request r{};
+    bool render = false;          // a pose request: depth maps rendered on the device
+    float* depth_map_out = nullptr;   // a pose request's rendered maps, if asked for
     std::vector<int32_t> obj, layout, sensor;
     int64_t n_taxel = 0, n_pixel = 0, n_image = 0, bytes = 0;
     Clock::time_point t_submit, t_done;
@@ -102,14 +105,16 @@ struct Req {
 
 // Bytes a request adds to a batch: inputs (pose 28, twist 24, parameters 16 per pad;
 // depth 4 per pixel), outputs (28 per taxel, wrench 24 per pad, rgb 3 per pixel) and its
-// workspace share (32 per pad, 8 per image).
+// workspace share (32 per pad; 16 per image: its first pixel, pad and object).
 int64_t request_bytes(int64_t n_pad, int64_t n_taxel, int64_t n_pixel, int64_t n_image) {
-    return n_pad * (28 + 24 + 16 + 24 + 32) + n_taxel * 28 + n_pixel * 7 + n_image * 8;
+    return n_pad * (28 + 24 + 16 + 24 + 32) + n_taxel * 28 + n_pixel * 7 + n_image * 16;
 }
 constexpr int64_t kBatchSlack = 16 * kGranule + 512;   // per-array alignment and the workspace header
 
 struct Batch {
     std::vector<std::shared_ptr<Req>> reqs;
+    bool render = false;               // pose requests: depth maps rendered on the device
+    std::vector<CameraArgs> cams;      // the cameras when the batch was formed
     int stream = 0;
     int64_t off = -1, bytes = 0;
     Clock::time_point t_launch;
@@ -167,17 +172,61 @@ class Server {
         return ok();
     }
 
+    int set_cameras(const tacsl_camera* cams, int32_t n) {
+        if (cams == nullptr) return fail(TACSL_ERR_INVALID_ARG, "cameras is NULL");
+        if (n != static_cast<int32_t>(models_.size()))
+            return fail(TACSL_ERR_INVALID_ARG, "%d cameras for %d sensor models", n, (int)models_.size());
+        std::vector<CameraArgs> c(n);
+        for (int m = 0; m < n; ++m) {
+            const int rc = check_camera(&cams[m], c[m]);
+            if (rc) return rc;
+            if (c[m].H != models_[m].H || c[m].W != models_[m].W)
+                return fail(TACSL_ERR_INVALID_ARG, "camera %d is %d x %d, sensor model %d is %d x %d", m, c[m].H, c[m].W,
+                            m, models_[m].H, models_[m].W);
+        }
+        std::lock_guard<std::mutex> lk(mu_);
+        cams_ = c;
+        return ok();
+    }
+
+    int submit_poses(const tacsl_pose_request* q, int64_t* id) {
+        if (q == nullptr || id == nullptr) return fail(TACSL_ERR_INVALID_ARG, "request or id is NULL");
+        tacsl_request r{};
+        r.n_pad = q->n_pad;
+        r.obj_id = q->obj_id;
+        r.layout = q->layout;
+        r.sensor = q->sensor;
+        r.pad_pose = q->pad_pose;
+        r.pad_twist = q->pad_twist;
+        r.k_n = q->k_n;
+        r.k_d = q->k_d;
+        r.k_t = q->k_t;
+        r.mu = q->mu;
+        r.depth = q->depth;
+        r.f_n = q->f_n;
+        r.f_t = q->f_t;
+        r.wrench = q->wrench;
+        r.rgb = q->rgb;
+        return submit_any(&r, true, q->depth_map, id);
+    }
+
     int submit(const tacsl_request* q, int64_t* id) {
         if (q == nullptr || id == nullptr) return fail(TACSL_ERR_INVALID_ARG, "request or id is NULL");
+        return submit_any(q, false, nullptr, id);
+    }
+
+    int submit_any(const tacsl_request* q, bool render, float* depth_map_out, int64_t* id) {
         const int n = q->n_pad;
         if (n < 1) return fail(TACSL_ERR_INVALID_ARG, "a request needs at least one pad");
         if (n > cfg_.max_pads) return fail(TACSL_ERR_UNSUPPORTED, "request of %d pads > max_pads %d", n, cfg_.max_pads);
         if (q->obj_id == nullptr || q->layout == nullptr || q->sensor == nullptr || q->pad_pose == nullptr ||
             q->pad_twist == nullptr || q->k_n == nullptr || q->k_d == nullptr || q->k_t == nullptr ||
-            q->mu == nullptr || q->depth == nullptr || q->f_n == nullptr || q->f_t == nullptr)
+            q->mu == nullptr || (!render && (q->depth == nullptr || q->f_n == nullptr || q->f_t == nullptr)))
             return fail(TACSL_ERR_INVALID_ARG, "a required request array is NULL");
         auto r = std::make_shared<Req>();
         r->r = *q;
+        r->render = render;
+        r->depth_map_out = depth_map_out;
         r->obj.assign(q->obj_id, q->obj_id + n);
         r->layout.assign(q->layout, q->layout + n);
         r->sensor.assign(q->sensor, q->sensor + n);
@@ -194,8 +243,12 @@ class Server {
                 ++r->n_image;
             }
         }
-        if (r->n_image > 0 && (q->depth_map == nullptr || q->rgb == nullptr))
+        if (!render && r->n_image > 0 && (q->depth_map == nullptr || q->rgb == nullptr))
             return fail(TACSL_ERR_INVALID_ARG, "a request with images needs depth_map and rgb");
+        if (render && r->n_image > 0) {
+            std::lock_guard<std::mutex> lk(mu_);
+            if (cams_.empty()) return fail(TACSL_ERR_INVALID_ARG, "a pose request with images needs the cameras set");
+        }
         r->bytes = request_bytes(n, r->n_taxel, r->n_pixel, r->n_image);
         if (r->bytes + kBatchSlack > cfg_.hbm_budget_bytes)
             return fail(TACSL_ERR_UNSUPPORTED, "request needs %lld bytes, the budget is %lld", (long long)r->bytes,
@@ -278,8 +331,12 @@ class Server {
     bool take_batch(Batch& bt) {
         const int64_t room = arena_.largest_free();
         int64_t bytes = kBatchSlack, pads = 0;
+        const bool render = pending_.empty() ? false : pending_.front()->render;
+        bt.render = render;
+        bt.cams = cams_;
         while (!pending_.empty()) {
             const auto& r = pending_.front();
+            if (r->render != render) break;   // a batch holds requests of one kind
             if (pads + r->r.n_pad > cfg_.max_pads || bytes + r->bytes > room) break;
             bytes += r->bytes;
             pads += r->r.n_pad;
@@ -342,7 +399,7 @@ class Server {
             if (e == cudaSuccess) e = copy(pose + 7 * p0, r->r.pad_pose, 28 * np, cudaMemcpyHostToDevice);
             if (e == cudaSuccess) e = copy(twist + 6 * p0, r->r.pad_twist, 24 * np, cudaMemcpyHostToDevice);
             for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = copy(prm[k] + p0, src[k], 4 * np, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess && r->n_pixel > 0)
+            if (e == cudaSuccess && r->n_pixel > 0 && !bt.render)
                 e = copy(dmap + q0, r->r.depth_map, 4 * r->n_pixel, cudaMemcpyHostToDevice);
             p0 += np;
             t0 += r->n_taxel;
@@ -354,17 +411,31 @@ class Server {
         c.tab = tab_;
         c.prm = Params4{prm[0], prm[1], prm[2], prm[3], n};
         c.dev = dev_;
-        if (plan.n_image > 0 && (rc = launch_batch_shade(&plan, ws, &ss, &io, *dev_, 0, 0, st))) return rc;
+        // a batch of pose requests renders its depth maps, and renders and shades only
+        // if some request asks for the maps or the images
+        bool want_rgb = !bt.render, want_map = false;
+        for (auto& r : bt.reqs)
+            if (r->n_pixel > 0) {
+                want_rgb = want_rgb || r->r.rgb != nullptr;
+                want_map = want_map || r->depth_map_out != nullptr;
+            }
+        if (bt.render && plan.n_image > 0 && (want_rgb || want_map) &&
+            (rc = launch_batch_render(&plan, ws, tab_, bt.cams.data(), pose, dmap, st)))
+            return rc;
+        if (plan.n_image > 0 && want_rgb && (rc = launch_batch_shade(&plan, ws, &ss, &io, *dev_, 0, 0, st))) return rc;
         if ((rc = launch_batch_forces(&plan, ws, c.tab, c.prm, &io, *dev_, 4, true, st))) return rc;
         p0 = t0 = q0 = 0;
         for (auto& r : bt.reqs) {
             const int64_t np = r->r.n_pad;
-            if (e == cudaSuccess) e = copy(r->r.depth, depth + t0, 4 * r->n_taxel, cudaMemcpyDeviceToHost);
-            if (e == cudaSuccess) e = copy(r->r.f_n, fn + 3 * t0, 12 * r->n_taxel, cudaMemcpyDeviceToHost);
-            if (e == cudaSuccess) e = copy(r->r.f_t, ft + 3 * t0, 12 * r->n_taxel, cudaMemcpyDeviceToHost);
+            // (a pose request's outputs are optional: only those asked for travel back)
+            if (e == cudaSuccess && r->r.depth) e = copy(r->r.depth, depth + t0, 4 * r->n_taxel, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && r->r.f_n) e = copy(r->r.f_n, fn + 3 * t0, 12 * r->n_taxel, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && r->r.f_t) e = copy(r->r.f_t, ft + 3 * t0, 12 * r->n_taxel, cudaMemcpyDeviceToHost);
             if (e == cudaSuccess && r->r.wrench) e = copy(r->r.wrench, wrench + 6 * p0, 24 * np, cudaMemcpyDeviceToHost);
-            if (e == cudaSuccess && r->n_pixel > 0)
+            if (e == cudaSuccess && r->n_pixel > 0 && r->r.rgb)
                 e = copy(r->r.rgb, rgb + 3 * q0, 3 * r->n_pixel, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && r->n_pixel > 0 && r->depth_map_out)
+                e = copy(r->depth_map_out, dmap + q0, 4 * r->n_pixel, cudaMemcpyDeviceToHost);
             p0 += np;
             t0 += r->n_taxel;
             q0 += r->n_pixel;
@@ -438,6 +509,7 @@ class Server {
     tacsl_server_config cfg_{};
     SdfTable tab_{};
     std::vector<tacsl_sensor_model> models_;
+    std::vector<CameraArgs> cams_;   // per sensor model, for pose requests (under mu_)
     std::vector<int64_t> layout_first_;
     std::vector<int32_t> layout_count_;
     const float* taxels_ = nullptr;
@@ -495,6 +567,16 @@ int tacsl_server_wait(tacsl_server_t server, int64_t request_id, int32_t timeout
                       double* latency_ms) {
     if (server == nullptr) return fail(TACSL_ERR_INVALID_ARG, "server is NULL");
     return reinterpret_cast<tacsl::serve::Server*>(server)->wait(request_id, timeout_ms, status, latency_ms);
+}
+
+int tacsl_server_set_cameras(tacsl_server_t server, const tacsl_camera* cameras, int32_t n_camera) {
+    if (server == nullptr) return fail(TACSL_ERR_INVALID_ARG, "server is NULL");
+    return reinterpret_cast<tacsl::serve::Server*>(server)->set_cameras(cameras, n_camera);
+}
+
+int tacsl_server_submit_poses(tacsl_server_t server, const tacsl_pose_request* request, int64_t* request_id) {
+    if (server == nullptr) return fail(TACSL_ERR_INVALID_ARG, "server is NULL");
+    return reinterpret_cast<tacsl::serve::Server*>(server)->submit_poses(request, request_id);
 }
 
 int tacsl_server_get_stats(tacsl_server_t server, tacsl_server_stats* stats) {

@@ -322,7 +322,7 @@ int launch_render(const SdfTable& tab, int64_t B, int P, const int32_t* obj_id, 
     if (tiles > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "camera image too large");
     // each block loops over images: about (tiles x 64) blocks in all, whatever the batch
     const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(std::min<int64_t>(B, 64)));
-    render_kernel<<<grid, 256, 0, stream>>>(tab, B, P, obj_id, pad_pose, c, depth_map);
+    render_kernel<<<grid, 256, 0, stream>>>(tab, B, P, obj_id, pad_pose, c, depth_map, nullptr, nullptr);
     return check_launch("render kernel");
 }
 
@@ -556,6 +556,12 @@ uint64_t batch_fingerprint(const tacsl_batch_desc* d, const tacsl_batch_plan& pl
 
 int shade_stage_floats(int max_w) { return kShTile + 2 * max_w; }
 
+// Workspace offset of the per-image (pad, object) list, which follows the list of each
+// image's first pixel (both grouped by model, pad order within a model).
+int64_t image_po_offset(const tacsl_batch_plan& p) {
+    return (p.off_images + (int64_t)sizeof(int64_t) * p.n_image + 255) / 256 * 256;
+}
+
 int batch_plan(const tacsl_batch_desc* d, const tacsl_sensor_set* sensors, tacsl_batch_plan* plan,
                int64_t* taxel_offset, int64_t* pixel_offset) {
     if (d == nullptr || plan == nullptr) return fail(TACSL_ERR_INVALID_ARG, "batch description or plan is NULL");
@@ -624,7 +630,7 @@ int batch_plan(const tacsl_batch_desc* d, const tacsl_sensor_set* sensors, tacsl
     for (int m = 0; m < p.n_model; ++m) p.model_img_begin[m + 1] = p.model_img_begin[m] + (int32_t)per_model[m];
     p.off_sched = kBatchHeader;
     p.off_images = (p.off_sched + (int64_t)sizeof(BatchPad) * p.n_pad + 255) / 256 * 256;
-    p.workspace_bytes = (p.off_images + (int64_t)sizeof(int64_t) * p.n_image + 255) / 256 * 256;
+    p.workspace_bytes = (image_po_offset(p) + (int64_t)sizeof(int2) * p.n_image + 255) / 256 * 256;
     p.fingerprint = batch_fingerprint(d, p);
     *plan = p;
     return ok();
@@ -661,11 +667,17 @@ int batch_pack(const tacsl_batch_plan* plan, const tacsl_batch_desc* d, void* ho
         const int l = d->layout[b];
         sched[i] = BatchPad{b, d->layout_count[l], d->obj_id[b], 0, d->layout_first[l], out[b]};
     }
-    // image list: grouped by model, pad order within a model
+    // image list: grouped by model, pad order within a model; each image's first pixel,
+    // then (in a second array) its pad and object
     int64_t* img = reinterpret_cast<int64_t*>(base + plan->off_images);
+    int2* po = reinterpret_cast<int2*>(base + image_po_offset(*plan));
     std::vector<int32_t> fill(plan->model_img_begin, plan->model_img_begin + plan->n_model);
     for (int b = 0; b < d->n_pad; ++b)
-        if (d->sensor[b] >= 0) img[fill[d->sensor[b]]++] = px[b];
+        if (d->sensor[b] >= 0) {
+            const int i = fill[d->sensor[b]]++;
+            img[i] = px[b];
+            po[i] = make_int2(b, d->obj_id[b]);
+        }
     return ok();
 }
 
@@ -899,10 +911,65 @@ int time_launches(F&& launch, int reps, tacsl_stream_t stream, float* ms) {
     return rc;
 }
 
+// Depth maps of every image of a packed batch: one render launch per camera model, over
+// that model's run of the image list (pad, object, first pixel).
+int launch_batch_render(const tacsl_batch_plan* plan, const void* ws, const SdfTable& tab, const CameraArgs* cams,
+                        const float* pad_pose, float* depth_map, tacsl_stream_t stream) {
+    const unsigned char* w = static_cast<const unsigned char*>(ws);
+    const int64_t* img = reinterpret_cast<const int64_t*>(w + plan->off_images);
+    const int2* po = reinterpret_cast<const int2*>(w + image_po_offset(*plan));
+    for (int m = 0; m < plan->n_model; ++m) {
+        const int b0 = plan->model_img_begin[m], n = plan->model_img_begin[m + 1] - b0;
+        if (n == 0) continue;
+        const CameraArgs& c = cams[m];
+        const int64_t tiles = (int64_t)((c.W + 31) / 32) * ((c.H + 7) / 8);
+        const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(std::min(n, 64)));
+        render_kernel<<<grid, 256, 0, stream>>>(tab, n, 1, nullptr, pad_pose, c, depth_map, po + b0, img + b0);
+        const int rc = check_launch("batched render kernel");
+        if (rc) return rc;
+    }
+    return TACSL_OK;
+}
+
+// Host checks of tacsl_batch_render's arguments; the cameras of the models with images
+// are converted into cams (n_model entries).
+int check_batch_render(const tacsl_batch_plan* plan, const void* ws, const tacsl_camera* cameras,
+                       const float* pad_pose, const float* depth_map, CameraArgs* cams) {
+    if (plan == nullptr) return fail(TACSL_ERR_INVALID_ARG, "plan is NULL");
+    if (ws == nullptr || !aligned(ws, 256)) return fail(TACSL_ERR_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+    if (plan->n_image == 0) return TACSL_OK;
+    if (cameras == nullptr) return fail(TACSL_ERR_INVALID_ARG, "cameras is NULL");
+    for (int m = 0; m < plan->n_model; ++m) {
+        if (plan->model_img_begin[m + 1] == plan->model_img_begin[m]) continue;
+        const int rc = check_camera(&cameras[m], cams[m]);
+        if (rc) return rc;
+        if (cams[m].H != plan->model_h[m] || cams[m].W != plan->model_w[m])
+            return fail(TACSL_ERR_INVALID_ARG, "camera %d is %d x %d, sensor model %d is %d x %d", m, cams[m].H,
+                        cams[m].W, m, plan->model_h[m], plan->model_w[m]);
+    }
+    if (pad_pose == nullptr || !aligned(pad_pose, 4)) return fail(TACSL_ERR_INVALID_ARG, "pad_pose NULL or misaligned");
+    if (depth_map == nullptr || !aligned(depth_map, 16))
+        return fail(TACSL_ERR_INVALID_ARG, "depth_map NULL or not 16-byte aligned");
+    return TACSL_OK;
+}
+
 }  // namespace
 }  // namespace tacsl
 
 extern "C" {
+
+int tacsl_batch_render(const tacsl_batch_plan* plan, const void* workspace, const tacsl_sdf_set* set,
+                       const tacsl_camera* cameras, const float* pad_pose, float* depth_map, tacsl_stream_t stream) {
+    using namespace tacsl;
+    CameraArgs cams[TACSL_MAX_MODEL];
+    int rc = check_batch_render(plan, workspace, cameras, pad_pose, depth_map, cams);
+    if (rc) return rc;
+    SdfTable tab;
+    if ((rc = build_table(set, tab))) return rc;
+    if (plan->n_image == 0) return ok();
+    if ((rc = launch_batch_render(plan, workspace, tab, cams, pad_pose, depth_map, stream))) return rc;
+    return ok();
+}
 
 int tacsl_batch_plan_create(const tacsl_batch_desc* desc, const tacsl_sensor_set* sensors, tacsl_batch_plan* plan,
                             int64_t* taxel_offset, int64_t* pixel_offset) {

@@ -11,8 +11,8 @@ import ctypes as C
 import numpy as np
 import torch
 
-from . import TacslError, _check, _SdfSet, load
-from .batch import MAX_MODEL, SensorSet, _SensorSet   # noqa: F401
+from . import TacslError, _Camera, _check, _SdfSet, load
+from .batch import MAX_MODEL, SensorSet, _SensorSet, cameras_array   # noqa: F401
 
 _P, _I32, _I64 = C.c_void_p, C.c_int32, C.c_int64
 TACSL_ERR_TIMEOUT = 4
@@ -26,6 +26,12 @@ class _Request(C.Structure):
     _fields_ = [("n_pad", _I32)] + [(n, _P) for n in (
         "obj_id", "layout", "sensor", "pad_pose", "pad_twist", "k_n", "k_d", "k_t", "mu", "depth_map", "depth", "f_n",
         "f_t", "wrench", "rgb")]
+
+
+class _PoseRequest(C.Structure):
+    _fields_ = [("n_pad", _I32)] + [(n, _P) for n in (
+        "obj_id", "layout", "sensor", "pad_pose", "pad_twist", "k_n", "k_d", "k_t", "mu", "wrench", "depth", "f_n",
+        "f_t", "rgb", "depth_map")]
 
 
 class _Stats(C.Structure):
@@ -45,6 +51,8 @@ def _lib():
             "tacsl_server_create": [C.POINTER(_Config), C.POINTER(_SdfSet), C.POINTER(_SensorSet), _P, _I64, _I32, _P,
                                     _P, C.POINTER(_P)],
             "tacsl_server_submit": [_P, C.POINTER(_Request), C.POINTER(_I64)],
+            "tacsl_server_set_cameras": [_P, C.POINTER(_Camera), _I32],
+            "tacsl_server_submit_poses": [_P, C.POINTER(_PoseRequest), C.POINTER(_I64)],
             "tacsl_server_wait": [_P, _I64, _I32, C.POINTER(_I32), C.POINTER(C.c_double)],
             "tacsl_server_get_stats": [_P, C.POINTER(_Stats)],
             "tacsl_server_destroy": [_P],
@@ -125,6 +133,45 @@ class Server:
                        h(out["rgb"], torch.uint8) if out.get("rgb") is not None else None)
         rid = C.c_int64()
         _check(_lib().tacsl_server_submit(self._h, C.byref(req), C.byref(rid)))
+        self._live[rid.value] = keep
+        return rid.value
+
+    def set_cameras(self, cameras):
+        """The tactile camera of each sensor model (tacsl.Camera list), for pose requests."""
+        arr = cameras_array(cameras)
+        _check(_lib().tacsl_server_set_cameras(self._h, arr, len(cameras)))
+
+    def pose_outputs_for(self, layout, sensor, want=("wrench", "f_n", "f_t"), pin=True):
+        """Host outputs of a pose request: only the names in `want` (wrench, depth, f_n,
+        f_t, rgb, depth_map); the others are None and do not travel back."""
+        nt, npx = self.sizes_of(layout, sensor)
+        mk = (lambda *s, dtype=torch.float32: torch.empty(*s, dtype=dtype).pin_memory()) if pin else \
+            (lambda *s, dtype=torch.float32: torch.empty(*s, dtype=dtype))
+        shapes = {"wrench": ((len(layout), 6), torch.float32), "depth": ((nt,), torch.float32),
+                  "f_n": ((nt, 3), torch.float32), "f_t": ((nt, 3), torch.float32),
+                  "rgb": ((max(npx, 1), 3), torch.uint8), "depth_map": ((max(npx, 1),), torch.float32)}
+        return {k: (mk(*sh, dtype=dt) if k in want else None) for k, (sh, dt) in shapes.items()}
+
+    def submit_poses(self, obj_id, layout, sensor, pad_pose, pad_twist, k_n, k_d, k_t, mu, out) -> int:
+        """Queue one pose request: the server renders the depth maps of the pads with an
+        image from their poses; out's None entries are not returned."""
+        keep = []
+
+        def h(a, dt):
+            if a is None:
+                return None
+            arr, ptr = _host(a, dt)
+            keep.append(arr)
+            return ptr
+
+        req = _PoseRequest(len(obj_id), h(obj_id, torch.int32), h(layout, torch.int32), h(sensor, torch.int32),
+                           h(pad_pose, torch.float32), h(pad_twist, torch.float32), h(k_n, torch.float32),
+                           h(k_d, torch.float32), h(k_t, torch.float32), h(mu, torch.float32),
+                           h(out.get("wrench"), torch.float32), h(out.get("depth"), torch.float32),
+                           h(out.get("f_n"), torch.float32), h(out.get("f_t"), torch.float32),
+                           h(out.get("rgb"), torch.uint8), h(out.get("depth_map"), torch.float32))
+        rid = C.c_int64()
+        _check(_lib().tacsl_server_submit_poses(self._h, C.byref(req), C.byref(rid)))
         self._live[rid.value] = keep
         return rid.value
 
