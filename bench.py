@@ -154,6 +154,10 @@ def profiled_traffic(name, n_units, algorithmic_bytes_per_unit):
     files = kv.get("source_files", "").split(",")
     if not files[0] or kv.get("source_hash") != _source_hash(files):
         return None
+    if "algorithmic_bytes_per_launch" in kv:   # counters of one launch of exactly this workload
+        if int(kv["algorithmic_bytes_per_launch"]) != int(n_units * algorithmic_bytes_per_unit):
+            return None
+        return int(kv["dram_bytes_per_launch"])
     if int(kv.get("algorithmic_bytes_per_unit", -1)) != int(algorithmic_bytes_per_unit):
         return None
     return int(round(float(kv["dram_bytes_fixed"]) + float(kv["dram_bytes_per_unit"]) * n_units))
@@ -959,7 +963,7 @@ def run_batch(args, rank, world, local_rank, dist):
         "roofline": {"bound": "hbm", "kernel": "tacsl::batch_shade_kernel", "algorithmic_bytes": img_bytes,
                      "achieved": img_bytes / (shade_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": img_bytes / (shade_ms * 1e-3) / 1e9 / peak,
-                     "traffic": profiled_traffic("batch_shade_kernel", img_bytes)},
+                     "traffic": profiled_traffic("batch_shade_kernel", 1, img_bytes)},
         "roofline_force": {"bound": "hbm", "kernel": "tacsl::batch_force_kernel", "algorithmic_bytes": force_bytes,
                            "sdf_sectors_touched": sdf_bytes, "achieved": force_bytes / (forces_ms * 1e-3) / 1e9,
                            "frac": force_bytes / (forces_ms * 1e-3) / 1e9 / peak},
