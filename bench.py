@@ -1169,7 +1169,15 @@ def run_grad(args, rank, world, local_rank, dist):
     k_ms["shade_mse_kernel (depth gradient)"] = timed(lambda: lib.tacsl_shade_mse(
         C.byref(shading.c), E * P, tacsl._ptr(sid), tacsl._ptr(depth_map), tacsl._ptr(tI), None, None, None,
         tacsl._ptr(gdep), None), 5)
-    del gI, gdep
+    # the two-pass depth gradient of the autograd bindings: the loss pass also writes the
+    # pixel slopes; the backward is their transposed difference stencil
+    slopes = torch.empty(E * P, sc.H, sc.W, 2, device="cuda")
+    k_ms["shade_mse_kernel (loss map + coefficient gradient + slopes)"] = timed(lambda: lib.tacsl_shade_mse_slopes(
+        C.byref(shading.c), E * P, tacsl._ptr(sid), tacsl._ptr(depth_map), tacsl._ptr(tI), tacsl._ptr(lmap),
+        tacsl._ptr(gc), tacsl._ptr(slopes), None), 5)
+    k_ms["slopes_to_depth_kernel"] = timed(lambda: lib.tacsl_shade_depth_from_slopes(
+        C.byref(shading.c), E * P, tacsl._ptr(sid), tacsl._ptr(slopes), None, tacsl._ptr(gdep), None), 10)
+    del gI, gdep, slopes
     rendered = tacsl.render_depth(sdfs, cam, obj, pz)
     gD = torch.randn(E, P, sc.H, sc.W, device="cuda")
     k_ms["render_kernel"] = timed(lambda: tacsl.render_depth(sdfs, cam, obj, pz, depth_map=rendered), 10)
@@ -1193,6 +1201,9 @@ def run_grad(args, rank, world, local_rank, dist):
     # the fused loss reads the depth (4 B/px) and the target (12 B/px), the coefficients
     # once, and writes the loss map (and the coefficient gradient) once
     mse_bytes = 16 * npx + coef_bytes + coef_bytes // 18
+    # with the coefficient gradient and the pixel slopes (8 B/px) written as well; the
+    # stencil pass reads the slopes and writes the depth gradient (12 B/px)
+    slopes_fwd_bytes = 24 * npx + 2 * coef_bytes + coef_bytes // 18
     return {
         "workload": GRAD_WORKLOAD, "envs_per_gpu": E, "steps": K,
         "ms_per_step": ms, "unit": "taxel-points/s", "value": world * E * P * T / (ms * 1e-3),
@@ -1205,7 +1216,7 @@ def run_grad(args, rank, world, local_rank, dist):
         "unfused": {"ms_per_step": ms_unfused, "value": world * E * P * T / (ms_unfused * 1e-3),
                     "path": "shade_intensity, then ((I - target)^2).mean() in torch", "gpu_launches_per_step": 4},
         "pose_chain": {"ms_per_step": ms_pose, "value": world * E * P * T / (ms_pose * 1e-3),
-                       "images_per_s": world * E * P / (ms_pose * 1e-3), "gpu_launches_per_step": 7,
+                       "images_per_s": world * E * P / (ms_pose * 1e-3), "gpu_launches_per_step": 6,
                        "unfused_ms_per_step": ms_pose_unfused, "graph_ms_per_step": ms_pose_graph,
                        "path": "force_field + render_depth -> shade_mse (images from the poses), backward to pose, "
                                "twist, contact parameters and coefficients"},
@@ -1221,6 +1232,13 @@ def run_grad(args, rank, world, local_rank, dist):
             "shade_mse_kernel (depth gradient)": {
                 "algorithmic_bytes": mse_bytes + 4 * npx,
                 "frac": (mse_bytes + 4 * npx) / (k_ms["shade_mse_kernel (depth gradient)"] * 1e-3) / 1e9 / peak},
+            "shade_mse_kernel (loss map + coefficient gradient + slopes)": {
+                "algorithmic_bytes": slopes_fwd_bytes,
+                "frac": slopes_fwd_bytes / (k_ms["shade_mse_kernel (loss map + coefficient gradient + slopes)"]
+                                            * 1e-3) / 1e9 / peak},
+            "slopes_to_depth_kernel": {
+                "algorithmic_bytes": 12 * npx,
+                "frac": 12 * npx / (k_ms["slopes_to_depth_kernel"] * 1e-3) / 1e9 / peak},
             "render_adjoint_kernel": {"algorithmic_bytes": radj_bytes, "hit_columns": n_hit,
                                       "frac": radj_bytes / (k_ms["render_adjoint_kernel"] * 1e-3) / 1e9 / peak},
             "peak_gbs": peak},

@@ -70,6 +70,42 @@ int tacsl_shade_mse(const tacsl_shading* shading, int64_t B, const int32_t* sens
                     const float* target, const float* scale, float* loss_map, float* grad_coeffs,
                     float* grad_depth, tacsl_stream_t stream);
 
+/* The depth gradient in two passes (the form the torch.autograd bindings take): the pass
+ * that evaluates the shading anyway (the loss forward, or the coefficient adjoint) also
+ * writes per-pixel slopes, and the backward applies the transposed difference stencil
+ * to them, so that the shading is evaluated once per pixel and image instead of again,
+ * with a halo, in the backward.
+ *
+ * slopes [B][H][W][2] (device, 16-byte aligned, caller-owned; B*H*W*8 bytes): for each
+ * image b with a valid sensor id and pixel (y, x), (dL/dD_x, dL/dD_y) of that pixel's
+ * own term of L, D_x and D_y the depth differences its normal reads (central inside,
+ * one-sided on the border, as in tacsl_shade_image).  Images with a bad sensor_id are
+ * not written.
+ *
+ * tacsl_shade_mse_slopes: tacsl_shade_mse's loss_map and grad_coeffs for scale = 1 (both
+ * may be NULL) and the slopes of L = sum(loss_map).  Same arguments and checks as
+ * tacsl_shade_mse otherwise. */
+int tacsl_shade_mse_slopes(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id,
+                           const float* depth_map, const float* target, float* loss_map,
+                           float* grad_coeffs, float* slopes, tacsl_stream_t stream);
+
+/* tacsl_shade_adjoint's grad_coeffs (may be NULL) and the slopes of L with dL/dI =
+ * g_intensity.  Same arguments and checks as tacsl_shade_adjoint otherwise. */
+int tacsl_shade_adjoint_slopes(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id,
+                               const float* depth_map, const float* g_intensity, float* grad_coeffs,
+                               float* slopes, tacsl_stream_t stream);
+
+/* grad_depth [B][H][W] (device, 8-byte aligned, overwritten) = scale * dL/dD from the
+ * slopes one of the two calls above wrote for the same images and sensor ids:
+ * grad_depth[b][q] = scale * sum over the pixels p whose difference stencils read
+ * D[b][q] of (stencil weight of D[q] at p) * slope(p), the two axes' slots summed in the
+ * order of tacsl_shade_mse's depth gradient.  scale: device float[1], NULL = 1.  Zero for
+ * an image with a bad sensor_id.  Of the shading only H, W, n_sensor and the pitch are
+ * used (its coeffs pointer is checked as for every shading call, not read). */
+int tacsl_shade_depth_from_slopes(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id,
+                                  const float* slopes, const float* scale, float* grad_depth,
+                                  tacsl_stream_t stream);
+
 /* Adjoint of tacsl_render_depth w.r.t. the pad poses (the pose -> depth -> image chain;
  * same set, E, P, obj_id, pad_pose, camera).  depth_map [E*P][H][W] (device, 16-byte
  * aligned) is the render of these poses and g_depth [E*P][H][W] (device) the upstream

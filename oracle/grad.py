@@ -36,7 +36,9 @@ depth maps, whose hit search stops at voxel/65536), and closed forms (d f_n / d 
 depth n; stick and slip derivatives; a half-space whose field is exactly linear, for the
 forces and for the depth maps; d I / d A_k = m_k; the flat-gel derivative of I w.r.t.
 the depth).  The image loss (shade_mse) is pinned by its value from the C oracle's
-intensities and by central differences of that value.
+intensities and by central differences of that value.  The pixel slopes (shade_slopes)
+are pinned by their closed form on a flat gel and by the chain rule: their image under
+the transposed derivative stencils is the (pinned) depth gradient.
 """
 from __future__ import annotations
 
@@ -207,8 +209,11 @@ def _axis_derivative(D, axis, pitch):
 def shade_intensity(coeffs, depth, pitch_x, pitch_y):
     """Clamped intensity [H, W, 3] of one image: coeffs [6, 3, H, W], depth [H, W]
     (float64 tensors, either may require grad)."""
-    dx = _axis_derivative(depth, 1, pitch_x)
-    dy = _axis_derivative(depth, 0, pitch_y)
+    return _intensity_of_derivatives(coeffs, _axis_derivative(depth, 1, pitch_x), _axis_derivative(depth, 0, pitch_y))
+
+
+def _intensity_of_derivatives(coeffs, dx, dy):
+    """Clamped intensity [H, W, 3] from the depth derivatives dx = D_x, dy = D_y [H, W]."""
     inv = 1.0 / torch.sqrt(1.0 + dx * dx + dy * dy)
     nx, ny = dx * inv, dy * inv
     m = torch.stack([torch.ones_like(nx), nx, ny, nx * nx, ny * ny, nx * ny])       # [6, H, W]
@@ -262,6 +267,39 @@ def shade_mse(coeffs, pitch_x, pitch_y, sensor_id, depth, target):
         err.sum().backward()
         g_depth[b] = D.grad.numpy()
     return {"loss_map": loss_map, "coeffs": A.grad.numpy(), "depth": g_depth}
+
+
+def shade_slopes(coeffs, pitch_x, pitch_y, sensor_id, depth, g_intensity=None, target=None):
+    """Pixel slopes [B, H, W, 2]: at each pixel of each image, the gradient of that
+    pixel's own term of L with respect to the two depth derivatives (D_x, D_y) its normal
+    reads, the derivatives taken as independent variables.  L is sum(g_intensity * I)
+    (g_intensity [B, H, W, 3]) or, with target [B, H, W, 3] instead, the squared error of
+    shade_mse.  The depth gradient of L is the transpose of the derivative stencils
+    applied to these slopes (chain rule through D -> (D_x, D_y)).  Images with a sensor id
+    outside [0, S) are left at zero."""
+    coeffs = np.asarray(coeffs, np.float32)
+    S, _, _, H, W = coeffs.shape
+    depth = np.asarray(depth, np.float32).reshape(-1, H, W)
+    B = depth.shape[0]
+    A = torch.tensor(coeffs.astype(np.float64))
+    px, py = float(np.float32(pitch_x)), float(np.float32(pitch_y))
+    out = np.zeros((B, H, W, 2))
+    for b in range(B):
+        s = int(np.asarray(sensor_id).reshape(-1)[b])
+        if s < 0 or s >= S:
+            continue
+        D = torch.tensor(depth[b].astype(np.float64))
+        dx = _axis_derivative(D, 1, px).requires_grad_(True)
+        dy = _axis_derivative(D, 0, py).requires_grad_(True)
+        I = _intensity_of_derivatives(A[s], dx, dy)
+        if target is not None:
+            T = torch.from_numpy(np.asarray(target, np.float64).reshape(B, H, W, 3)[b])
+            ((I - T) ** 2).sum().backward()
+        else:
+            (I * torch.from_numpy(np.asarray(g_intensity, np.float64).reshape(B, H, W, 3)[b])).sum().backward()
+        out[b, :, :, 0] = dx.grad.numpy()
+        out[b, :, :, 1] = dy.grad.numpy()
+    return out
 
 
 GRAZING = 0.05   # |d phi / dz| below this: a grazing column, whose depth gradient is left out

@@ -34,6 +34,12 @@ def _lib():
         lib.tacsl_shade_adjoint.argtypes = [C.POINTER(_Shading), I64, P, P, P, P, P, P]
         lib.tacsl_shade_mse.restype = C.c_int
         lib.tacsl_shade_mse.argtypes = [C.POINTER(_Shading), I64, P, P, P, P, P, P, P, P]
+        lib.tacsl_shade_mse_slopes.restype = C.c_int
+        lib.tacsl_shade_mse_slopes.argtypes = [C.POINTER(_Shading), I64, P, P, P, P, P, P, P]
+        lib.tacsl_shade_adjoint_slopes.restype = C.c_int
+        lib.tacsl_shade_adjoint_slopes.argtypes = [C.POINTER(_Shading), I64, P, P, P, P, P, P]
+        lib.tacsl_shade_depth_from_slopes.restype = C.c_int
+        lib.tacsl_shade_depth_from_slopes.argtypes = [C.POINTER(_Shading), I64, P, P, P, P, P]
         lib.tacsl_render_depth_adjoint.restype = C.c_int
         lib.tacsl_render_depth_adjoint.argtypes = [C.POINTER(_SdfSet), I32, I32, P, P, C.POINTER(_Camera), P, P, P, P]
         _bound = True
@@ -106,9 +112,19 @@ class _ShadeIntensity(torch.autograd.Function):
         B = depth_map.numel() // (H * W)
         sh = Shading(coeffs.detach().contiguous(), *ctx.pitch)
         gc = torch.empty_like(coeffs) if need[0] else None
-        gd = torch.empty(depth_map.shape, dtype=torch.float32, device=depth_map.device) if need[1] else None
-        _check(_lib().tacsl_shade_adjoint(C.byref(sh.c), B, _ptr(sensor_id), _ptr(depth_map.detach()),
-                                          _ptr(g.contiguous()), _ptr(gc), _ptr(gd), _stream(None)))
+        gd = None
+        if need[1]:
+            # the coefficient adjoint also writes the pixel slopes; the depth gradient is
+            # their transposed difference stencil
+            gd = torch.empty(depth_map.shape, dtype=torch.float32, device=depth_map.device)
+            slopes = torch.empty(B, H, W, 2, dtype=torch.float32, device=depth_map.device)
+            _check(_lib().tacsl_shade_adjoint_slopes(C.byref(sh.c), B, _ptr(sensor_id), _ptr(depth_map.detach()),
+                                                     _ptr(g.contiguous()), _ptr(gc), _ptr(slopes), _stream(None)))
+            _check(_lib().tacsl_shade_depth_from_slopes(C.byref(sh.c), B, _ptr(sensor_id), _ptr(slopes), None,
+                                                        _ptr(gd), _stream(None)))
+        elif gc is not None:
+            _check(_lib().tacsl_shade_adjoint(C.byref(sh.c), B, _ptr(sensor_id), _ptr(depth_map.detach()),
+                                              _ptr(g.contiguous()), _ptr(gc), None, _stream(None)))
         return gc, gd, None, None, None
 
 
@@ -128,39 +144,50 @@ class _ShadeMse(torch.autograd.Function):
         B = depth_map.numel() // (H * W)
         sh = Shading(coeffs.detach().contiguous(), pitch_x, pitch_y)
         loss_map = torch.empty(S, H, W, dtype=torch.float32, device=depth_map.device)
-        # the coefficient gradient costs the loss pass nothing extra: take it here (for a
-        # unit upstream gradient) and scale it in backward
-        gc = torch.empty_like(coeffs) if coeffs.requires_grad else None
-        _check(_lib().tacsl_shade_mse(C.byref(sh.c), B, _ptr(sensor_id), _ptr(depth_map.detach()), _ptr(target),
-                                      None, _ptr(loss_map), _ptr(gc), None, _stream(None)))
-        ctx.save_for_backward(coeffs, depth_map, sensor_id, target)
-        ctx.gc = gc
+        # the coefficient gradient and the depth map's pixel slopes cost the loss pass
+        # little: take them here (for a unit upstream gradient) and scale them in backward
+        gc = torch.empty_like(coeffs) if ctx.needs_input_grad[0] else None
+        slopes = None
+        if ctx.needs_input_grad[1] and B > 0:
+            slopes = torch.empty(B, H, W, 2, dtype=torch.float32, device=depth_map.device)
+            _check(_lib().tacsl_shade_mse_slopes(C.byref(sh.c), B, _ptr(sensor_id), _ptr(depth_map.detach()),
+                                                 _ptr(target), _ptr(loss_map), _ptr(gc), _ptr(slopes),
+                                                 _stream(None)))
+        else:
+            _check(_lib().tacsl_shade_mse(C.byref(sh.c), B, _ptr(sensor_id), _ptr(depth_map.detach()),
+                                          _ptr(target), None, _ptr(loss_map), _ptr(gc), None, _stream(None)))
+        ctx.save_for_backward(coeffs, depth_map, sensor_id)
+        ctx.gc, ctx.slopes = gc, slopes
         ctx.pitch = (pitch_x, pitch_y)
         return loss_map.sum()
 
     @staticmethod
     def backward(ctx, g):
-        coeffs, depth_map, sensor_id, target = ctx.saved_tensors
+        coeffs, depth_map, sensor_id = ctx.saved_tensors
         need = ctx.needs_input_grad
         S, _, _, H, W = coeffs.shape
         B = depth_map.numel() // (H * W)
         gc = ctx.gc * g if need[0] and ctx.gc is not None else None
         gd = None
         if need[1]:
-            sh = Shading(coeffs.detach().contiguous(), *ctx.pitch)
             gd = torch.empty(depth_map.shape, dtype=torch.float32, device=depth_map.device)
-            scale = g.reshape(1).to(torch.float32).contiguous()
-            _check(_lib().tacsl_shade_mse(C.byref(sh.c), B, _ptr(sensor_id), _ptr(depth_map.detach()), _ptr(target),
-                                          _ptr(scale), None, None, _ptr(gd), _stream(None)))
-        ctx.gc = None
+            if ctx.slopes is not None:
+                sh = Shading(coeffs.detach().contiguous(), *ctx.pitch)
+                scale = g.reshape(1).to(torch.float32).contiguous()
+                _check(_lib().tacsl_shade_depth_from_slopes(C.byref(sh.c), B, _ptr(sensor_id), _ptr(ctx.slopes),
+                                                            _ptr(scale), _ptr(gd), _stream(None)))
+            else:
+                gd.zero_()      # no images
+        ctx.gc = ctx.slopes = None
         return gc, gd, None, None, None, None
 
 
 def shade_mse(coeffs, depth_map, sensor_id, pitch_x, pitch_y, target):
     """Differentiable squared error sum((clamp(I) - target)^2) over the B images [B, H, W]
     against target intensities [B, H, W, 3], without materialising I: one fused pass
-    forward (which also takes the coefficient gradient when coeffs require grad) and one
-    backward for the depth gradient; gradients flow to coeffs and depth_map."""
+    forward (which also takes the coefficient gradient when coeffs require grad, and the
+    pixel slopes of the depth gradient when depth_map does) and, backward, the
+    transposed difference stencil of the slopes; gradients flow to coeffs and depth_map."""
     _dev(coeffs.detach(), torch.float32, "coeffs")
     _dev(depth_map.detach(), torch.float32, "depth_map")
     _dev(sensor_id, torch.int32, "sensor_id")

@@ -463,7 +463,13 @@ __device__ __forceinline__ void cp_async8(float2* smem, const float* gmem) {
 // copies and scalar arithmetic per pixel and image, issue-bound): the same bits, 0.78 ->
 // 0.68 ms for the adjoint and 0.80 -> 0.78 ms for the loss form on 2048 maps of 320x240;
 // the registers (126-128) leave two CTAs per SM.
-template <bool kMse, bool kU8>
+// kSlopes: the kernel also writes, for every image it visits, the pixel slopes
+// slopes[b][px] = (dL/dD_x, dL/dD_y) of the pixel's own term of L with respect to the
+// two depth differences its normal reads (the chain of the Sec. III-B shading model
+// through the normal n = (D_x, D_y, 1)/|.|), as one 16-byte store per lane; the depth
+// gradient is then the transposed difference stencil of these slopes
+// (slopes_to_depth_kernel), so the backward pass no longer evaluates the shading.
+template <bool kMse, bool kU8, bool kSlopes>
 __global__ void __launch_bounds__(256, 2) shade_coeff_grad_kernel(ShadeGeom G, int64_t B,
                                                                    const float* __restrict__ coeffs,
                                                                    const int32_t* __restrict__ sensor_id,
@@ -471,7 +477,8 @@ __global__ void __launch_bounds__(256, 2) shade_coeff_grad_kernel(ShadeGeom G, i
                                                                    const float* __restrict__ u_inten,
                                                                    const float* __restrict__ scale,
                                                                    float* __restrict__ grad_coeffs,
-                                                                   float* __restrict__ loss_map) {
+                                                                   float* __restrict__ loss_map,
+                                                                   float* __restrict__ slopes) {
     constexpr int kTerms = kMse ? 19 : 18;
     extern __shared__ __align__(16) unsigned char dsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -571,6 +578,9 @@ __global__ void __launch_bounds__(256, 2) shade_coeff_grad_kernel(ShadeGeom G, i
 #pragma unroll
             for (int kk = 0; kk < 6; ++kk) ma[kk] = pk(fa ? lo(m[kk]) : 0.f, fb ? hi(m[kk]) : 0.f);
             const float ua[3] = {u01.x, u01.y, u23.x}, ub[3] = {u23.y, u45.x, u45.y};
+            f2 gm[6];       // kSlopes: dL/dm_k, from the raw coefficients
+#pragma unroll
+            for (int kk = 0; kk < 6; ++kk) gm[kk] = pk(0.f, 0.f);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 f2 I = pk(0.f, 0.f);
@@ -587,6 +597,26 @@ __global__ void __launch_bounds__(256, 2) shade_coeff_grad_kernel(ShadeGeom G, i
                 const f2 gc = pk(ga, gb);
 #pragma unroll
                 for (int kk = 0; kk < 6; ++kk) acc[kk][c] = fma2(gc, ma[kk], acc[kk][c]);
+                if (kSlopes) {
+#pragma unroll
+                    for (int kk = 0; kk < 6; ++kk) gm[kk] = fma2(gc, a[kk][c], gm[kk]);
+                }
+            }
+            if (kSlopes) {
+                // n = (D_x, D_y, 1) r with r = |(D_x, D_y, 1)|^-1: dn_x/dD_x = r - D_x^2 r^3,
+                // dn_x/dD_y = dn_y/dD_x = -D_x D_y r^3, dn_y/dD_y = r - D_y^2 r^3; and
+                // m = (1, n_x, n_y, n_x^2, n_y^2, n_x n_y)
+                const f2 two = pk(2.f, 2.f);
+                const f2 gnx = fma2(mul2(two, nx), gm[3], fma2(ny, gm[5], gm[1]));
+                const f2 gny = fma2(mul2(two, ny), gm[4], fma2(nx, gm[5], gm[2]));
+                const f2 r3 = mul2(mul2(r, r), r);
+                const f2 cxy = mul2(mul2(dxp, dyp), r3);
+                const f2 kx = sub2(r, mul2(mul2(dxp, dxp), r3));
+                const f2 ky = sub2(r, mul2(mul2(dyp, dyp), r3));
+                const f2 sx = sub2(mul2(gnx, kx), mul2(gny, cxy));
+                const f2 sy = sub2(mul2(gny, ky), mul2(gnx, cxy));
+                *reinterpret_cast<float4*>(slopes + (static_cast<int64_t>(list[i]) * G.HW + p0) * 2) =
+                    make_float4(lo(sx), lo(sy), hi(sx), hi(sy));
             }
         }
         cp_async_wait<0>();
@@ -954,6 +984,92 @@ __global__ void __launch_bounds__(256) zero_bad_sensor_images_kernel(int64_t B, 
         const int s = __ldg(sensor_id + b);
         if (s >= 0 && s < S) continue;
         for (int64_t k = threadIdx.x; k < HW; k += blockDim.x) grad_depth[b * HW + k] = 0.f;
+    }
+}
+
+// Depth gradient from pixel slopes: grad_depth[b][q] = scale * sum over the pixels p
+// whose difference stencils read D[q] of w(p, q) * slope(p) (the transpose of the
+// central / one-sided differences of the normal), with the four slots of depth_slots
+// summed in slot order.  Grid (512-pixel strips of the image plane, image chunks), 256
+// threads, two horizontally adjacent pixels per thread (W is a multiple of 4, so a pair
+// never straddles a row): per image a thread reads its pair's slopes and the pairs in
+// the rows above and below (16-byte loads; those rows are read again by the neighbouring
+// strips at the same time, so they come from L2), takes the horizontal neighbours'
+// D_x slopes by shuffle (lanes 0 and 31 load theirs), and writes its two gradients as
+// one 8-byte store.  The stencil weights are fixed per pixel and computed once; images
+// with a bad sensor id get zero.  Two images per iteration keep more loads in flight.
+constexpr int kSdPx = 512;
+
+struct SlopeRows {
+    float4 own, up, dn;
+    float left, right;
+};
+
+__global__ void __launch_bounds__(256, 4) slopes_to_depth_kernel(ShadeGeom G, int64_t B, int64_t chunk,
+                                                              const int32_t* __restrict__ sensor_id,
+                                                              const float* __restrict__ slopes,
+                                                              const float* __restrict__ scale,
+                                                              float* __restrict__ grad_depth) {
+    const int lane = threadIdx.x & 31;
+    const int64_t p0 = static_cast<int64_t>(blockIdx.x) * kSdPx + 2 * threadIdx.x;
+    const bool valid = p0 < G.HW;
+    const int y = valid ? static_cast<int>(p0 / G.W) : 0, x = valid ? static_cast<int>(p0 - static_cast<int64_t>(y) * G.W) : 0;
+    DepthSlot sa[4], sb[4];
+    depth_slots(G, x, y, sa);
+    depth_slots(G, x + 1, y, sb);
+    // pixel x reads D_x at x - 1 (or x on the left border) and x + 1; pixel x + 1 at x and
+    // x + 2 (or x + 1 on the right border); both read D_y in rows sa[2].qy and sa[3].qy
+    const bool hasL = x > 0, hasR = x + 2 < G.W;
+    const int o_up = sa[2].qy * G.W + x, o_dn = sa[3].qy * G.W + x, o_c = y * G.W + x;
+    const float sc = scale != nullptr ? __ldg(scale) : 1.f;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.y) * chunk, c1 = min(c0 + chunk, B);
+    auto load = [&](int64_t b, SlopeRows& v) {
+        const float* Sb = slopes + b * G.HW * 2;
+        if (valid) {
+            v.own = __ldg(reinterpret_cast<const float4*>(Sb + 2 * static_cast<int64_t>(o_c)));
+            v.up = __ldg(reinterpret_cast<const float4*>(Sb + 2 * static_cast<int64_t>(o_up)));
+            v.dn = __ldg(reinterpret_cast<const float4*>(Sb + 2 * static_cast<int64_t>(o_dn)));
+        } else {
+            v.own = v.up = v.dn = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        v.left = (valid && lane == 0 && hasL) ? __ldg(Sb + 2 * static_cast<int64_t>(o_c - 1)) : 0.f;
+        v.right = (valid && lane == 31 && hasR) ? __ldg(Sb + 2 * static_cast<int64_t>(o_c + 2)) : 0.f;
+    };
+    auto finish = [&](int64_t b, const SlopeRows& v) {
+        // every lane takes part in the shuffles
+        float L = __shfl_up_sync(0xffffffffu, v.own.z, 1);
+        float R = __shfl_down_sync(0xffffffffu, v.own.x, 1);
+        if (lane == 0) L = v.left;
+        if (lane == 31) R = v.right;
+        if (!valid) return;
+        const int s = __ldg(sensor_id + b);
+        float ga = 0.f, gb = 0.f;
+        if (s >= 0 && s < G.S) {
+            ga = sa[0].w * (hasL ? L : v.own.x);
+            ga = fmaf(sa[1].w, v.own.z, ga);
+            ga = fmaf(sa[2].w, v.up.y, ga);
+            ga = fmaf(sa[3].w, v.dn.y, ga);
+            gb = sb[0].w * v.own.x;
+            gb = fmaf(sb[1].w, hasR ? R : v.own.z, gb);
+            gb = fmaf(sb[2].w, v.up.w, gb);
+            gb = fmaf(sb[3].w, v.dn.w, gb);
+            ga *= sc;
+            gb *= sc;
+        }
+        *reinterpret_cast<float2*>(grad_depth + b * G.HW + o_c) = make_float2(ga, gb);
+    };
+    int64_t b = c0;
+    for (; b + 1 < c1; b += 2) {
+        SlopeRows v0, v1;
+        load(b, v0);
+        load(b + 1, v1);
+        finish(b, v0);
+        finish(b + 1, v1);
+    }
+    if (b < c1) {
+        SlopeRows v0;
+        load(b, v0);
+        finish(b, v0);
     }
 }
 

@@ -1281,38 +1281,75 @@ int shade_geom(const tacsl_shading* sh, ShadeGeom& G) {
     return TACSL_OK;
 }
 
-// Coefficient gradient (and, for the image loss, the loss map): the two-pixels-per-lane
-// kernel, with 8-byte copies of the upstream values where that array allows them.
+// Coefficient gradient (and, for the image loss, the loss map; with slopes, the pixel
+// slopes of the depth gradient): the two-pixels-per-lane kernel, with 8-byte copies of
+// the upstream values where that array allows them.
+template <bool kMse, bool kU8, bool kSlopes>
+cudaError_t coeff_grad_attr(int bytes) {
+    return cudaFuncSetAttribute(shade_coeff_grad_kernel<kMse, kU8, kSlopes>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 template <bool kMse>
 int launch_coeff_grad(const ShadeGeom& G, int64_t B, const float* coeffs, const int32_t* sensor_id,
                       const float* depth, const float* u, const float* scale, float* grad_coeffs, float* loss_map,
-                      DevInfo& dev, tacsl_stream_t stream) {
+                      float* slopes, DevInfo& dev, tacsl_stream_t stream) {
     const int64_t tiles = (G.HW + kCgPx - 1) / kCgPx;
     if (tiles > INT32_MAX || G.HW > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "image too large");
     if (!dev.cg_attr_set) {
         const int bytes = static_cast<int>(kCgSmemBytes);
-        cudaError_t e = cudaFuncSetAttribute(shade_coeff_grad_kernel<false, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(shade_coeff_grad_kernel<false, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(shade_coeff_grad_kernel<true, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(shade_coeff_grad_kernel<true, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaError_t e = coeff_grad_attr<false, false, false>(bytes);
+        if (e == cudaSuccess) e = coeff_grad_attr<false, true, false>(bytes);
+        if (e == cudaSuccess) e = coeff_grad_attr<true, false, false>(bytes);
+        if (e == cudaSuccess) e = coeff_grad_attr<true, true, false>(bytes);
+        if (e == cudaSuccess) e = coeff_grad_attr<false, false, true>(bytes);
+        if (e == cudaSuccess) e = coeff_grad_attr<false, true, true>(bytes);
+        if (e == cudaSuccess) e = coeff_grad_attr<true, false, true>(bytes);
+        if (e == cudaSuccess) e = coeff_grad_attr<true, true, true>(bytes);
         if (e != cudaSuccess) return fail(TACSL_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
         dev.cg_attr_set = true;
     }
     const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(G.S));
-    if (aligned(u, 8))
-        shade_coeff_grad_kernel<kMse, true><<<grid, 256, kCgSmemBytes, stream>>>(
-            G, B, coeffs, sensor_id, depth, u, scale, grad_coeffs, loss_map);
-    else
-        shade_coeff_grad_kernel<kMse, false><<<grid, 256, kCgSmemBytes, stream>>>(
-            G, B, coeffs, sensor_id, depth, u, scale, grad_coeffs, loss_map);
+    const bool u8 = aligned(u, 8);
+    if (slopes != nullptr) {
+        if (u8)
+            shade_coeff_grad_kernel<kMse, true, true><<<grid, 256, kCgSmemBytes, stream>>>(
+                G, B, coeffs, sensor_id, depth, u, scale, grad_coeffs, loss_map, slopes);
+        else
+            shade_coeff_grad_kernel<kMse, false, true><<<grid, 256, kCgSmemBytes, stream>>>(
+                G, B, coeffs, sensor_id, depth, u, scale, grad_coeffs, loss_map, slopes);
+    } else if (u8) {
+        shade_coeff_grad_kernel<kMse, true, false><<<grid, 256, kCgSmemBytes, stream>>>(
+            G, B, coeffs, sensor_id, depth, u, scale, grad_coeffs, loss_map, nullptr);
+    } else {
+        shade_coeff_grad_kernel<kMse, false, false><<<grid, 256, kCgSmemBytes, stream>>>(
+            G, B, coeffs, sensor_id, depth, u, scale, grad_coeffs, loss_map, nullptr);
+    }
     return check_launch(kMse ? "tacsl_shade_mse (loss map / coefficients)" : "tacsl_shade_adjoint (coefficients)");
+}
+
+// The depth gradient from pixel slopes: CTAs over (512-pixel strips, image chunks), the
+// number of chunks chosen (as for the depth-gradient kernel) so that the waves of four
+// CTAs per SM (64 registers a thread) are nearly full, with at least 8 images per CTA.
+int launch_slopes_to_depth(const ShadeGeom& G, int64_t B, const int32_t* sensor_id, const float* slopes,
+                           const float* scale, float* grad_depth, const DevInfo& dev, tacsl_stream_t stream) {
+    const int64_t strips = (G.HW + kSdPx - 1) / kSdPx;
+    if (strips > INT32_MAX || G.HW > INT32_MAX) return fail(TACSL_ERR_UNSUPPORTED, "image too large");
+    const int64_t slots = 4 * (int64_t)dev.sms;
+    const int64_t c_max = std::max<int64_t>(1, std::min<int64_t>((B + 7) / 8, 65535));
+    int64_t chunks = 1;
+    double best = 1e30;
+    for (int64_t c = 1; c <= std::min<int64_t>(c_max, 64); ++c) {
+        const double t = (double)((strips * c + slots - 1) / slots) / (double)c;
+        if (t < best - 1e-9) {
+            best = t;
+            chunks = c;
+        }
+    }
+    const int64_t chunk = (B + chunks - 1) / chunks;
+    const dim3 grid(static_cast<unsigned>(strips), static_cast<unsigned>((B + chunk - 1) / chunk));
+    slopes_to_depth_kernel<<<grid, 256, 0, stream>>>(G, B, chunk, sensor_id, slopes, scale, grad_depth);
+    return check_launch("depth gradient from slopes");
 }
 
 // Grid of the depth-gradient kernel: (32 x 8 tiles, sensors, image chunks), with enough
@@ -1449,7 +1486,7 @@ int tacsl_shade_adjoint(const tacsl_shading* shading, int64_t B, const int32_t* 
     shade_geom(shading, G);
     if (grad_coeffs != nullptr) {
         if ((rc = launch_coeff_grad<false>(G, B, shading->coeffs, sensor_id, depth_map, g_intensity, nullptr,
-                                           grad_coeffs, nullptr, *dev, stream)))
+                                           grad_coeffs, nullptr, nullptr, *dev, stream)))
             return rc;
     }
     if (grad_depth != nullptr && B > 0) {
@@ -1478,7 +1515,7 @@ int tacsl_shade_mse(const tacsl_shading* shading, int64_t B, const int32_t* sens
     shade_geom(shading, G);
     if (per_sensor) {
         if ((rc = launch_coeff_grad<true>(G, B, shading->coeffs, sensor_id, depth_map, target, scale, grad_coeffs,
-                                          loss_map, *dev, stream)))
+                                          loss_map, nullptr, *dev, stream)))
             return rc;
     }
     if (grad_depth != nullptr && B > 0) {
@@ -1487,6 +1524,62 @@ int tacsl_shade_mse(const tacsl_shading* shading, int64_t B, const int32_t* sens
             return rc;
     }
     return ok();
+}
+
+int tacsl_shade_mse_slopes(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id, const float* depth_map,
+                           const float* target, float* loss_map, float* grad_coeffs, float* slopes,
+                           tacsl_stream_t stream) {
+    const bool per_sensor = loss_map != nullptr || grad_coeffs != nullptr;
+    if (shading != nullptr && B == 0 && !per_sensor) return ok();
+    int rc = check_shade_args(shading, B, sensor_id, depth_map, reinterpret_cast<const uint8_t*>(target));
+    if (rc) return rc;
+    if (!aligned(target, 4) || !aligned(loss_map, 4) || !aligned(grad_coeffs, 4))
+        return fail(TACSL_ERR_INVALID_ARG, "target, loss_map and grad_coeffs must be 4-byte aligned");
+    if (B > 0 && (slopes == nullptr || !aligned(slopes, 16)))
+        return fail(TACSL_ERR_INVALID_ARG, "slopes must be non-NULL and 16-byte aligned");
+    if (shading->H > 65535) return fail(TACSL_ERR_UNSUPPORTED, "image height %d > 65535", shading->H);
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    ShadeGeom G;
+    shade_geom(shading, G);
+    return launch_coeff_grad<true>(G, B, shading->coeffs, sensor_id, depth_map, target, nullptr, grad_coeffs,
+                                   loss_map, B > 0 ? slopes : nullptr, *dev, stream);
+}
+
+int tacsl_shade_adjoint_slopes(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id,
+                               const float* depth_map, const float* g_intensity, float* grad_coeffs, float* slopes,
+                               tacsl_stream_t stream) {
+    if (shading != nullptr && B == 0 && grad_coeffs == nullptr) return ok();
+    int rc = check_shade_args(shading, B, sensor_id, depth_map, reinterpret_cast<const uint8_t*>(g_intensity));
+    if (rc) return rc;
+    if (!aligned(g_intensity, 4) || !aligned(grad_coeffs, 4))
+        return fail(TACSL_ERR_INVALID_ARG, "g_intensity and grad_coeffs must be 4-byte aligned");
+    if (B > 0 && (slopes == nullptr || !aligned(slopes, 16)))
+        return fail(TACSL_ERR_INVALID_ARG, "slopes must be non-NULL and 16-byte aligned");
+    if (shading->H > 65535) return fail(TACSL_ERR_UNSUPPORTED, "image height %d > 65535", shading->H);
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    ShadeGeom G;
+    shade_geom(shading, G);
+    return launch_coeff_grad<false>(G, B, shading->coeffs, sensor_id, depth_map, g_intensity, nullptr, grad_coeffs,
+                                    nullptr, B > 0 ? slopes : nullptr, *dev, stream);
+}
+
+int tacsl_shade_depth_from_slopes(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id,
+                                  const float* slopes, const float* scale, float* grad_depth, tacsl_stream_t stream) {
+    if (shading != nullptr && B == 0) return ok();
+    // the image checks of tacsl_shade_image, with the slopes in the places of the depth
+    // maps and of the output
+    int rc = check_shade_args(shading, B, sensor_id, slopes, reinterpret_cast<const uint8_t*>(grad_depth));
+    if (rc) return rc;
+    if (!aligned(grad_depth, 8) || !aligned(scale, 4))
+        return fail(TACSL_ERR_INVALID_ARG, "grad_depth must be 8-byte and scale 4-byte aligned");
+    if (shading->H > 65535) return fail(TACSL_ERR_UNSUPPORTED, "image height %d > 65535", shading->H);
+    DevInfo* dev;
+    if ((rc = device_info(&dev))) return rc;
+    ShadeGeom G;
+    shade_geom(shading, G);
+    return launch_slopes_to_depth(G, B, sensor_id, slopes, scale, grad_depth, *dev, stream);
 }
 
 int tacsl_render_depth_adjoint(const tacsl_sdf_set* set, int32_t E, int32_t P, const int32_t* obj_id,

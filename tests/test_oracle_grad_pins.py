@@ -452,10 +452,65 @@ def check_shade_mse(G):
         assert abs(got - fd) <= 2e-3 * max(abs(fd), 1e-3 * np.abs(r["depth"]).max()), (got, fd)
 
 
+def check_shade_slopes(G):
+    """The pixel slopes (dL/dD_x, dL/dD_y): on a flat gel (D_x = D_y = 0, so n = 0 and
+    dn/d(D_x, D_y) is the identity) they are sum_c g_c A[1, c] and sum_c g_c A[2, c] over
+    the unclamped channels, g = g_intensity or 2 (I - T); on a relief their image under
+    the transposed derivative stencils (built column by column from numpy.gradient:
+    central inside, one-sided on the border) is the depth gradient of shade_gradients and
+    shade_mse; an image with a bad sensor id keeps zero slopes."""
+    rng = np.random.default_rng(15)
+    H, W, S, B = 5, 8, 2, 3
+    px, py = 2e-4, 3e-4
+    co = synth.shading_coeffs(S, H, W, 22)
+    sid = np.array([1, 0, 1], np.int32)
+    flat = np.full((B, H, W), synth.D0, np.float32)
+    gI = rng.normal(size=(B, H, W, 3))
+    got = G.shade_slopes(co, px, py, sid, flat, g_intensity=gI)
+    _, inten, _ = oracle.shade(co, px, py, sid, flat, with_intensity=True)
+    live = (inten > 0) & (inten < 255)
+    assert live.mean() > 0.5
+    tgt = inten + rng.normal(0, 20, size=inten.shape)
+    got_mse = G.shade_slopes(co, px, py, sid, flat, target=tgt)
+    for b in range(B):
+        A = co[sid[b]].astype(np.float64)                       # [6, 3, H, W]
+        g = np.where(live[b], gI[b], 0.0)                       # [H, W, 3]
+        e = np.where(live[b], 2 * (inten[b] - tgt[b]), 0.0)
+        for axis in (0, 1):
+            want = (g * np.moveaxis(A[1 + axis], 0, -1)).sum(-1)
+            assert np.abs(got[b, :, :, axis] - want).max() <= 1e-9 * np.abs(want).max()
+            want = (e * np.moveaxis(A[1 + axis], 0, -1)).sum(-1)
+            assert np.abs(got_mse[b, :, :, axis] - want).max() <= 1e-9 * np.abs(want).max()
+    dm = (synth.D0 + 2e-5 * rng.normal(size=(B, H, W))).astype(np.float32)
+    _, inten, _ = oracle.shade(co, px, py, sid, dm, with_intensity=True)
+    tgt = inten + rng.normal(0, 20, size=inten.shape)
+
+    def transpose_stencil(sl):
+        out = np.zeros((H, W))
+        for y in range(H):
+            for x in range(W):
+                e = np.zeros((H, W))
+                e[y, x] = 1.0
+                # the pitches as the kernels and the oracle take them: float32 values
+                out[y, x] = (sl[..., 0] * np.gradient(e, float(np.float32(px)), axis=1)).sum() + \
+                    (sl[..., 1] * np.gradient(e, float(np.float32(py)), axis=0)).sum()
+        return out
+
+    sl = G.shade_slopes(co, px, py, sid, dm, g_intensity=gI)
+    sl_mse = G.shade_slopes(co, px, py, sid, dm, target=tgt)
+    gd = G.shade_gradients(co, px, py, sid, dm, gI)["depth"]
+    gd_mse = G.shade_mse(co, px, py, sid, dm, tgt)["depth"]
+    for b in range(B):
+        assert np.abs(transpose_stencil(sl[b]) - gd[b]).max() <= 1e-9 * np.abs(gd[b]).max()
+        assert np.abs(transpose_stencil(sl_mse[b]) - gd_mse[b]).max() <= 1e-9 * np.abs(gd_mse[b]).max()
+    bad = G.shade_slopes(co, px, py, np.array([1, -1, 2], np.int32), dm, g_intensity=gI)
+    assert np.array_equal(bad[0], sl[0]) and not bad[1].any() and not bad[2].any()
+
+
 CHECKS = [check_forward_matches_c_oracle, check_intensity_matches_c_oracle,
           check_force_gradients_match_central_differences, check_closed_forms_kn_kt_mu, check_half_space,
           check_shading_closed_forms, check_render_tilted_half_space, check_render_central_differences,
-          check_shade_mse]
+          check_shade_mse, check_shade_slopes]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=[c.__name__ for c in CHECKS])
