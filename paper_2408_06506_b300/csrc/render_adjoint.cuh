@@ -13,11 +13,17 @@
 //
 // Launch: CTA clusters of C CTAs per pad, C chosen on the host so that the launch fills
 // whole waves of resident CTAs (C = 1 when the batch alone does).  The C CTAs take
-// contiguous pixel ranges of the pad's image, streaming the depth map as float4 (the
-// upstream gradient is read only at hit columns); each reduces its 12 sums (t, R)
-// in a fixed order (shuffles, then warps in order); the cluster's rank 0 reads the other
-// ranks' sums from their shared memory (DSMEM) in rank order after a cluster barrier, so
-// the result does not depend on scheduling.
+// contiguous pixel ranges of the pad's image; each warp of a CTA walks its share of the
+// range in passes of 512 pixels (four coalesced float4 loads per lane), lists the pass's
+// hit columns in its own slice of shared memory in a fixed order (a prefix sum of the
+// lanes' counts by shuffles), and then its 32 lanes take the list entries e = lane,
+// lane + 32, ...: the upstream gradient (read only at hit columns) and the SDF cell of
+// each hit are gathered 32 at a time instead of one after another by the lane whose
+// pixels hit (hits come in contact patches, so a few lanes held most of a warp's hits).
+// The warps never wait for one another inside the walk.  Each CTA reduces its 12 sums
+// (t, R) in a fixed order (shuffles, then warps in order); the cluster's rank 0 reads
+// the other ranks' sums from their shared memory (DSMEM) in rank order after a cluster
+// barrier, so the result does not depend on scheduling.
 #pragma once
 
 #include "adjoint.cuh"
@@ -28,7 +34,8 @@
 namespace tacsl {
 
 constexpr int kRenderAdjThreads = 256;
-constexpr int kRenderAdjUnroll = 4;     // float4 depth loads in flight per thread
+constexpr int kRenderAdjUnroll = 4;     // float4 loads in flight per lane
+constexpr int kRenderAdjPass = 4 * kRenderAdjUnroll * 32;   // pixels per warp pass
 constexpr int kRenderAdjMaxCluster = 8;
 constexpr float kGrazing = 0.05f;   // |d phi / dz| below this: no derivative (grazing column)
 
@@ -120,11 +127,14 @@ __device__ __forceinline__ void render_pixel_adjoint(const DevSdf& S, const floa
 __global__ void __launch_bounds__(kRenderAdjThreads, 4) render_adjoint_kernel(const RenderAdjointArgs A) {
     __shared__ float warp_sum[kRenderAdjThreads / 32][12];
     __shared__ float cta_sum[12];
+    __shared__ uint16_t hit_k[kRenderAdjThreads / 32][kRenderAdjPass];   // a pass's hits, per warp
+    __shared__ float hit_d[kRenderAdjThreads / 32][kRenderAdjPass];
     const int C = A.cluster;
     const int64_t b = static_cast<int64_t>(blockIdx.x) / C;
     const uint32_t rank = C > 1 ? cluster_cta_rank() : 0u;
     const int id = __ldg(A.obj_id + static_cast<int>(b / A.P));
     const bool bad = id < 0 || id >= A.tab.count;
+    const int warp = static_cast<int>(threadIdx.x >> 5), lane = static_cast<int>(threadIdx.x & 31);
     float acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = 0.f;
@@ -145,51 +155,66 @@ __global__ void __launch_bounds__(kRenderAdjThreads, 4) render_adjoint_kernel(co
         const int n4 = HW >> 2;
         const int beg = static_cast<int>(static_cast<int64_t>(n4) * rank / C);
         const int end = static_cast<int>(static_cast<int64_t>(n4) * (rank + 1) / C);
-        const float* D = A.depth + b * HW;
         const float* G = A.g_depth + b * HW;
-        const float4* D4 = reinterpret_cast<const float4*>(D);
+        const float4* D4 = reinterpret_cast<const float4*>(A.depth + b * HW);
         const uint64_t pol = policy_evict_last();
-        // Stream the depth map 16 pixels per thread per pass (kRenderAdjUnroll float4
-        // loads in flight); the upstream gradient is read only at hit columns.
-        for (int k4 = beg + static_cast<int>(threadIdx.x); k4 < end; k4 += kRenderAdjUnroll * kRenderAdjThreads) {
+        float r[9], t[3];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) r[q] = rt_s[q];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) t[q] = rt_s[9 + q];
+        uint16_t* wk = hit_k[warp];
+        float* wd = hit_d[warp];
+        constexpr int kQ = kRenderAdjPass / 4;   // float4 per pass
+        // pass p of the CTA's range covers float4 beg + p * kQ ...; warp w takes p = w, w + 8, ...
+        for (int q0 = beg + warp * kQ; q0 < end; q0 += (kRenderAdjThreads / 32) * kQ) {
             float4 dv[kRenderAdjUnroll];
 #pragma unroll
             for (int u = 0; u < kRenderAdjUnroll; ++u) {
-                const int q = k4 + u * kRenderAdjThreads;
+                const int q = q0 + u * 32 + lane;
                 dv[u] = q < end ? __ldcs(D4 + q) : make_float4(cam.d0, cam.d0, cam.d0, cam.d0);
             }
             uint32_t hits = 0;
 #pragma unroll
             for (int u = 0; u < kRenderAdjUnroll; ++u) {
-                const float c4[4] = {dv[u].x, dv[u].y, dv[u].z, dv[u].w};
+                const float c4v[4] = {dv[u].x, dv[u].y, dv[u].z, dv[u].w};
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    if (c4[c] < cam.d0 && c4[c] > bottom) hits |= 1u << (4 * u + c);
+                    if (c4v[c] < cam.d0 && c4v[c] > bottom) hits |= 1u << (4 * u + c);
             }
-            while (hits != 0u) {
-                const int h = __ffs(hits) - 1;
-                hits &= hits - 1u;
-                const int k = 4 * (k4 + (h >> 2) * kRenderAdjThreads) + (h & 3);
+            if (__ballot_sync(0xffffffffu, hits != 0u) == 0u) continue;
+            // the pass's hits listed in (lane, u, c) order: prefix sum of the lanes' counts
+            const int n = __popc(hits);
+            int incl = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            int pos = incl - n;
+#pragma unroll
+            for (int u = 0; u < kRenderAdjUnroll; ++u) {
+                const float c4v[4] = {dv[u].x, dv[u].y, dv[u].z, dv[u].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (hits & (1u << (4 * u + c))) {
+                        wk[pos] = static_cast<uint16_t>(4 * (u * 32 + lane) + c);
+                        wd[pos] = c4v[c];
+                        ++pos;
+                    }
+            }
+            __syncwarp();
+            for (int e = lane; e < total; e += 32) {
+                const int k = 4 * q0 + wk[e];            // pixel index in the image
                 const float g = __ldcs(G + k);
                 if (g == 0.f) continue;
-                float d = 0.f;                     // dv's element h, selected without local memory
-#pragma unroll
-                for (int u = 0; u < kRenderAdjUnroll; ++u) {
-                    d = h == 4 * u ? dv[u].x : d;
-                    d = h == 4 * u + 1 ? dv[u].y : d;
-                    d = h == 4 * u + 2 ? dv[u].z : d;
-                    d = h == 4 * u + 3 ? dv[u].w : d;
-                }
                 const int j = k / cam.W, i = k - j * cam.W;
                 const float px = fmaf(static_cast<float>(i), cam.pitch_x, cam.x0);
                 const float py = fmaf(static_cast<float>(j), cam.pitch_y, cam.y0);
-                float r[9], t[3];
-#pragma unroll
-                for (int q = 0; q < 9; ++q) r[q] = rt_s[q];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) t[q] = rt_s[9 + q];
-                render_pixel_adjoint(S, r, t, px, py, d - cam.d0, g, pol, acc);
+                render_pixel_adjoint(S, r, t, px, py, wd[e] - cam.d0, g, pol, acc);
             }
+            __syncwarp();          // the list is rewritten by the next pass
         }
     }
     // CTA reduction in a fixed order: lanes by xor shuffles, then warps in index order
@@ -198,7 +223,6 @@ __global__ void __launch_bounds__(kRenderAdjThreads, 4) render_adjoint_kernel(co
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
     }
-    const int warp = static_cast<int>(threadIdx.x >> 5), lane = static_cast<int>(threadIdx.x & 31);
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < 12; ++k) warp_sum[warp][k] = acc[k];

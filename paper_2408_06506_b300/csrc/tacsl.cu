@@ -60,7 +60,7 @@ struct DevInfo {
     bool cg_attr_set = false;                   // shade_coeff_grad_kernel: dynamic shared memory
     bool in_attr_set = false;                   // shade_intensity_kernel: dynamic shared memory
     int batch_force_ctas[4] = {0, 0, 0, 0};   // resident CTAs per SM: [np == 4][dynamic]
-    int render_adj_ctas = 0;                    // resident render-adjoint CTAs per SM
+    int render_adj_slots[9] = {};               // render adjoint: co-resident CTAs in clusters of C (index C)
     // streams and events of tacsl_tactile_step_host, created on its first call here
     cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t pipe_start = nullptr, pipe_done[3] = {nullptr, nullptr, nullptr};
@@ -1601,22 +1601,35 @@ int tacsl_render_depth_adjoint(const tacsl_sdf_set* set, int32_t E, int32_t P, c
         return fail(TACSL_ERR_INVALID_ARG, "g_depth and grad_pose must be non-NULL and 4-byte aligned");
     DevInfo* dev;
     if ((rc = device_info(&dev))) return rc;
-    if (dev->render_adj_ctas == 0) {
-        int n = 0;
-        const cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_adjoint_kernel,
-                                                                             kRenderAdjThreads, 0);
-        if (oe != cudaSuccess || n < 1) return fail(TACSL_ERR_CUDA, "render adjoint occupancy query failed");
-        dev->render_adj_ctas = n;
+    const int64_t HW = (int64_t)c.H * c.W;
+    if (dev->render_adj_slots[1] == 0) {
+        // co-resident CTAs for each cluster size (the GPU places a cluster's CTAs together,
+        // so clusters of 8 can leave SMs idle that single CTAs would fill)
+        for (int cc = 1; cc <= kRenderAdjMaxCluster; ++cc) {
+            cudaLaunchConfig_t q = {};
+            q.gridDim = dim3(static_cast<unsigned>(cc * 1024));
+            q.blockDim = dim3(kRenderAdjThreads);
+            cudaLaunchAttribute qa[1];
+            qa[0].id = cudaLaunchAttributeClusterDimension;
+            qa[0].val.clusterDim.x = static_cast<unsigned>(cc);
+            qa[0].val.clusterDim.y = 1;
+            qa[0].val.clusterDim.z = 1;
+            q.attrs = qa;
+            q.numAttrs = 1;
+            int n = 0;
+            const cudaError_t oe = cudaOccupancyMaxActiveClusters(&n, render_adjoint_kernel, &q);
+            if (oe != cudaSuccess || n < 1) return fail(TACSL_ERR_CUDA, "render adjoint occupancy query failed");
+            dev->render_adj_slots[cc] = n * cc;
+        }
     }
     // CTAs per pad: the C in 1..8 (each CTA keeping at least 2048 pixels) whose launch
-    // of B*C CTAs, each taking 1/C of an image, ends soonest on the resident CTA slots:
-    // minimise ceil(B*C / slots) / C, ties to the smaller C
-    const int64_t HW = (int64_t)c.H * c.W;
-    const int64_t slots = (int64_t)dev->render_adj_ctas * dev->sms;
+    // of B*C CTAs, each taking 1/C of an image, ends soonest on the co-resident CTAs of
+    // clusters of C: minimise ceil(B*C / slots_C) / C, ties to the smaller C
     const int64_t c_max = std::min<int64_t>(kRenderAdjMaxCluster, std::max<int64_t>(1, HW / 2048));
     int C = 1;
-    double best = (double)((B + slots - 1) / slots);
+    double best = (double)((B + dev->render_adj_slots[1] - 1) / dev->render_adj_slots[1]);
     for (int64_t cc = 2; cc <= c_max; ++cc) {
+        const int64_t slots = dev->render_adj_slots[cc];
         const double t = (double)((B * cc + slots - 1) / slots) / (double)cc;
         if (t < best - 1e-9) {
             best = t;
