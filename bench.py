@@ -146,7 +146,9 @@ def profiled_traffic(name, n_units, algorithmic_bytes_per_unit):
     a linear fit (fixed + per unit) of single-pass ncu counters taken on two smaller
     launches of the same kernel, used only while the kernel's listed sources hash to the
     recorded value and a unit has the recorded algorithmic bytes (else None: the counters
-    are stale, or belong to another image size)."""
+    are stale, or belong to another image size); or, for a workload whose units differ
+    (the uneven batch), the DRAM bytes per algorithmic byte of smaller launches times this
+    launch's algorithmic bytes."""
     tfile = os.path.join(ROOT, "profiles", f"{name}_traffic.txt")
     if not os.path.exists(tfile):
         return None
@@ -154,6 +156,10 @@ def profiled_traffic(name, n_units, algorithmic_bytes_per_unit):
     files = kv.get("source_files", "").split(",")
     if not files[0] or kv.get("source_hash") != _source_hash(files):
         return None
+    if "dram_bytes_per_algorithmic_byte" in kv:
+        # counters of smaller launches of the same kernel, whose traffic grew in proportion
+        # to their algorithmic bytes: scaled to this launch's algorithmic bytes
+        return int(round(float(kv["dram_bytes_per_algorithmic_byte"]) * n_units * algorithmic_bytes_per_unit))
     if "algorithmic_bytes_per_launch" in kv:   # counters of one launch of exactly this workload
         if int(kv["algorithmic_bytes_per_launch"]) != int(n_units * algorithmic_bytes_per_unit):
             return None
