@@ -1210,6 +1210,8 @@ def run_grad(args, rank, world, local_rank, dist):
     # with the coefficient gradient and the pixel slopes (8 B/px) written as well; the
     # stencil pass reads the slopes and writes the depth gradient (12 B/px)
     slopes_fwd_bytes = 24 * npx + 2 * coef_bytes + coef_bytes // 18
+    two_pass_ms = (k_ms["shade_mse_kernel (loss map + coefficient gradient + slopes)"]
+                   - k_ms["shade_mse_kernel (loss map + coefficient gradient)"] + k_ms["slopes_to_depth_kernel"])
     return {
         "workload": GRAD_WORKLOAD, "envs_per_gpu": E, "steps": K,
         "ms_per_step": ms, "unit": "taxel-points/s", "value": world * E * P * T / (ms * 1e-3),
@@ -1245,6 +1247,11 @@ def run_grad(args, rank, world, local_rank, dist):
             "slopes_to_depth_kernel": {
                 "algorithmic_bytes": 12 * npx,
                 "frac": 12 * npx / (k_ms["slopes_to_depth_kernel"] * 1e-3) / 1e9 / peak},
+            # the depth gradient as the autograd binding computes it: what the slopes add to the
+            # loss forward plus the stencil pass, against the one-pass kernel's algorithmic bytes
+            "image-loss depth gradient (two-pass: slopes added to the forward + stencil)": {
+                "ms": two_pass_ms, "algorithmic_bytes": mse_bytes + 4 * npx,
+                "frac": (mse_bytes + 4 * npx) / (two_pass_ms * 1e-3) / 1e9 / peak},
             "render_adjoint_kernel": {"algorithmic_bytes": radj_bytes, "hit_columns": n_hit,
                                       "frac": radj_bytes / (k_ms["render_adjoint_kernel"] * 1e-3) / 1e9 / peak},
             "peak_gbs": peak},

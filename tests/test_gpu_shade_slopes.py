@@ -89,7 +89,10 @@ def _one_pass(sh, B, H, W, sid, dm, u, mse, S):
     return lm, gc, gd
 
 
-SHAPES = [(2, 6, 24, 32), (1, 3, 7, 12), (3, 10, 16, 12), (1, 2, 1, 8), (2, 5, 9, 36), (2, 4, 5, 4), (1, 3, 2, 4)]
+# the last two: several 512-pixel strips per image with a ragged last strip, and one
+# image row longer than a strip
+SHAPES = [(2, 6, 24, 32), (1, 3, 7, 12), (3, 10, 16, 12), (1, 2, 1, 8), (2, 5, 9, 36), (2, 4, 5, 4), (1, 3, 2, 4),
+          (2, 5, 40, 20), (1, 2, 3, 7040)]
 
 
 @pytest.mark.parametrize("mse", [True, False], ids=["mse", "adjoint"])
