@@ -96,15 +96,18 @@ struct __align__(16) RenderFrame {
     float u00[3];
     int id;          // object id, -1 when out of range
     float ui[3], kappa;   // kappa: march step per unit of phi, 1 / |R e_z|_1
-    float uj[3], pad1;
+    float uj[3];
+    int tile_out;         // every column of the block's tile misses the grid's domain
     float du[3], pad2;
     float inv_du[3], pad3;
 };
 constexpr int kRenderFrames = 256;   // frames a block keeps in shared memory at a time
 
-// Frame of the image of pad b (pose row b) against object id.
+// Frame of the image of pad b (pose row b) against object id, for the tile of pixel
+// columns i in [i0, i1], j in [j0, j1].
 __device__ __forceinline__ void render_frame(const SdfTable& tab, int id, const float* pad_pose, int64_t b,
-                                             const CameraArgs& cam, RenderFrame& f) {
+                                             const CameraArgs& cam, int i0, int i1, int j0, int j1,
+                                             RenderFrame& f) {
     if (id < 0 || id >= tab.count) {
         f.id = -1;
         return;
@@ -125,6 +128,22 @@ __device__ __forceinline__ void render_frame(const SdfTable& tab, int id, const 
     }
     f.kappa = 1.f / (fabsf(r[2]) + fabsf(r[5]) + fabsf(r[8]));
     f.id = id;
+    // The tile's columns fill the box i in [i0, i1], j in [j0, j1], z in [-z_max, 0], whose
+    // image under the affine u has, per axis, the range [lo, hi] below; when some axis's
+    // range lies outside [0.5, n_a - 1.5] (by a margin of 1/64 voxel, far above the
+    // rounding of the per-column slab test), no column of the tile meets the domain, so
+    // each reads d0, as its own slab test would find.
+    const float n[3] = {static_cast<float>(S.n0), static_cast<float>(S.n1), static_cast<float>(S.n2)};
+    bool out = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo = f.u00[a] + fminf(i0 * f.ui[a], i1 * f.ui[a]) + fminf(j0 * f.uj[a], j1 * f.uj[a]) +
+                         fminf(-cam.z_max * f.du[a], 0.f);
+        const float hi = f.u00[a] + fmaxf(i0 * f.ui[a], i1 * f.ui[a]) + fmaxf(j0 * f.uj[a], j1 * f.uj[a]) +
+                         fmaxf(-cam.z_max * f.du[a], 0.f);
+        out = out || hi < 0.5f - 1.f / 64.f || lo > n[a] - 1.5f + 1.f / 64.f;
+    }
+    f.tile_out = out ? 1 : 0;
 }
 
 // Grid: (32 x 8 pixel tiles of the image, up to 64 image slots); block y takes images
@@ -156,11 +175,14 @@ __global__ void __launch_bounds__(256) render_kernel(const SdfTable tab, int64_t
         __syncthreads();       // the previous frames are no longer read
         if (static_cast<int>(threadIdx.x) < n_here) {
             const int64_t b = static_cast<int64_t>(blockIdx.y) + (base + threadIdx.x) * gridDim.y;
+            const int ti0 = tile_x * 32, tj0 = tile_y * 8;
+            const int ti1 = min(ti0 + 31, cam.W - 1), tj1 = min(tj0 + 7, cam.H - 1);
             if (img_po == nullptr) {
-                render_frame(tab, __ldg(obj_id + static_cast<int>(b / P)), pad_pose, b, cam, frames[threadIdx.x]);
+                render_frame(tab, __ldg(obj_id + static_cast<int>(b / P)), pad_pose, b, cam, ti0, ti1, tj0, tj1,
+                             frames[threadIdx.x]);
             } else {
                 const int2 po = __ldg(img_po + b);
-                render_frame(tab, po.y, pad_pose, po.x, cam, frames[threadIdx.x]);
+                render_frame(tab, po.y, pad_pose, po.x, cam, ti0, ti1, tj0, tj1, frames[threadIdx.x]);
             }
         }
         __syncthreads();
@@ -172,6 +194,10 @@ __global__ void __launch_bounds__(256) render_kernel(const SdfTable tab, int64_t
             if (F.id < 0) {
                 depth[k] = __int_as_float(0x7fc00000);
                 raise_dev_error(TACSL_DEVERR_BAD_OBJ_ID);
+                continue;
+            }
+            if (F.tile_out) {              // the whole tile misses the domain (block-uniform)
+                depth[k] = cam.d0;
                 continue;
             }
             const DevSdf& S = tab.s[F.id];

@@ -155,10 +155,14 @@ def test_pose_requests_equal_alone_and_mixed(scene):
         assert srv.wait(rid)[0] == 0
         alone.append(_clone(out))
     # mixed: a large pose request holds the only stream while the others queue, so they
-    # are then served together in one batch
-    big = _pose_request(sc, np.tile(np.arange(sc.n_pad), 200))
-    ids = [_submit(srv, big)]
-    ids += [_submit(srv, _pose_request(sc, pads)) for pads in groups]
+    # are then served together in one batch; the small requests and their output buffers
+    # are built before the large one goes in, so that they queue within its run time
+    big = _pose_request(sc, np.tile(np.arange(sc.n_pad), 600))
+    small = [_pose_request(sc, pads) for pads in groups]
+    outs = [srv.pose_outputs_for(r["layout"], r["sensor"], want=ALL) for r in small]
+    big_out = srv.pose_outputs_for(big["layout"], big["sensor"], want=("wrench",))
+    ids = [(srv.submit_poses(out=big_out, **big), big_out)]
+    ids += [(srv.submit_poses(out=o, **r), o) for r, o in zip(small, outs)]
     for rid, _ in ids:
         assert srv.wait(rid)[0] == 0
     assert srv.stats()["max_batch_requests"] >= len(groups)
