@@ -157,7 +157,7 @@ def test_pose_requests_equal_alone_and_mixed(scene):
     # mixed: a large pose request holds the only stream while the others queue, so they
     # are then served together in one batch; the small requests and their output buffers
     # are built before the large one goes in, so that they queue within its run time
-    big = _pose_request(sc, np.tile(np.arange(sc.n_pad), 600))
+    big = _pose_request(sc, np.tile(np.arange(sc.n_pad), 1000))
     small = [_pose_request(sc, pads) for pads in groups]
     outs = [srv.pose_outputs_for(r["layout"], r["sensor"], want=ALL) for r in small]
     big_out = srv.pose_outputs_for(big["layout"], big["sensor"], want=("wrench",))
