@@ -562,12 +562,46 @@ __global__ void __launch_bounds__(256, 2) shade_coeff_grad_kernel(ShadeGeom G, i
             float R = __shfl_down_sync(0xffffffffu, ce.x, 1);
             if (lane == 0) L = sl[96].x;
             if (lane == 31) R = sl[96].x;
-            if (!valid) continue;
-            const float2 u01 = sl[128], u23 = sl[160], u45 = sl[192];
             const f2 dxp = pk((ce.y - (hasL ? L : ce.x)) * cx0, ((hasR ? R : ce.y) - ce.x) * cx1);
             const f2 dyp = mul2(sub2(pk(dn.x, dn.y), pk(up.x, up.y)), cyy);
+            // a warp whose pixels all see a flat gel (both depth differences exactly zero):
+            // n = (0, 0), so m = (1, +-0, +-0, 0, 0, +-0) and every term but m_0's adds a
+            // signed zero to a sum that is never -0; the flat path leaves those terms out,
+            // with the same bits (coefficients finite)
+            const bool flat = __all_sync(0xffffffffu, !valid || ((dxp | dyp) & 0x7fffffff7fffffffull) == 0ull);
+            if (!valid) continue;
+            const float2 u01 = sl[128], u23 = sl[160], u45 = sl[192];
             const f2 s2 = fma2(dxp, dxp, fma2(dyp, dyp, one2));
             const f2 r = pk(rsqrtf(lo(s2)), rsqrtf(hi(s2)));
+            const float ua[3] = {u01.x, u01.y, u23.x}, ub[3] = {u23.y, u45.x, u45.y};
+            if (flat) {
+                f2 gm1 = pk(0.f, 0.f), gm2 = pk(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const f2 I = fma2(a[0][c], one2, pk(0.f, 0.f));
+                    const float Ia = lo(I), Ib = hi(I);
+                    if (kMse) {
+                        const float ea = fminf(fmaxf(Ia, 0.f), 255.f) - ua[c];
+                        const float eb = fminf(fmaxf(Ib, 0.f), 255.f) - ub[c];
+                        lacc = pk(fmaf(ea, ea, lo(lacc)), fmaf(eb, eb, hi(lacc)));
+                    }
+                    const float ga = (Ia > 0.f && Ia < 255.f) ? (kMse ? w2s * (Ia - ua[c]) : ua[c]) : 0.f;
+                    const float gb = (Ib > 0.f && Ib < 255.f) ? (kMse ? w2s * (Ib - ub[c]) : ub[c]) : 0.f;
+                    const f2 gc = pk(ga, gb);
+                    acc[0][c] = fma2(gc, one2, acc[0][c]);
+                    if (kSlopes) {
+                        gm1 = fma2(gc, a[1][c], gm1);
+                        gm2 = fma2(gc, a[2][c], gm2);
+                    }
+                }
+                if (kSlopes) {
+                    // (dL/dD_x, dL/dD_y) = (gm_1, gm_2) r at n = 0
+                    const f2 sx = mul2(gm1, r), sy = mul2(gm2, r);
+                    *reinterpret_cast<float4*>(slopes + (static_cast<int64_t>(list[i]) * G.HW + p0) * 2) =
+                        make_float4(lo(sx), lo(sy), hi(sx), hi(sy));
+                }
+                continue;
+            }
             const f2 nx = mul2(dxp, r), ny = mul2(dyp, r);
             const f2 m[6] = {one2, nx, ny, mul2(nx, nx), mul2(ny, ny), mul2(nx, ny)};
             // the accumulation reads the monomials with a non-finite depth difference set to
@@ -577,7 +611,6 @@ __global__ void __launch_bounds__(256, 2) shade_coeff_grad_kernel(ShadeGeom G, i
             f2 ma[6];
 #pragma unroll
             for (int kk = 0; kk < 6; ++kk) ma[kk] = pk(fa ? lo(m[kk]) : 0.f, fb ? hi(m[kk]) : 0.f);
-            const float ua[3] = {u01.x, u01.y, u23.x}, ub[3] = {u23.y, u45.x, u45.y};
             f2 gm[6];       // kSlopes: dL/dm_k, from the raw coefficients
 #pragma unroll
             for (int kk = 0; kk < 6; ++kk) gm[kk] = pk(0.f, 0.f);
@@ -730,21 +763,33 @@ __global__ void __launch_bounds__(256) shade_intensity_kernel(ShadeGeom G, int64
             float R = __shfl_down_sync(0xffffffffu, ce.x, 1);
             if (lane == 0) L = sl[96].x;
             if (lane == 31) R = sl[96].x;
-            if (!valid) continue;
             const f2 dxp = pk((ce.y - (hasL ? L : ce.x)) * cx0, ((hasR ? R : ce.y) - ce.x) * cx1);
             const f2 dyp = mul2(sub2(pk(dn.x, dn.y), pk(up.x, up.y)), cyy);
-            const f2 s2 = fma2(dxp, dxp, fma2(dyp, dyp, one2));
-            const f2 r = pk(rsqrtf(lo(s2)), rsqrtf(hi(s2)));
-            const f2 nx = mul2(dxp, r), ny = mul2(dyp, r);
-            const f2 m[6] = {one2, nx, ny, mul2(nx, nx), mul2(ny, ny), mul2(nx, ny)};
+            // a flat warp (both depth differences exactly zero at every pixel): I = A_0, with
+            // the bits of the full sum (its other terms add signed zeros; coefficients finite)
+            const bool flat = __all_sync(0xffffffffu, !valid || ((dxp | dyp) & 0x7fffffff7fffffffull) == 0ull);
+            if (!valid) continue;
             float o[6];
+            if (flat) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                f2 I = pk(0.f, 0.f);
+                for (int c = 0; c < 3; ++c) {
+                    const f2 I = fma2(a[0][c], one2, pk(0.f, 0.f));
+                    o[c] = fminf(fmaxf(lo(I), 0.f), 255.f);
+                    o[3 + c] = fminf(fmaxf(hi(I), 0.f), 255.f);
+                }
+            } else {
+                const f2 s2 = fma2(dxp, dxp, fma2(dyp, dyp, one2));
+                const f2 r = pk(rsqrtf(lo(s2)), rsqrtf(hi(s2)));
+                const f2 nx = mul2(dxp, r), ny = mul2(dyp, r);
+                const f2 m[6] = {one2, nx, ny, mul2(nx, nx), mul2(ny, ny), mul2(nx, ny)};
 #pragma unroll
-                for (int kk = 0; kk < 6; ++kk) I = fma2(a[kk][c], m[kk], I);
-                o[c] = fminf(fmaxf(lo(I), 0.f), 255.f);
-                o[3 + c] = fminf(fmaxf(hi(I), 0.f), 255.f);
+                for (int c = 0; c < 3; ++c) {
+                    f2 I = pk(0.f, 0.f);
+#pragma unroll
+                    for (int kk = 0; kk < 6; ++kk) I = fma2(a[kk][c], m[kk], I);
+                    o[c] = fminf(fmaxf(lo(I), 0.f), 255.f);
+                    o[3 + c] = fminf(fmaxf(hi(I), 0.f), 255.f);
+                }
             }
             float* out = inten + (static_cast<int64_t>(list[i]) * G.HW + p0) * 3;
             if (kO8) {
