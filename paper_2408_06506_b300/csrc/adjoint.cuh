@@ -571,8 +571,11 @@ __global__ void __launch_bounds__(256, 2) shade_coeff_grad_kernel(ShadeGeom G, i
             const bool flat = __all_sync(0xffffffffu, !valid || ((dxp | dyp) & 0x7fffffff7fffffffull) == 0ull);
             if (!valid) continue;
             const float2 u01 = sl[128], u23 = sl[160], u45 = sl[192];
-            const f2 s2 = fma2(dxp, dxp, fma2(dyp, dyp, one2));
-            const f2 r = pk(rsqrtf(lo(s2)), rsqrtf(hi(s2)));
+            // |(D_x, D_y, 1)|^-1 (the flat form needs it only for the slopes)
+            auto inv_norm = [&]() {
+                const f2 s2 = fma2(dxp, dxp, fma2(dyp, dyp, one2));
+                return pk(rsqrtf(lo(s2)), rsqrtf(hi(s2)));
+            };
             const float ua[3] = {u01.x, u01.y, u23.x}, ub[3] = {u23.y, u45.x, u45.y};
             if (flat) {
                 f2 gm1 = pk(0.f, 0.f), gm2 = pk(0.f, 0.f);
@@ -596,12 +599,14 @@ __global__ void __launch_bounds__(256, 2) shade_coeff_grad_kernel(ShadeGeom G, i
                 }
                 if (kSlopes) {
                     // (dL/dD_x, dL/dD_y) = (gm_1, gm_2) r at n = 0
+                    const f2 r = inv_norm();
                     const f2 sx = mul2(gm1, r), sy = mul2(gm2, r);
                     *reinterpret_cast<float4*>(slopes + (static_cast<int64_t>(list[i]) * G.HW + p0) * 2) =
                         make_float4(lo(sx), lo(sy), hi(sx), hi(sy));
                 }
                 continue;
             }
+            const f2 r = inv_norm();
             const f2 nx = mul2(dxp, r), ny = mul2(dyp, r);
             const f2 m[6] = {one2, nx, ny, mul2(nx, nx), mul2(ny, ny), mul2(nx, ny)};
             // the accumulation reads the monomials with a non-finite depth difference set to
