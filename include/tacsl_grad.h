@@ -43,7 +43,10 @@ int tacsl_penalty_forces_adjoint(const tacsl_sdf_set* set, const tacsl_contact_p
 
 /* Clamped intensities [B][H][W][3] (float, HWC) of the images tacsl_shade_image would
  * quantise: the forward of the differentiable image.  An image with a bad sensor_id is
- * left untouched and sets TACSL_DEVERR_BAD_SENSOR_ID. */
+ * left untouched and sets TACSL_DEVERR_BAD_SENSOR_ID.
+ * The image entry points below take finite coefficients: where a group of pixels sees a
+ * flat gel (n = 0) the kernels leave out the terms of the zero monomials, which is exact
+ * for finite coefficients but drops a NaN or infinity such a term would have carried. */
 int tacsl_shade_intensity(const tacsl_shading* shading, int64_t B, const int32_t* sensor_id,
                           const float* depth_map, float* intensity, tacsl_stream_t stream);
 
