@@ -225,3 +225,54 @@ def test_full_size_against_one_pass():
     scale = gd1.abs().amax(dim=(1, 2), keepdim=True)
     assert bool((err <= 1e-5 * scale + 1e-30).all()), float((err / scale.clamp_min(1e-30)).max())
     assert bool(torch.isfinite(gd).all())
+
+
+def test_flat_and_relief_warps_match_oracle():
+    """Maps that are a flat gel except for a bump on some images, so that in one launch
+    some warps take the flat form (every pixel of their 64-pixel segment flat) and others
+    the full one: intensity, coefficient adjoint, loss map, coefficient gradient, slopes and
+    depth gradient against the oracle, and the flat images' slopes against their closed
+    form."""
+    S, B, H, W = 2, 6, 24, 128
+    px, py = 2e-4, 3e-4
+    rng = np.random.default_rng(80)
+    co = synth.shading_coeffs(S, H, W, 181)
+    dm = np.full((B, H, W), synth.D0, np.float32)
+    yy, xx = np.mgrid[0:H, 0:W]
+    for b in (1, 2, 4):          # a bump of 40 um on part of the image
+        cy, cx = rng.uniform(6, H - 6), rng.uniform(20, W - 20)
+        dm[b] -= (4e-5 * np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / 30.0)).astype(np.float32)
+    sid = (np.arange(B) % S).astype(np.int32)
+    _, inten, _ = oracle.shade(co, px, py, sid, dm, with_intensity=True)
+    assert (np.minimum(np.abs(inten), np.abs(inten - 255)) > CLAMP_MARGIN).all()
+    tgt = np.clip(inten + rng.normal(0, 15, size=inten.shape), 0, 255).astype(np.float32)
+    gI = rng.normal(size=(B, H, W, 3)).astype(np.float32)
+    sh = tacsl.Shading(dev(co), px, py)
+    d_sid, d_dm = dev(sid), dev(dm)
+    lib = ta._lib()
+    out = torch.empty(B, H, W, 3, device="cuda")
+    assert lib.tacsl_shade_intensity(C.byref(sh.c), B, P(d_sid), P(d_dm), P(out), None) == 0
+    torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy() - inten).max() <= 1e-3
+    for mse in (True, False):
+        u = dev(tgt) if mse else dev(gI)
+        lm, gc, sl, gd = _two_pass(sh, B, H, W, d_sid, d_dm, u, mse, S=S)
+        if mse:
+            ref = G.shade_mse(co, px, py, sid, dm, tgt)
+            ref_sl = G.shade_slopes(co, px, py, sid, dm, target=tgt)
+            _close(lm.cpu().numpy(), ref["loss_map"], 1e-4)
+        else:
+            ref = G.shade_gradients(co, px, py, sid, dm, gI)
+            ref_sl = G.shade_slopes(co, px, py, sid, dm, g_intensity=gI)
+        _close(gc.cpu().numpy(), ref["coeffs"], 1e-3)
+        _close(sl.cpu().numpy(), ref_sl, 1e-3)
+        _close(gd.cpu().numpy(), ref["depth"], 1e-3)
+        # a flat image's slopes: (sum_c g_c A_1c, sum_c g_c A_2c) at every pixel
+        slh = sl.cpu().numpy().astype(np.float64)
+        for b in (0, 3, 5):
+            A = co[sid[b]].astype(np.float64)
+            g = 2 * (inten[b] - tgt[b]) if mse else gI[b].astype(np.float64)
+            for axis in (0, 1):
+                want = (g * np.moveaxis(A[1 + axis], 0, -1)).sum(-1)
+                assert np.abs(slh[b, :, :, axis] - want).max() <= 1e-4 * np.abs(want).max()
+    assert tacsl.check_errors() == 0
