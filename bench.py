@@ -651,6 +651,12 @@ def run_ours(args, rank, world, local_rank, dist):
         "roofline_step": {"bound": "hbm", "achieved": step_achieved, "peak": peak, "unit": "GB/s",
                           "frac": step_achieved / peak, "algorithmic_bytes": alg, "bytes": parts,
                           "kernels": ["tacsl::shade_kernel", "tacsl::penalty_kernel"]},
+        # the image kernel on the same maps with every pixel perturbed (no flat neighbourhoods)
+        "roofline_dense": {"bound": "hbm", "kernel": "tacsl::shade_kernel", "algorithmic_bytes": img_bytes,
+                           "avg_launch_ms": breakdown["shade_image_dense_ms"],
+                           "achieved": img_bytes / (breakdown["shade_image_dense_ms"] * 1e-3) / 1e9, "peak": peak,
+                           "unit": "GB/s",
+                           "frac": img_bytes / (breakdown["shade_image_dense_ms"] * 1e-3) / 1e9 / peak},
         "clocks": clk.summary(),
         "timed_region": {"repeats": len(reps), "steps_per_repeat": args.steps, "seconds": timed_s,
                          "ms_per_step": {"median": ms_step, "min": min(reps) / args.steps,
