@@ -260,6 +260,40 @@ def test_shade_mse_rejects(lib):
     assert call(B=0, lm=None, gc=None, gd=None) == 0   # nothing to do
 
 
+def test_shade_slopes_entry_points_reject(lib):
+    """The two-pass depth gradient's entry points refuse bad arguments on the host, before
+    any device call (so this runs without a GPU)."""
+    from paper_2408_06506_b300 import autograd as ta
+    L = ta._lib()
+    sh = _shading()
+    S = C.byref(sh)
+    # tacsl_shade_mse_slopes(shading, B, sid, dm, target, loss_map, grad_coeffs, slopes, stream)
+    f = L.tacsl_shade_mse_slopes
+    assert f(None, 4, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, None) == INVALID
+    assert f(C.byref(_shading(W=18)), 4, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, None) == INVALID
+    assert f(S, -1, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, None) == INVALID
+    assert f(S, 4, FAKE, FAKE, FAKE, FAKE, FAKE, None, None) == INVALID          # slopes missing
+    assert f(S, 4, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE + 8, None) == INVALID      # not 16-byte aligned
+    assert f(S, 4, FAKE, FAKE, FAKE + 2, FAKE, FAKE, FAKE, None) == INVALID      # target
+    assert f(S, 4, FAKE, FAKE + 4, FAKE, FAKE, FAKE, FAKE, None) == INVALID      # depth maps
+    assert f(S, 0, None, None, None, None, None, None, None) == 0               # nothing to do
+    # tacsl_shade_adjoint_slopes(shading, B, sid, dm, g_intensity, grad_coeffs, slopes, stream)
+    g = L.tacsl_shade_adjoint_slopes
+    assert g(None, 4, FAKE, FAKE, FAKE, FAKE, FAKE, None) == INVALID
+    assert g(S, 4, FAKE, FAKE, FAKE, FAKE, None, None) == INVALID
+    assert g(S, 4, FAKE, FAKE, FAKE, FAKE + 2, FAKE, None) == INVALID            # grad_coeffs
+    assert g(S, 4, 0, FAKE, FAKE, FAKE, FAKE, None) == INVALID                   # sensor ids
+    assert g(S, 0, None, None, None, None, None, None) == 0
+    # tacsl_shade_depth_from_slopes(shading, B, sid, slopes, scale, grad_depth, stream)
+    h = L.tacsl_shade_depth_from_slopes
+    assert h(None, 4, FAKE, FAKE, None, FAKE, None) == INVALID
+    assert h(S, 4, FAKE, FAKE + 8, None, FAKE, None) == INVALID                 # slopes: 16-byte aligned
+    assert h(S, 4, FAKE, FAKE, None, FAKE + 4, None) == INVALID                 # grad_depth: 8-byte aligned
+    assert h(S, 4, FAKE, FAKE, FAKE + 2, FAKE, None) == INVALID                 # scale
+    assert h(S, 4, FAKE, FAKE, None, None, None) == INVALID
+    assert h(S, 0, None, None, None, None, None) == 0
+
+
 def test_render_step_requires_matching_camera(lib):
     st, prm, cam = _set(_sdf()), _params(), _camera(H=8, W=16)
     sh = _shading(H=12, W=16)
